@@ -1,0 +1,214 @@
+"""Seeded, synthetic initial data for the 1D WCC workloads.
+
+This module is the only code shared by the CUDA path's tests/bench and the CPU
+oracle.  It holds no arithmetic of the scheme: it only evaluates initial
+conditions and turns them into the paper's DOFs, the scaled derivatives
+u_kx = dx^k d^k u0/dx^k at every cell centre of the integer stage
+(Eqs. 1D_Derivative_DEF, 1DPolynomial_Space).  Piecewise-constant data get the
+exact cell average of the data and zero derivatives.
+
+Random numbers come from splitmix64 (Steele, Lea & Flood 2014), so every
+workload is reproducible from its seed on any machine.
+
+Array layout of every generator's result: float64 [cells, nv, P+1].
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+ADVECTION, BURGERS, EULER = 0, 1, 2
+PERIODIC, TRANSMISSIVE = 0, 1
+GAMMA = 1.4
+
+_MASK = (1 << 64) - 1
+
+
+class SplitMix64:
+    """splitmix64 generator; ``uniform()`` gives doubles in [0, 1) from the top
+    53 bits."""
+
+    def __init__(self, seed: int):
+        self.state = seed & _MASK
+
+    def next_u64(self) -> int:
+        self.state = (self.state + 0x9E3779B97F4A7C15) & _MASK
+        z = self.state
+        z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & _MASK
+        z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & _MASK
+        return z ^ (z >> 31)
+
+    def uniform(self, lo: float = 0.0, hi: float = 1.0) -> float:
+        return lo + (hi - lo) * ((self.next_u64() >> 11) * (1.0 / (1 << 53)))
+
+
+def num_cells(N: int, bc: int, parity: int = 0) -> int:
+    """Cells of a stage: N for periodic; N+1 on the integer stage and N on the
+    half stage for non-periodic boundaries (Sec. 2.1)."""
+    if bc == PERIODIC:
+        return N
+    return N + 1 if parity == 0 else N
+
+
+def centres(N: int, x_l: float, x_r: float, bc: int, parity: int = 0) -> np.ndarray:
+    """Cell centres: x_L + i dx on the integer stage, x_L + (i + 1/2) dx on the
+    half stage."""
+    dx = (x_r - x_l) / N
+    off = 0.0 if parity == 0 else 0.5
+    return x_l + (np.arange(num_cells(N, bc, parity)) + off) * dx
+
+
+def smooth_dofs(derivs, x: np.ndarray, dx: float, P: int) -> np.ndarray:
+    """DOFs of smooth data: derivs(x, k) returns d^k u0/dx^k; result [cells, P+1]."""
+    return np.stack([derivs(x, k) * dx ** k for k in range(P + 1)], axis=1)
+
+
+# ---------------------------------------------------------------- problems
+
+
+@dataclass
+class Problem:
+    """A workload: the conservation law, mesh, boundary and integer-stage DOFs."""
+
+    system: int
+    N: int
+    P: int
+    x_l: float
+    x_r: float
+    bc: int
+    q0: np.ndarray  # [cells, nv, P+1]
+    name: str = ""
+
+    @property
+    def dx(self) -> float:
+        return (self.x_r - self.x_l) / self.N
+
+    @property
+    def nv(self) -> int:
+        return 3 if self.system == EULER else 1
+
+
+def sine_derivative(x, k, freq=math.pi, amp=1.0, phase=0.0):
+    """k-th derivative of amp * sin(freq x + phase)."""
+    return amp * freq ** k * np.sin(freq * x + phase + k * math.pi / 2)
+
+
+def advection_sine(N: int, P: int, x_l: float = -1.0, x_r: float = 1.0) -> Problem:
+    """u0 = sin(pi x) on a periodic domain (Sec. 5.1, first case)."""
+    x = centres(N, x_l, x_r, PERIODIC)
+    dx = (x_r - x_l) / N
+    q = smooth_dofs(lambda xx, k: sine_derivative(xx, k), x, dx, P)[:, None, :]
+    return Problem(ADVECTION, N, P, x_l, x_r, PERIODIC, q, "advection-sine")
+
+
+def advection_polynomial(N: int, P: int, coeffs, x_l: float = 0.0, x_r: float = 1.0) -> Problem:
+    """u0 = sum_j coeffs[j] x^j with transmissive boundaries."""
+    x = centres(N, x_l, x_r, TRANSMISSIVE)
+    dx = (x_r - x_l) / N
+    poly = np.polynomial.Polynomial(coeffs)
+
+    def d(xx, k):
+        return poly.deriv(k)(xx) if k <= poly.degree() else np.zeros_like(xx)
+
+    q = smooth_dofs(d, x, dx, P)[:, None, :]
+    return Problem(ADVECTION, N, P, x_l, x_r, TRANSMISSIVE, q, "advection-polynomial")
+
+
+@dataclass
+class FourierData:
+    mean: float
+    amps: np.ndarray
+    phases: np.ndarray
+
+    def derivative(self, x, k):
+        out = np.full_like(x, self.mean if k == 0 else 0.0, dtype=np.float64)
+        for j, (A, ph) in enumerate(zip(self.amps, self.phases), start=1):
+            out = out + sine_derivative(x, k, freq=float(j), amp=A, phase=ph)
+        return out
+
+
+def burgers_fourier_data(seed: int = 2104043470, modes: int = 8) -> FourierData:
+    """u0 = 0.5 + sum_{k=1}^{8} A_k sin(k x + phi_k), A_k ~ U(-0.2, 0.2),
+    phi_k ~ U(0, 2 pi)."""
+    rng = SplitMix64(seed)
+    amps = np.array([rng.uniform(-0.2, 0.2) for _ in range(modes)])
+    phases = np.array([rng.uniform(0.0, 2 * math.pi) for _ in range(modes)])
+    return FourierData(0.5, amps, phases)
+
+
+def burgers_fourier(N: int, P: int, seed: int = 2104043470) -> Problem:
+    """Burgers on periodic [0, 2 pi] with seeded Fourier initial data."""
+    data = burgers_fourier_data(seed)
+    x_l, x_r = 0.0, 2 * math.pi
+    x = centres(N, x_l, x_r, PERIODIC)
+    q = smooth_dofs(data.derivative, x, (x_r - x_l) / N, P)[:, None, :]
+    return Problem(BURGERS, N, P, x_l, x_r, PERIODIC, q, "burgers-fourier")
+
+
+def shock_time(data: FourierData) -> float:
+    """t_s = -1 / min u0' (first gradient catastrophe of Burgers)."""
+    x = np.linspace(0.0, 2 * math.pi, 200001)
+    return -1.0 / float(np.min(data.derivative(x, 1)))
+
+
+def primitive_to_conserved(rho, u, p, gamma=GAMMA):
+    return np.stack([rho, rho * u, p / (gamma - 1.0) + 0.5 * rho * u * u], axis=-1)
+
+
+def riemann_states(seed: int = 2104043471):
+    """rho, p ~ U(0.1, 1), u ~ U(-0.5, 0.5) on each side: ((rl, ul, pl), (rr, ur, pr))."""
+    rng = SplitMix64(seed)
+    rl, ul, pl = rng.uniform(0.1, 1.0), rng.uniform(-0.5, 0.5), rng.uniform(0.1, 1.0)
+    rr, ur, pr = rng.uniform(0.1, 1.0), rng.uniform(-0.5, 0.5), rng.uniform(0.1, 1.0)
+    return (rl, ul, pl), (rr, ur, pr)
+
+
+def euler_riemann(N: int, P: int, left, right, x_l: float = 0.0, x_r: float = 1.0,
+                  x0: float = 0.5, gamma: float = GAMMA, name: str = "euler-riemann") -> Problem:
+    """Piecewise-constant Euler data with a jump at x0, transmissive boundaries.
+    Each cell holds the exact cell average of the data (a cell cut by x0 gets
+    the length-weighted mix of the two states) and zero derivatives."""
+    x = centres(N, x_l, x_r, TRANSMISSIVE)
+    dx = (x_r - x_l) / N
+    UL = primitive_to_conserved(*[np.float64(v) for v in left], gamma=gamma)
+    UR = primitive_to_conserved(*[np.float64(v) for v in right], gamma=gamma)
+    frac_left = np.clip((x0 - (x - 0.5 * dx)) / dx, 0.0, 1.0)
+    q = np.zeros((x.size, 3, P + 1))
+    q[:, :, 0] = frac_left[:, None] * UL[None, :] + (1.0 - frac_left[:, None]) * UR[None, :]
+    return Problem(EULER, N, P, x_l, x_r, TRANSMISSIVE, q, name)
+
+
+def euler_riemann_seeded(N: int, P: int, seed: int = 2104043471) -> Problem:
+    left, right = riemann_states(seed)
+    return euler_riemann(N, P, left, right)
+
+
+def sod(N: int, P: int) -> Problem:
+    """Sod shock tube on [0, 2], jump at x = 1 (Sec. 5.2)."""
+    return euler_riemann(N, P, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 0.0, 2.0, 1.0, name="sod")
+
+
+def euler_density_wave(N: int, P: int, amp: float = 0.2, gamma: float = GAMMA) -> Problem:
+    """rho = 1 + amp sin(2 pi x), u = 1, p = 1 on periodic [0, 1]: conserved
+    variables rho, m = rho, E = p/(gamma-1) + rho/2."""
+    x_l, x_r = 0.0, 1.0
+    x = centres(N, x_l, x_r, PERIODIC)
+    dx = (x_r - x_l) / N
+
+    def rho_d(xx, k):
+        base = sine_derivative(xx, k, freq=2 * math.pi, amp=amp)
+        return base + (1.0 if k == 0 else 0.0)
+
+    rho = smooth_dofs(rho_d, x, dx, P)
+    E = 0.5 * rho.copy()
+    E[:, 0] += 1.0 / (gamma - 1.0)
+    q = np.stack([rho, rho.copy(), E], axis=1)
+    return Problem(EULER, N, P, x_l, x_r, PERIODIC, q, "euler-density-wave")
+
+
+def random_smooth_dofs(ncells: int, nv: int, P: int, seed: int, scale: float = 1.0) -> np.ndarray:
+    """Uniform random DOFs in [-scale, scale] (for unit-level checks)."""
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-scale, scale, size=(ncells, nv, P + 1))
