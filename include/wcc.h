@@ -1,0 +1,142 @@
+/*
+ * wcc.h -- C ABI of the GB300 (sm_103a) implementation of the 1D weighted
+ * compact central (WCC) scheme of Shen & Parsani, "A class of high-order
+ * weighted compact central schemes for solving hyperbolic conservation laws"
+ * (arXiv 2104.04347), for u_t + f(u)_x = 0 with
+ *   f = a u (linear advection), f = u^2/2 (Burgers), or the 1D Euler
+ *   equations U = (rho, rho u, rho e), F = (rho u, rho u^2 + p, (rho e + p) u),
+ *   p = (gamma - 1)(rho e - rho u^2 / 2)            (Sec. 2.1 Eq. 1DHCL; Sec. 5.2)
+ *
+ * Every function returns WCC_OK (0) or a negative WCC_E_* code; the message
+ * of the last failure on a handle is returned by wcc_last_error(handle)
+ * (wcc_last_error(NULL) for failures of wcc_create itself).  No function
+ * has a CPU fallback: without a usable CUDA device every call that needs
+ * one returns WCC_E_CUDA.
+ *
+ * Units and layout shared by all calls:
+ *   - A "stage" is the set of cells at one time level.  Integer stages
+ *     (t^n) hold cells centred on x_L + i dx, half stages (t^{n+1/2}) cells
+ *     centred on x_L + (i + 1/2) dx, dx = (x_R - x_L)/N (Sec. 2.1, Fig. 1).
+ *     Periodic: N cells per stage.  Transmissive ("non-reflection", Sec. 5.2):
+ *     N+1 cells on integer stages, N on half stages; the ghost staggered
+ *     cells are copies of the adjacent cell.
+ *   - DOF arrays on the host side of this ABI are FP64 [cell][var][k],
+ *     k = 0..P, holding the paper's scaled derivatives u_kx = dx^k d^k u/dx^k
+ *     at the cell centre (Eq. 1D_Derivative_DEF, Eq. 1DPolynomial_Space),
+ *     in conserved variables.  count = cells * nv * (P+1), nv = 1 or 3.
+ *   - Time steps are HALF steps: one wcc_step half-step advances a stage to
+ *     the next staggered stage, dt = t^{n+1/2} - t^n (Eq. 1DFlux), and the
+ *     CFL number is nu = a_max dt / dx (Table 1 caption).
+ *   - The device layout is private (planes [var][k][cell] of Taylor
+ *     coefficients u_kx / k!, FP64 or FP32-mixed).
+ *
+ * Ownership: the handle owns all device memory it allocates (cudaMalloc in
+ * wcc_create); caller buffers are borrowed for the duration of a call only.
+ * Calls on one handle are not thread-safe.  wcc_step only enqueues work on
+ * the handle's stream; device-side errors (non-finite values, non-positive
+ * density or pressure) are reported by the next call that synchronises
+ * (wcc_synchronize, wcc_get_*).
+ */
+#ifndef WCC_H
+#define WCC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum { WCC_ADVECTION = 0, WCC_BURGERS = 1, WCC_EULER = 2 };
+enum { WCC_BC_PERIODIC = 0, WCC_BC_TRANSMISSIVE = 1 };
+enum { WCC_FP64 = 0, WCC_FP32_MIXED = 1 };
+
+enum {
+    WCC_OK = 0,
+    WCC_E_INVAL = -1,      /* bad argument (system, N, P, domain, bc, count, pointer) */
+    WCC_E_STATE = -2,      /* call out of order (e.g. wcc_step before wcc_set_initial) */
+    WCC_E_NOMEM = -3,      /* device or host allocation failed */
+    WCC_E_CUDA = -4,       /* CUDA runtime error (no device, launch failure, ...) */
+    WCC_E_NONFINITE = -5,  /* a new DOF or the CFL bound became NaN / Inf */
+    WCC_E_POSITIVITY = -6, /* Euler: non-positive density or pressure at a cell centre */
+    WCC_E_CAPACITY = -7    /* a size above a documented maximum */
+};
+
+/* Scheme and launch options.  wcc_default_options fills:
+ *   precision = WCC_FP64, limiter = 1,
+ *   alpha = 2 (Eq. 1DHighOrderWeights; Sec. 2.2 sets alpha = 2; the same
+ *   value is used for P = 1, where the paper does not state it),
+ *   eps = 1e-40 (Eq. 1D2ndOrderWeights), gamma = 1.4, adv_speed = 1,
+ *   graph_chunk = 32 (half-steps per captured CUDA graph; 0 disables graphs),
+ *   cuda_stream = NULL (the handle creates its own non-blocking stream). */
+typedef struct {
+    int precision;
+    int limiter;
+    double alpha;
+    double eps;
+    double gamma;
+    double adv_speed;
+    int graph_chunk;
+    int reserved;
+    void* cuda_stream; /* cudaStream_t to run on, or NULL */
+} wcc_options;
+
+typedef struct wcc_ctx* wcc_handle;
+
+void wcc_default_options(wcc_options* opt);
+
+/* Create a solver for `system` on [domain[0], domain[1]] with N cells of
+ * width dx and polynomial degree P (1 <= P <= 4; order P+1, Sec. 2.1).
+ * N >= 4; bc is WCC_BC_PERIODIC or WCC_BC_TRANSMISSIVE.  opt may be NULL.
+ * On success *out holds the handle (free with wcc_destroy). */
+int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domain[2], int bc,
+               const wcc_options* opt);
+
+/* Number of cells of the current stage (see the stage rules above). */
+int wcc_num_cells(wcc_handle h, int64_t* ncells);
+
+/* Load an integer stage (t = 0, parity 0) from host FP64 DOFs
+ * [cell][var][k] (see layout above); count must equal cells*nv*(P+1) of an
+ * integer stage.  Synchronous; also evaluates the CFL bound of the stage. */
+int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count);
+
+/* Advance nsteps half-steps with dt = cfl * dx / a_max, a_max the largest
+ * characteristic speed (|a|, |u| or |u| + c) over the centre point values of
+ * the stage being advanced, evaluated on the device (no host round trip).
+ * cfl > 0.  Asynchronous on the handle's stream. */
+int wcc_step(wcc_handle h, int64_t nsteps, double cfl);
+
+/* Advance nsteps half-steps with the given half-step sizes (host array of
+ * nsteps doubles, each > 0).  Asynchronous; dts is read before return. */
+int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts);
+
+/* Copy the current stage to host FP64 DOFs [cell][var][k] (count =
+ * cells*nv*(P+1) of the current stage).  Synchronises the stream and
+ * reports any device-side error raised since the last check. */
+int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count);
+
+/* Time, number of half-steps taken and stage parity (0: integer stage,
+ * 1: half stage).  Synchronises and reports device-side errors. */
+int wcc_get_state(wcc_handle h, double* t, int64_t* half_steps, int* parity);
+
+/* Half-step sizes actually used, oldest first: copies min(cap, taken)
+ * values to dts and sets *n to the number taken since wcc_set_initial. */
+int wcc_get_dt_history(wcc_handle h, double* dts, int64_t cap, int64_t* n);
+
+/* Wait for all work queued on the handle; reports device-side errors. */
+int wcc_synchronize(wcc_handle h);
+
+/* Device memory footprint of the handle in bytes. */
+int wcc_device_bytes(wcc_handle h, int64_t* bytes);
+
+/* Number of kernel launches (graph nodes included) enqueued by the handle
+ * since wcc_create. */
+int wcc_launch_count(wcc_handle h, int64_t* launches);
+
+const char* wcc_last_error(wcc_handle h);
+void wcc_destroy(wcc_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* WCC_H */

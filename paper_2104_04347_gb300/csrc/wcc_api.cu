@@ -1,0 +1,488 @@
+// wcc_api.cu -- the C ABI of include/wcc.h: solver handle, device memory,
+// layout conversion, time marching with device-side dt and CUDA graphs.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/wcc.h"
+#include "wcc_launch.h"
+#include "wcc_scheme.cuh"
+
+using namespace wcc;
+
+namespace {
+
+thread_local std::string g_create_error;
+
+// ------------------------------------------------ layout conversion kernels
+
+// Host layout [cell][var][k] of paper-scaled derivatives u_kx  <->  device
+// planes of Taylor coefficients e_k = u_kx / k!.  One thread per element:
+// reads of the host-layout array are coalesced.
+__global__ void aos_to_planes_fp64(const double* __restrict__ aos, long long n, int nv, int K, long long pitch,
+                                   double* __restrict__ planes) {
+    const long long total = n * nv * K;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % K);
+        const long long rest = e / K;
+        const int v = (int)(rest % nv);
+        const long long cell = rest / nv;
+        double inv_fact = 1.0;
+        for (int j = 2; j <= k; ++j) inv_fact /= (double)j;
+        planes[(long long)(v * K + k) * pitch + cell] = aos[e] * inv_fact;
+    }
+}
+
+__global__ void planes_to_aos_fp64(const double* __restrict__ planes, long long n, int nv, int K, long long pitch,
+                                   double* __restrict__ aos) {
+    const long long total = n * nv * K;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % K);
+        const long long rest = e / K;
+        const int v = (int)(rest % nv);
+        const long long cell = rest / nv;
+        double fact = 1.0;
+        for (int j = 2; j <= k; ++j) fact *= (double)j;
+        aos[e] = planes[(long long)(v * K + k) * pitch + cell] * fact;
+    }
+}
+
+unsigned elementwise_grid(long long total) {
+    long long b = (total + 255) / 256;
+    if (b > 152 * 16) b = 152 * 16;
+    return (unsigned)(b < 1 ? 1 : b);
+}
+
+}  // namespace
+
+struct wcc_ctx {
+    int system = 0, P = 0, nv = 1, K = 2, bc = 0;
+    long long N = 0;
+    double xl = 0, xr = 1, dx = 1;
+    wcc_options opt{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int device = 0;
+
+    long long pitch = 0;
+    double* s64[2] = {nullptr, nullptr};
+    double* staging = nullptr;  // host-layout FP64 staging buffer
+    DevState* st = nullptr;
+    double* hist = nullptr;
+    long long hist_cap = 0;
+    long long bytes = 0;
+
+    int cur = 0;          // buffer holding the current stage
+    int parity = 0;       // stage parity of the current stage
+    long long steps = 0;  // half-steps since wcc_set_initial
+    bool initialised = false;
+
+    cudaGraphExec_t gexec = nullptr;
+    int g_cur = -1, g_parity = -1, g_chunk = 0;
+    double g_cfl = 0.0;
+
+    long long launches = 0;
+    std::string err;
+};
+
+namespace {
+
+int fail(wcc_ctx* h, int code, const std::string& msg) {
+    if (h) h->err = msg; else g_create_error = msg;
+    return code;
+}
+
+int cuda_fail(wcc_ctx* h, cudaError_t e, const char* what) {
+    return fail(h, WCC_E_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define WCC_CHECK(h, call)                                              \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);        \
+    } while (0)
+
+long long stage_cells(const wcc_ctx* h, int parity) {
+    if (h->bc == WCC_BC_PERIODIC) return h->N;
+    return parity == 0 ? h->N + 1 : h->N;
+}
+
+long long next_cells(const wcc_ctx* h, int parity) { return stage_cells(h, parity ^ 1); }
+
+cudaError_t launch_step_kernel(wcc_ctx* h, const StepArgs& a) {
+    switch (h->system) {
+        case WCC_ADVECTION: return launch_halfstep<ADVECTION>(h->P, h->opt.precision, a, h->stream);
+        case WCC_BURGERS: return launch_halfstep<BURGERS>(h->P, h->opt.precision, a, h->stream);
+        default: return launch_halfstep<EULER>(h->P, h->opt.precision, a, h->stream);
+    }
+}
+
+StepArgs make_args(wcc_ctx* h, int cur, int parity, double cfl, double dt_fixed) {
+    StepArgs a{};
+    a.in64 = h->s64[cur];
+    a.out64 = h->s64[cur ^ 1];
+    a.in32 = nullptr;
+    a.out32 = nullptr;
+    a.pitch = h->pitch;
+    a.n_old = stage_cells(h, parity);
+    a.n_new = next_cells(h, parity);
+    a.parity = parity;
+    a.bc = h->bc;
+    a.limiter = h->opt.limiter;
+    a.alpha_is_two = (h->opt.alpha == 2.0);
+    a.dx = h->dx;
+    a.cfl = cfl;
+    a.dt_fixed = dt_fixed;
+    a.adv = h->opt.adv_speed;
+    a.gamma = h->opt.gamma;
+    a.alpha = h->opt.alpha;
+    a.eps = h->opt.eps;
+    a.st = h->st;
+    a.hist = h->hist;
+    a.hist_cap = h->hist_cap;
+    return a;
+}
+
+int read_state(wcc_ctx* h, DevState* out) {
+    WCC_CHECK(h, cudaStreamSynchronize(h->stream));
+    WCC_CHECK(h, cudaMemcpy(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost));
+    if (out->err & ERR_NONFINITE) return fail(h, WCC_E_NONFINITE, "a DOF or the CFL bound became NaN/Inf");
+    if (out->err & ERR_POSITIVITY)
+        return fail(h, WCC_E_POSITIVITY, "non-positive density or pressure at a cell centre");
+    return WCC_OK;
+}
+
+int ensure_history(wcc_ctx* h, long long need) {
+    if (need <= h->hist_cap) return WCC_OK;
+    long long cap = h->hist_cap > 0 ? h->hist_cap : 1024;
+    while (cap < need) cap *= 2;
+    double* nh = nullptr;
+    WCC_CHECK(h, cudaStreamSynchronize(h->stream));
+    cudaError_t e = cudaMalloc(&nh, cap * sizeof(double));
+    if (e != cudaSuccess) return fail(h, WCC_E_NOMEM, "cudaMalloc of the dt history failed");
+    if (h->hist) {
+        WCC_CHECK(h, cudaMemcpy(nh, h->hist, h->hist_cap * sizeof(double), cudaMemcpyDeviceToDevice));
+        cudaFree(h->hist);
+    }
+    h->bytes += (cap - h->hist_cap) * (long long)sizeof(double);
+    h->hist = nh;
+    h->hist_cap = cap;
+    if (h->gexec) {  // captured launches hold the old pointer
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    return WCC_OK;
+}
+
+int enqueue_one(wcc_ctx* h, double cfl, double dt_fixed) {
+    StepArgs a = make_args(h, h->cur, h->parity, cfl, dt_fixed);
+    cudaError_t e = launch_step_kernel(h, a);
+    if (e != cudaSuccess) return cuda_fail(h, e, "half-step launch");
+    h->launches += 1;
+    h->cur ^= 1;
+    h->parity ^= 1;
+    h->steps += 1;
+    return WCC_OK;
+}
+
+// Capture `chunk` (even) CFL half-steps starting from the current buffer and
+// parity into one graph; after it the buffer and parity are unchanged.
+int build_graph(wcc_ctx* h, int chunk, double cfl) {
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    WCC_CHECK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int cur = h->cur, parity = h->parity;
+    for (int s = 0; s < chunk; ++s) {
+        StepArgs a = make_args(h, cur, parity, cfl, 0.0);
+        cudaError_t e = launch_step_kernel(h, a);
+        if (e != cudaSuccess) {
+            cudaStreamEndCapture(h->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(h, e, "half-step launch during capture");
+        }
+        cur ^= 1;
+        parity ^= 1;
+    }
+    WCC_CHECK(h, cudaStreamEndCapture(h->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->gexec = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    h->g_cur = h->cur;
+    h->g_parity = h->parity;
+    h->g_cfl = cfl;
+    h->g_chunk = chunk;
+    return WCC_OK;
+}
+
+void release(wcc_ctx* h) {
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    for (int i = 0; i < 2; ++i)
+        if (h->s64[i]) cudaFree(h->s64[i]);
+    if (h->staging) cudaFree(h->staging);
+    if (h->st) cudaFree(h->st);
+    if (h->hist) cudaFree(h->hist);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+void wcc_default_options(wcc_options* opt) {
+    if (!opt) return;
+    std::memset(opt, 0, sizeof(*opt));
+    opt->precision = WCC_FP64;
+    opt->limiter = 1;
+    opt->alpha = 2.0;
+    opt->eps = 1e-40;
+    opt->gamma = 1.4;
+    opt->adv_speed = 1.0;
+    opt->graph_chunk = 32;
+    opt->cuda_stream = nullptr;
+}
+
+int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domain[2], int bc,
+               const wcc_options* opt) {
+    if (!out) return fail(nullptr, WCC_E_INVAL, "out is NULL");
+    *out = nullptr;
+    if (system < WCC_ADVECTION || system > WCC_EULER) return fail(nullptr, WCC_E_INVAL, "unknown system");
+    if (P < 1 || P > 4) return fail(nullptr, WCC_E_INVAL, "P must be in 1..4");
+    if (N < 4 || N > (1ll << 31)) return fail(nullptr, WCC_E_INVAL, "N must be in 4..2^31");
+    if (!domain || !(domain[1] > domain[0])) return fail(nullptr, WCC_E_INVAL, "domain must satisfy x_L < x_R");
+    if (bc != WCC_BC_PERIODIC && bc != WCC_BC_TRANSMISSIVE) return fail(nullptr, WCC_E_INVAL, "unknown bc");
+    wcc_options o;
+    wcc_default_options(&o);
+    if (opt) o = *opt;
+    if (o.precision != WCC_FP64)
+        return fail(nullptr, WCC_E_INVAL, "precision not available in this build");
+    if (!(o.eps >= 0.0) || !(o.alpha > 0.0) || !(o.gamma > 1.0))
+        return fail(nullptr, WCC_E_INVAL, "need eps >= 0, alpha > 0, gamma > 1");
+    if (o.graph_chunk < 0) return fail(nullptr, WCC_E_INVAL, "graph_chunk must be >= 0");
+
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess || ndev == 0) return fail(nullptr, WCC_E_CUDA, "no CUDA device available");
+
+    wcc_ctx* h = new (std::nothrow) wcc_ctx();
+    if (!h) return fail(nullptr, WCC_E_NOMEM, "host allocation failed");
+    h->system = system;
+    h->P = P;
+    h->nv = (system == WCC_EULER) ? 3 : 1;
+    h->K = P + 1;
+    h->bc = bc;
+    h->N = N;
+    h->xl = domain[0];
+    h->xr = domain[1];
+    h->dx = (domain[1] - domain[0]) / (double)N;
+    h->opt = o;
+    if (h->opt.graph_chunk & 1) h->opt.graph_chunk += 1;
+    cudaGetDevice(&h->device);
+
+    if (o.cuda_stream) {
+        h->stream = (cudaStream_t)o.cuda_stream;
+    } else {
+        e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete h;
+            return cuda_fail(nullptr, e, "cudaStreamCreate");
+        }
+        h->own_stream = true;
+    }
+
+    const long long maxcells = N + 1;
+    h->pitch = (maxcells + 63) / 64 * 64;  // 512-byte aligned planes
+    const long long planes = (long long)h->nv * h->K;
+    const size_t state_bytes = (size_t)(planes * h->pitch) * sizeof(double);
+    const size_t staging_bytes = (size_t)(maxcells * planes) * sizeof(double);
+    bool ok = cudaMalloc(&h->s64[0], state_bytes) == cudaSuccess &&
+              cudaMalloc(&h->s64[1], state_bytes) == cudaSuccess &&
+              cudaMalloc(&h->staging, staging_bytes) == cudaSuccess &&
+              cudaMalloc(&h->st, sizeof(DevState)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        release(h);
+        delete h;
+        return fail(nullptr, WCC_E_NOMEM, "cudaMalloc of the solver state failed");
+    }
+    h->bytes = 2 * (long long)state_bytes + (long long)staging_bytes + (long long)sizeof(DevState);
+    // zero the padding once so that no plane ever holds uninitialised data
+    cudaMemsetAsync(h->s64[0], 0, state_bytes, h->stream);
+    cudaMemsetAsync(h->s64[1], 0, state_bytes, h->stream);
+    cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream);
+    if (ensure_history(h, 4096) != WCC_OK) {
+        std::string m = h->err;
+        release(h);
+        delete h;
+        return fail(nullptr, WCC_E_NOMEM, m);
+    }
+    e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        release(h);
+        delete h;
+        return cuda_fail(nullptr, e, "wcc_create");
+    }
+    *out = h;
+    return WCC_OK;
+}
+
+int wcc_num_cells(wcc_handle h, int64_t* ncells) {
+    if (!h || !ncells) return fail(h, WCC_E_INVAL, "NULL argument");
+    *ncells = stage_cells(h, h->parity);
+    return WCC_OK;
+}
+
+int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    if (!dofs) return fail(h, WCC_E_INVAL, "dofs is NULL");
+    const long long n = stage_cells(h, 0);
+    if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match cells*nv*(P+1) of an integer stage");
+    WCC_CHECK(h, cudaMemcpyAsync(h->staging, dofs, (size_t)count * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    h->cur = 0;
+    h->parity = 0;
+    h->steps = 0;
+    aos_to_planes_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->staging, n, h->nv, h->K, h->pitch,
+                                                                          h->s64[0]);
+    WCC_CHECK(h, cudaGetLastError());
+    WCC_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
+    StepArgs a = make_args(h, 0, 0, 0.0, 0.0);
+    cudaError_t e;
+    const long long var_stride = (long long)h->K * h->pitch;
+    switch (h->system) {
+        case WCC_ADVECTION: e = launch_stage_speed<ADVECTION>(h->s64[0], var_stride, n, a, 0, h->stream); break;
+        case WCC_BURGERS: e = launch_stage_speed<BURGERS>(h->s64[0], var_stride, n, a, 0, h->stream); break;
+        default: e = launch_stage_speed<EULER>(h->s64[0], var_stride, n, a, 0, h->stream); break;
+    }
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage speed launch");
+    h->launches += 2;
+    h->initialised = true;
+    DevState s;
+    int rc = read_state(h, &s);
+    if (rc != WCC_OK) {
+        h->initialised = false;
+        return rc;
+    }
+    return WCC_OK;
+}
+
+int wcc_step(wcc_handle h, int64_t nsteps, double cfl) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
+    if (nsteps < 0) return fail(h, WCC_E_INVAL, "nsteps < 0");
+    if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
+    int rc = ensure_history(h, h->steps + nsteps);
+    if (rc != WCC_OK) return rc;
+    long long left = nsteps;
+    const int chunk = h->opt.graph_chunk;
+    if (chunk >= 2 && h->stream != nullptr && left >= chunk) {
+        if (!h->gexec || h->g_cur != h->cur || h->g_parity != h->parity || h->g_cfl != cfl ||
+            h->g_chunk != chunk) {
+            rc = build_graph(h, chunk, cfl);
+            if (rc != WCC_OK) return rc;
+        }
+        while (left >= chunk) {
+            WCC_CHECK(h, cudaGraphLaunch(h->gexec, h->stream));
+            h->launches += chunk;
+            h->steps += chunk;
+            left -= chunk;
+        }
+    }
+    for (; left > 0; --left) {
+        rc = enqueue_one(h, cfl, 0.0);
+        if (rc != WCC_OK) return rc;
+    }
+    return WCC_OK;
+}
+
+int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
+    if (nsteps < 0 || (nsteps > 0 && !dts)) return fail(h, WCC_E_INVAL, "bad nsteps / dts");
+    for (int64_t s = 0; s < nsteps; ++s)
+        if (!(dts[s] > 0.0) || !(dts[s] < 1e300)) return fail(h, WCC_E_INVAL, "every dt must be positive and finite");
+    int rc = ensure_history(h, h->steps + nsteps);
+    if (rc != WCC_OK) return rc;
+    for (int64_t s = 0; s < nsteps; ++s) {
+        rc = enqueue_one(h, 0.0, dts[s]);
+        if (rc != WCC_OK) return rc;
+    }
+    return WCC_OK;
+}
+
+int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    if (!dofs) return fail(h, WCC_E_INVAL, "dofs is NULL");
+    if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
+    const long long n = stage_cells(h, h->parity);
+    if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match the current stage");
+    planes_to_aos_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->s64[h->cur], n, h->nv, h->K, h->pitch,
+                                                                           h->staging);
+    WCC_CHECK(h, cudaGetLastError());
+    h->launches += 1;
+    WCC_CHECK(h, cudaMemcpyAsync(dofs, h->staging, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DevState s;
+    return read_state(h, &s);
+}
+
+int wcc_get_state(wcc_handle h, double* t, int64_t* half_steps, int* parity) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DevState s;
+    int rc = read_state(h, &s);
+    if (t) *t = s.t;
+    if (half_steps) *half_steps = s.step;
+    if (parity) *parity = h->parity;
+    return rc;
+}
+
+int wcc_get_dt_history(wcc_handle h, double* dts, int64_t cap, int64_t* n) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    if (cap < 0 || (cap > 0 && !dts)) return fail(h, WCC_E_INVAL, "bad dts / cap");
+    DevState s;
+    int rc = read_state(h, &s);
+    long long taken = s.step;
+    if (n) *n = taken;
+    long long m = taken < cap ? taken : cap;
+    if (m > h->hist_cap) m = h->hist_cap;
+    if (m > 0) WCC_CHECK(h, cudaMemcpy(dts, h->hist, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost));
+    return rc;
+}
+
+int wcc_synchronize(wcc_handle h) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DevState s;
+    return read_state(h, &s);
+}
+
+int wcc_device_bytes(wcc_handle h, int64_t* bytes) {
+    if (!h || !bytes) return fail(h, WCC_E_INVAL, "NULL argument");
+    *bytes = h->bytes;
+    return WCC_OK;
+}
+
+int wcc_launch_count(wcc_handle h, int64_t* launches) {
+    if (!h || !launches) return fail(h, WCC_E_INVAL, "NULL argument");
+    *launches = h->launches;
+    return WCC_OK;
+}
+
+const char* wcc_last_error(wcc_handle h) { return h ? h->err.c_str() : g_create_error.c_str(); }
+
+void wcc_destroy(wcc_handle h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    delete h;
+}
+
+}  // extern "C"

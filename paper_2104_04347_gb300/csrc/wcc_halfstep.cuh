@@ -1,0 +1,219 @@
+// wcc_halfstep.cuh -- the fused half-step kernel (FP64 instantiation) and
+// the small auxiliary kernels (stage CFL bound, layout conversion).
+//
+// One launch advances a whole stage by one staggered half-step
+// (Sec. 2.1, Fig. 1).  Each CTA:
+//   1. loads kThreads parent cells (coalesced: consecutive threads read
+//      consecutive cells of each [var][k] plane), runs the Cauchy-Kovalewski
+//      procedure once per parent, and keeps the parent record (two flux /
+//      half-average contributions and the vertex Taylor coefficients) in
+//      shared memory -- each parent is a vertex of two new cells;
+//   2. builds kTile new cells from neighbouring records: finite-volume cell
+//      average, central-difference derivatives, point value, limiter;
+//   3. reduces the new stage's largest characteristic speed (warp shuffles,
+//      one atomic per CTA); the last CTA to finish publishes the stage bound,
+//      advances t and records dt, so the next launch derives its dt on the
+//      device without a host round trip.
+#pragma once
+
+#include "wcc_scheme.cuh"
+
+namespace wcc {
+
+__device__ __forceinline__ long long parent_index(long long p, long long n, int bc) {
+    if (bc == BC_PERIODIC) {
+        if (p < 0) p += n;
+        if (p >= n) p -= n;
+        if (p < 0 || p >= n) p = ((p % n) + n) % n;  // tail CTAs reach past one period
+        return p;
+    }
+    // transmissive: ghost staggered cells copy the adjacent cell
+    return p < 0 ? 0 : (p >= n ? n - 1 : p);
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Block-wide max of the speed, one atomic per CTA, then the last CTA's
+// bookkeeping.  dt is the step this launch used.
+__device__ __forceinline__ void finish_halfstep(double speed, unsigned err, double dt, const StepArgs& args) {
+    __shared__ double s_max[kThreads / 32];
+    __shared__ unsigned s_err;
+    __shared__ int s_last;
+    if (threadIdx.x == 0) s_err = 0u;
+    __syncthreads();
+    // NaN must win the max: map it to +Inf and flag it
+    if (speed != speed) {
+        speed = __longlong_as_double(0x7ff0000000000000ll);
+        err |= ERR_NONFINITE;
+    }
+    speed = warp_max(speed);
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = speed;
+    if (err) atomicOr(&s_err, err);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = s_max[0];
+#pragma unroll
+        for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, s_max[w]);
+        if (m > 0.0) atomicMax(&args.st->amax_bits[args.parity ^ 1], (unsigned long long)__double_as_longlong(m));
+        if (s_err) atomicOr(&args.st->err, s_err);
+        __threadfence();
+        const unsigned done = atomicAdd(&args.st->blocks_done, 1u);
+        s_last = (done == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        DevState* st = args.st;
+        // Every CTA of this launch has read amax_bits[parity]; clear it for
+        // the launch after next, which accumulates into it.
+        st->amax_bits[args.parity] = 0ull;
+        const long long k = st->step;
+        if (k < args.hist_cap) args.hist[k] = dt;
+        st->step = k + 1;
+        st->t = st->t + dt;
+        st->blocks_done = 0u;
+        if (not_finite(dt)) st->err |= ERR_NONFINITE;
+        __threadfence();
+    }
+}
+
+template <int SYS, int P>
+__global__ void __launch_bounds__(kThreads) halfstep_fp64(const StepArgs args) {
+    constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
+    constexpr int NREC = NV * (P + 3);
+    __shared__ double rec[NREC][kThreads];
+
+    const int t = threadIdx.x;
+    const long long first_new = (long long)blockIdx.x * kTile;
+
+    double dt;
+    if (args.cfl > 0.0) {
+        const double amax = __longlong_as_double((long long)args.st->amax_bits[args.parity]);
+        dt = args.cfl * args.dx / amax;
+    } else {
+        dt = args.dt_fixed;
+    }
+    const double lam = dt / args.dx;
+
+    // ---- phase 1: parent record of parent slot t
+    {
+        const long long p = parent_index(first_new + t - (args.parity ? 1 : 0), args.n_old, args.bc);
+        double c[NV][K];
+        sfor<0, NV>([&](auto V) {
+            constexpr int v = decltype(V)::value;
+            sfor<0, K>([&](auto Ki) {
+                constexpr int k = decltype(Ki)::value;
+                c[v][k] = __ldg(args.in64 + (long long)(v * K + k) * args.pitch + p);
+            });
+        });
+        ParentRecord<SYS, P, double> r;
+        parent_record<SYS, P, double>(c, lam, args, r);
+        sfor<0, NV>([&](auto V) {
+            constexpr int v = decltype(V)::value;
+            rec[v][t] = r.A[v];
+            rec[NV + v][t] = r.B[v];
+            sfor<0, K>([&](auto Ki) {
+                constexpr int k = decltype(Ki)::value;
+                rec[2 * NV + v * K + k][t] = r.vtx[v][k];
+            });
+        });
+    }
+    __syncthreads();
+
+    // ---- phase 2: new cell t from parent slots t (left) and t + 1 (right)
+    const long long i = first_new + t;
+    double speed = 0.0;
+    unsigned err = 0u;
+    if (t < kTile && i < args.n_new) {
+        double e[NV][K], ubar[NV], vl[NV], vr[NV];
+        sfor<0, NV>([&](auto V) {
+            constexpr int v = decltype(V)::value;
+            double vL[K], vR[K];
+            sfor<0, K>([&](auto Ki) {
+                constexpr int k = decltype(Ki)::value;
+                vL[k] = rec[2 * NV + v * K + k][t];
+                vR[k] = rec[2 * NV + v * K + k][t + 1];
+            });
+            ubar[v] = rec[v][t] + rec[NV + v][t + 1];
+            vl[v] = vL[0];
+            vr[v] = vR[0];
+            derivatives_and_point_value<P, double>(ubar[v], vL, vR, e[v]);
+        });
+
+        if (args.limiter) {
+            if constexpr (NV == 1) {
+                limit_scalar<P, double>(e[0], ubar[0], vl[0], vr[0], args);
+            } else {
+                // Sec. 4: limit characteristic variables L(ubar) U, map back with R(ubar).
+                EulerEigen<double> E;
+                if (!euler_eigen<double>(ubar, args.gamma, E)) err |= ERR_POSITIVITY;
+                double ce[3][K], cub[3], cvl[3], cvr[3];
+                sfor<0, 3>([&](auto Ii) {
+                    constexpr int r = decltype(Ii)::value;
+                    cub[r] = E.L[r][0] * ubar[0] + E.L[r][1] * ubar[1] + E.L[r][2] * ubar[2];
+                    cvl[r] = E.L[r][0] * vl[0] + E.L[r][1] * vl[1] + E.L[r][2] * vl[2];
+                    cvr[r] = E.L[r][0] * vr[0] + E.L[r][1] * vr[1] + E.L[r][2] * vr[2];
+                    sfor<0, K>([&](auto Ki) {
+                        constexpr int k = decltype(Ki)::value;
+                        ce[r][k] = E.L[r][0] * e[0][k] + E.L[r][1] * e[1][k] + E.L[r][2] * e[2][k];
+                    });
+                    limit_scalar<P, double>(ce[r], cub[r], cvl[r], cvr[r], args);
+                });
+                sfor<0, 3>([&](auto Vi) {
+                    constexpr int v = decltype(Vi)::value;
+                    sfor<0, K>([&](auto Ki) {
+                        constexpr int k = decltype(Ki)::value;
+                        e[v][k] = E.Rm[v][0] * ce[0][k] + E.Rm[v][1] * ce[1][k] + E.Rm[v][2] * ce[2][k];
+                    });
+                });
+            }
+        }
+
+        bool bad = false;
+        sfor<0, NV>([&](auto V) {
+            constexpr int v = decltype(V)::value;
+            sfor<0, K>([&](auto Ki) {
+                constexpr int k = decltype(Ki)::value;
+                bad |= not_finite(e[v][k]);
+                __stcs(args.out64 + (long long)(v * K + k) * args.pitch + i, e[v][k]);
+            });
+        });
+        if (bad) err |= ERR_NONFINITE;
+        double u0[NV];
+        sfor<0, NV>([&](auto V) { u0[decltype(V)::value] = e[decltype(V)::value][0]; });
+        speed = wave_speed<SYS, double>(u0, args, err);
+    }
+    finish_halfstep(speed, err, dt, args);
+}
+
+// Largest characteristic speed of a stage (used once after loading data).
+template <int SYS>
+__global__ void __launch_bounds__(256) stage_speed(const double* u0planes, long long var_stride, long long n,
+                                                    StepArgs args, int slot) {
+    constexpr int NV = nvars(SYS);
+    double m = 0.0;
+    unsigned err = 0u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        double u0[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) u0[v] = u0planes[v * var_stride + i];
+        double s = wave_speed<SYS, double>(u0, args, err);
+        if (s != s) {
+            s = __longlong_as_double(0x7ff0000000000000ll);
+            err |= ERR_NONFINITE;
+        }
+        m = fmax(m, s);
+    }
+    m = warp_max(m);
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(&args.st->amax_bits[slot], (unsigned long long)__double_as_longlong(m));
+    if (err) atomicOr(&args.st->err, err);
+}
+
+}  // namespace wcc

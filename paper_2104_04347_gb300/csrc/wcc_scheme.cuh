@@ -1,0 +1,426 @@
+// wcc_scheme.cuh -- device building blocks of the fused WCC half-step
+// (Shen & Parsani, arXiv 2104.04347, Sec. 2.1-2.2 and Sec. 4).
+//
+// Internal representation: Taylor coefficients.  A cell polynomial
+// u(xi) = sum_k u_kx xi^k / k!  (xi = (x - x_i)/dx, Eq. 1DPolynomial_Space)
+// is held as e_k = u_kx / k!, and the space-time Cauchy-Kovalewski table as
+// X[a][b] = dx^a dt^b d_x^a d_t^b u / (a! b!).  In this form products of
+// series are plain Cauchy products (no binomial weights), the PDE
+// u_t = -f_x becomes X[a][b+1] = -lam (a+1)/(b+1) F[a+1][b], and every
+// constant of the scheme (flux-integral weights, central-difference weights,
+// smoothness-indicator quadratic form) is a compile-time double folded into
+// the instruction stream through the static loops below.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace wcc {
+
+enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
+enum { PREC_FP64 = 0, PREC_FP32_MIXED = 1 };
+
+// One CTA stages kThreads parent cells and produces kTile = kThreads - 1 new
+// cells: new cell t of the tile sits between parents t and t + 1.
+constexpr int kThreads = 128;
+constexpr int kTile = kThreads - 1;
+
+enum : unsigned { ERR_NONFINITE = 1u, ERR_POSITIVITY = 2u };
+
+// Device-resident time-marching state (one per solver).
+struct DevState {
+    // amax_bits[s]: largest characteristic speed of the stage with parity s,
+    // as the bit pattern of a non-negative double (integer max == double max).
+    unsigned long long amax_bits[2];
+    double t;
+    long long step;
+    unsigned int blocks_done;  // CTAs finished in the running half-step
+    unsigned int err;          // ERR_* bits, sticky
+};
+
+// Arguments of one half-step launch.  Plane (v, k) of a stage holds the
+// Taylor coefficient e_k of variable v for every cell, pitch elements apart.
+// FP64: every plane in *64.  FP32-mixed: plane k = 0 in *64 ([v][cell]),
+// planes k >= 1 in *32 ([v][k-1][cell]).
+struct StepArgs {
+    const double* in64;
+    const float* in32;
+    double* out64;
+    float* out32;
+    long long pitch;
+    long long n_old;
+    long long n_new;
+    int parity;   // 0: new[i] from old[i], old[i+1]; 1: from old[i-1], old[i]
+    int bc;
+    int limiter;
+    int alpha_is_two;
+    double dx;
+    double cfl;       // > 0: dt = cfl dx / amax of the stage being advanced
+    double dt_fixed;  // used when cfl <= 0
+    double adv;       // advection speed
+    double gamma;
+    double alpha;
+    double eps;
+    DevState* st;
+    double* hist;     // dt of every half-step, indexed by DevState::step
+    long long hist_cap;
+};
+
+// ------------------------------------------------------------ static loops
+
+template <int I>
+struct Int {
+    static constexpr int value = I;
+};
+
+// Calls f(Int<B>{}), ..., f(Int<E-1>{}); inside f the index is a constant
+// expression (decltype(i)::value), so array indices resolve to registers and
+// coefficient functions evaluate at compile time.
+template <int B, int E, class F>
+__device__ __forceinline__ void sfor(F&& f) {
+    if constexpr (B < E) {
+        f(Int<B>{});
+        sfor<B + 1, E>(static_cast<F&&>(f));
+    }
+}
+
+__host__ __device__ constexpr double cfact(int n) {
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+__host__ __device__ constexpr double cbinom(int n, int k) { return cfact(n) / (cfact(k) * cfact(n - k)); }
+__host__ __device__ constexpr double cpow2(int n) {
+    double r = 1.0;
+    for (int i = 0; i < (n < 0 ? -n : n); ++i) r = (n < 0) ? r * 0.5 : r * 2.0;
+    return r;
+}
+// (-1/2)^n and (1/2)^n
+__host__ __device__ constexpr double chalf(int n, bool negative) {
+    return (negative && (n & 1)) ? -cpow2(-n) : cpow2(-n);
+}
+// int_{-1/2}^{1/2} xi^e dxi
+__host__ __device__ constexpr double cmoment(int e) { return (e & 1) ? 0.0 : 1.0 / ((e + 1) * cpow2(e)); }
+// Quadratic form of the smoothness indicator (Eq. 1DSmoothIndicator) in
+// Taylor coefficients: beta = sum_{j,l >= 1} csmooth(j, l) e_j e_l, because
+// d^k u/dxi^k = sum_{j >= k} e_j j!/(j-k)! xi^{j-k} and the dx powers cancel.
+__host__ __device__ constexpr double csmooth(int j, int l) {
+    double s = 0.0;
+    const int m = j < l ? j : l;
+    for (int k = 1; k <= m; ++k)
+        s += cfact(j) / cfact(j - k) * cfact(l) / cfact(l - k) * cmoment(j + l - 2 * k);
+    return s;
+}
+
+__host__ __device__ constexpr int nvars(int sys) { return sys == EULER ? 3 : 1; }
+
+// NaN / Inf test on the exponent bits (integer pipe only).
+__device__ __forceinline__ bool not_finite(double x) {
+    return (__double2hiint(x) & 0x7ff00000) == 0x7ff00000;
+}
+__device__ __forceinline__ bool not_finite(float x) {
+    return (__float_as_int(x) & 0x7f800000) == 0x7f800000;
+}
+
+// ------------------------------------------------ Cauchy-Kovalewski (Eq. 1DCauchy_Kovalewski, Sec. 4)
+
+// Parent-cell quantities shared by the two new cells that touch this parent:
+//   A[v]    = ubar_R/2 + lam fbar   (contribution when the parent is the left one)
+//   B[v]    = ubar_L/2 - lam fbar   (contribution when it is the right one)
+//   vtx[v][k] = Taylor coefficient k of the vertex polynomial at t^{n+1/2}
+// so that the new cell average is A[left] + B[right] (Eq. SubEq:1DIntegral
+// with Eqs. SubEq:1DCellAVGR, SubEq:1DCellAVGL, Cal1DFlux) and the vertex
+// values of Eq. SubEq:Cal_1D_Derivatives_4 are k! vtx[k].
+template <int SYS, int P, class R>
+struct ParentRecord {
+    static constexpr int NV = nvars(SYS);
+    R A[NV];
+    R B[NV];
+    R vtx[NV][P + 1];
+};
+
+template <int SYS, int P, class R>
+__device__ __forceinline__ void parent_record(const R (&c)[nvars(SYS)][P + 1], R lam, const StepArgs& args,
+                                              ParentRecord<SYS, P, R>& out) {
+    constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
+    // X[v][a][b]: space-time Taylor table; F0[v][b]: flux coefficients at a = 0.
+    R X[NV][K][K];
+    R F0[NV][K];
+    sfor<0, NV>([&](auto V) {
+        constexpr int v = decltype(V)::value;
+        sfor<0, K>([&](auto A) { X[v][decltype(A)::value][0] = c[v][decltype(A)::value]; });
+    });
+
+    if constexpr (SYS == ADVECTION) {
+        const R a = (R)args.adv;
+        const R la = lam * a;
+        sfor<0, P>([&](auto Bi) {
+            constexpr int b = decltype(Bi)::value;
+            sfor<0, P - b>([&](auto Ai) {
+                constexpr int aa = decltype(Ai)::value;
+                constexpr double w = (aa + 1.0) / (b + 1.0);
+                X[0][aa][b + 1] = -(la * (R)w) * X[0][aa + 1][b];
+            });
+        });
+        sfor<0, K>([&](auto Bi) {
+            constexpr int b = decltype(Bi)::value;
+            F0[0][b] = a * X[0][0][b];
+        });
+    } else if constexpr (SYS == BURGERS) {
+        R F[K][K];
+        sfor<0, K>([&](auto Bi) {
+            constexpr int b = decltype(Bi)::value;
+            // F = u^2/2: Cauchy product, symmetric terms paired.
+            sfor<0, K - b>([&](auto Ai) {
+                constexpr int aa = decltype(Ai)::value;
+                R s = (R)0;
+                sfor<0, aa + 1>([&](auto Ii) {
+                    constexpr int i = decltype(Ii)::value;
+                    sfor<0, b + 1>([&](auto Ji) {
+                        constexpr int j = decltype(Ji)::value;
+                        constexpr int i2 = aa - i, j2 = b - j;
+                        // visit each unordered pair once
+                        if constexpr (i * (b + 1) + j < i2 * (b + 1) + j2) {
+                            s = fma(X[0][i][j], X[0][i2][j2], s);
+                        } else if constexpr (i == i2 && j == j2) {
+                            s = fma((R)0.5 * X[0][i][j], X[0][i][j], s);
+                        }
+                    });
+                });
+                F[aa][b] = s;
+            });
+            if constexpr (b < P) {
+                sfor<0, P - b>([&](auto Ai) {
+                    constexpr int aa = decltype(Ai)::value;
+                    constexpr double w = (aa + 1.0) / (b + 1.0);
+                    X[0][aa][b + 1] = -(lam * (R)w) * F[aa + 1][b];
+                });
+            }
+            F0[0][b] = F[0][b];
+        });
+    } else {
+        // Euler, U = (rho, m, E): velocity w = m / rho by series division,
+        // q = m w, p = (gamma - 1)(E - q/2), H = E + p, F = (m, q + p, H w).
+        const R g1 = (R)(args.gamma - 1.0);
+        R w[K][K] = {}, H[K][K] = {}, Fm[K][K] = {}, FE[K][K] = {};
+        const R inv_rho = (R)1 / X[0][0][0];
+        sfor<0, K>([&](auto Bi) {
+            constexpr int b = decltype(Bi)::value;
+            sfor<0, K - b>([&](auto Ai) {
+                constexpr int aa = decltype(Ai)::value;
+                R s = X[1][aa][b];
+                sfor<0, aa + 1>([&](auto Ii) {
+                    constexpr int i = decltype(Ii)::value;
+                    sfor<0, b + 1>([&](auto Ji) {
+                        constexpr int j = decltype(Ji)::value;
+                        if constexpr (i != 0 || j != 0) s = fma(-X[0][i][j], w[aa - i][b - j], s);
+                    });
+                });
+                w[aa][b] = s * inv_rho;
+                R q = (R)0;
+                sfor<0, aa + 1>([&](auto Ii) {
+                    constexpr int i = decltype(Ii)::value;
+                    sfor<0, b + 1>([&](auto Ji) {
+                        constexpr int j = decltype(Ji)::value;
+                        q = fma(X[1][i][j], w[aa - i][b - j], q);
+                    });
+                });
+                const R p = g1 * fma((R)-0.5, q, X[2][aa][b]);
+                H[aa][b] = X[2][aa][b] + p;
+                Fm[aa][b] = q + p;
+                R fe = (R)0;
+                sfor<0, aa + 1>([&](auto Ii) {
+                    constexpr int i = decltype(Ii)::value;
+                    sfor<0, b + 1>([&](auto Ji) {
+                        constexpr int j = decltype(Ji)::value;
+                        fe = fma(H[i][j], w[aa - i][b - j], fe);
+                    });
+                });
+                FE[aa][b] = fe;
+            });
+            if constexpr (b < P) {
+                sfor<0, P - b>([&](auto Ai) {
+                    constexpr int aa = decltype(Ai)::value;
+                    constexpr double wgt = (aa + 1.0) / (b + 1.0);
+                    const R lw = lam * (R)wgt;
+                    X[0][aa][b + 1] = -lw * X[1][aa + 1][b];
+                    X[1][aa][b + 1] = -lw * Fm[aa + 1][b];
+                    X[2][aa][b + 1] = -lw * FE[aa + 1][b];
+                });
+            }
+            F0[0][b] = X[1][0][b];
+            F0[1][b] = Fm[0][b];
+            F0[2][b] = FE[0][b];
+        });
+    }
+
+    sfor<0, NV>([&](auto V) {
+        constexpr int v = decltype(V)::value;
+        // Eq. Cal1DFlux in Taylor form: fbar = sum_b F[0][b] / (b + 1).
+        R fbar = F0[v][0];
+        sfor<1, K>([&](auto Bi) {
+            constexpr int b = decltype(Bi)::value;
+            fbar = fma((R)(1.0 / (b + 1.0)), F0[v][b], fbar);
+        });
+        // Eqs. SubEq:1DCellAVGR / SubEq:1DCellAVGL: half-cell averages.
+        R ur = c[v][0], ul = c[v][0];
+        sfor<1, K>([&](auto Ki) {
+            constexpr int k = decltype(Ki)::value;
+            constexpr double wk = 1.0 / ((k + 1.0) * cpow2(k));
+            ur = fma((R)wk, c[v][k], ur);
+            ul = fma((R)((k & 1) ? -wk : wk), c[v][k], ul);
+        });
+        out.A[v] = fma(lam, fbar, (R)0.5 * ur);
+        out.B[v] = fma(-lam, fbar, (R)0.5 * ul);
+        // Eq. SubEq:Cal_1D_Derivatives_4: vertex values at t^{n+1/2}.
+        sfor<0, K>([&](auto Ki) {
+            constexpr int k = decltype(Ki)::value;
+            R s = X[v][k][0];
+            sfor<1, K - k>([&](auto Mi) { s += X[v][k][decltype(Mi)::value]; });
+            out.vtx[v][k] = s;
+        });
+    });
+}
+
+// ------------------------------------------------------ new-cell update
+
+// Derivatives from high to low order (Eq. SubEq:Cal_1D_Derivatives_3) and
+// the point value (Eq. 1DCalU), in Taylor coefficients:
+//   e_{k+1} = (vR_k - vL_k - sum_{m>=3 odd} 2 C(k+m, m) 2^-m e_{k+m}) / (k+1)
+//   e_0     = ubar - sum_{k>=2 even} e_k / ((k+1) 2^k)
+template <int P, class R>
+__device__ __forceinline__ void derivatives_and_point_value(R ubar, const R (&vL)[P + 1], const R (&vR)[P + 1],
+                                                            R (&e)[P + 1]) {
+    sfor<0, P>([&](auto Ii) {
+        constexpr int k = P - 1 - decltype(Ii)::value;
+        R s = vR[k] - vL[k];
+        sfor<3, P - k + 1>([&](auto Mi) {
+            constexpr int m = decltype(Mi)::value;
+            if constexpr (m & 1) {
+                constexpr double cm = 2.0 * cbinom(k + m, m) * cpow2(-m);
+                s = fma((R)-cm, e[k + m], s);
+            }
+        });
+        e[k + 1] = (k == 0) ? s : s * (R)(1.0 / (k + 1.0));
+    });
+    R u0 = ubar;
+    sfor<2, P + 1>([&](auto Ki) {
+        constexpr int k = decltype(Ki)::value;
+        if constexpr ((k & 1) == 0) u0 = fma((R)(-1.0 / ((k + 1.0) * cpow2(k))), e[k], u0);
+    });
+    e[0] = u0;
+}
+
+// WENO-type limiter of Sec. 2.2 on one scalar (or characteristic) component.
+// e: Taylor coefficients of u_0 (overwritten by u_*), ubar its cell average,
+// vl / vr the time-extrapolated vertex values u_{i-1/2}, u_{i+1/2}.
+template <int P, class R>
+__device__ __forceinline__ void limit_scalar(R (&e)[P + 1], R ubar, R vl, R vr, const StepArgs& args) {
+    const R s1 = (R)2 * (ubar - vl);   // Eq. SubEq:1DU12, slope of u_1
+    const R s2 = (R)2 * (vr - ubar);   // slope of u_2
+    // beta_0 (Eq. 1DSmoothIndicator) as a quadratic form in e_1..e_P
+    R b0 = (R)0;
+    sfor<1, P + 1>([&](auto Ji) {
+        constexpr int j = decltype(Ji)::value;
+        R row = (R)0;
+        sfor<j, P + 1>([&](auto Li) {
+            constexpr int l = decltype(Li)::value;
+            constexpr double cjl = (l == j ? 1.0 : 2.0) * csmooth(j, l);
+            if constexpr (cjl != 0.0) row = fma((R)cjl, e[l], row);
+        });
+        b0 = fma(row, e[j], b0);
+    });
+    const R b1 = s1 * s1, b2 = s2 * s2;
+    const R eps = (R)args.eps;
+    R wh0, wh1, wh2;
+    if constexpr (P == 1) {
+        // Eq. 1D2ndOrderWeights: (1 / (beta + eps))^alpha
+        R i0 = (R)1 / (b0 + eps), i1 = (R)1 / (b1 + eps), i2 = (R)1 / (b2 + eps);
+        if (args.alpha_is_two) {
+            wh0 = i0 * i0; wh1 = i1 * i1; wh2 = i2 * i2;
+        } else {
+            const R al = (R)args.alpha;
+            wh0 = pow(i0, al); wh1 = pow(i1, al); wh2 = pow(i2, al);
+        }
+    } else {
+        // Eq. 1DHighOrderWeights: sigma from the residuals at both vertices,
+        // tau = (u_Px)^2 = (P! e_P)^2.
+        R up = e[0], um = e[0];
+        sfor<1, P + 1>([&](auto Ki) {
+            constexpr int k = decltype(Ki)::value;
+            up = fma((R)chalf(k, false), e[k], up);
+            um = fma((R)chalf(k, true), e[k], um);
+        });
+        const R rr = up - vr, rl = um - vl;
+        const R sigma = fma(rr, rr, rl * rl);
+        const R tp = (R)cfact(P) * e[P];
+        const R st = sigma * (tp * tp);
+        R r0 = st / fma(b0, b0, eps), r1 = st / fma(b1, b1, eps), r2 = st / fma(b2, b2, eps);
+        if (args.alpha_is_two) {
+            wh0 = fma(r0, r0, (R)1); wh1 = r1 * r1; wh2 = r2 * r2;
+        } else {
+            const R al = (R)args.alpha;
+            wh0 = (R)1 + pow(r0, al); wh1 = pow(r1, al); wh2 = pow(r2, al);
+        }
+    }
+    const R inv = (R)1 / (wh0 + wh1 + wh2);
+    const R w0 = wh0 * inv, w1 = wh1 * inv, w2 = wh2 * inv;
+    // Eq. 1DLimitedPolynomial, coefficient by coefficient.
+    e[0] = fma(w0, e[0], (w1 + w2) * ubar);
+    e[1] = fma(w0, e[1], fma(w1, s1, w2 * s2));
+    sfor<2, P + 1>([&](auto Ki) { e[decltype(Ki)::value] *= w0; });
+}
+
+// Eigenvectors of the Euler flux Jacobian at the cell average (conserved
+// variables; columns of R for u - c, u, u + c; textbook closed form cited in
+// Sec. 5.2) -- used by the characteristic limiter of Sec. 4.
+template <class R>
+struct EulerEigen {
+    R L[3][3];
+    R Rm[3][3];
+};
+
+template <class R>
+__device__ __forceinline__ bool euler_eigen(const R (&U)[3], R gamma, EulerEigen<R>& E) {
+    const R rho = U[0];
+    const R irho = (R)1 / rho;
+    const R u = U[1] * irho;
+    const R g1 = gamma - (R)1;
+    const R p = g1 * fma((R)-0.5 * U[1], u, U[2]);
+    const R c2 = gamma * p * irho;
+    const bool ok = (rho > (R)0) && (p > (R)0);
+    const R c = sqrt(c2);
+    const R ic = (R)1 / c;
+    const R H = (U[2] + p) * irho;
+    const R b1 = g1 / c2;
+    const R b2 = (R)0.5 * b1 * u * u;
+    E.Rm[0][0] = (R)1;       E.Rm[0][1] = (R)1;              E.Rm[0][2] = (R)1;
+    E.Rm[1][0] = u - c;      E.Rm[1][1] = u;                 E.Rm[1][2] = u + c;
+    E.Rm[2][0] = H - u * c;  E.Rm[2][1] = (R)0.5 * u * u;    E.Rm[2][2] = H + u * c;
+    const R uc = u * ic;
+    E.L[0][0] = (R)0.5 * (b2 + uc);  E.L[0][1] = (R)-0.5 * fma(b1, u, ic);  E.L[0][2] = (R)0.5 * b1;
+    E.L[1][0] = (R)1 - b2;           E.L[1][1] = b1 * u;                    E.L[1][2] = -b1;
+    E.L[2][0] = (R)0.5 * (b2 - uc);  E.L[2][1] = (R)-0.5 * fma(b1, u, -ic); E.L[2][2] = (R)0.5 * b1;
+    return ok;
+}
+
+// Characteristic speed |u| (Burgers), |a| (advection) or |u| + c (Euler)
+// at the centre point values; sets err bits for non-physical states.
+template <int SYS, class R>
+__device__ __forceinline__ double wave_speed(const R* u0, const StepArgs& args, unsigned& err) {
+    if constexpr (SYS == ADVECTION) {
+        return fabs(args.adv);
+    } else if constexpr (SYS == BURGERS) {
+        return fabs((double)u0[0]);
+    } else {
+        const R rho = u0[0];
+        const R u = u0[1] / rho;
+        const R p = (R)(args.gamma - 1.0) * fma((R)-0.5 * u0[1], u, u0[2]);
+        if (!(rho > (R)0) || !(p > (R)0)) err |= ERR_POSITIVITY;
+        return (double)(fabs(u) + sqrt((R)args.gamma * p / rho));
+    }
+}
+
+}  // namespace wcc

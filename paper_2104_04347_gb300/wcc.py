@@ -1,0 +1,215 @@
+"""Python binding of the WCC C ABI (include/wcc.h): argument marshalling only.
+
+Every step of the computation runs in libwcc.so's CUDA kernels.  If the
+library is missing or no GPU is usable, the calls raise -- there is no CPU
+fallback in this package.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libwcc.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "wcc.h")
+
+ADVECTION, BURGERS, EULER = 0, 1, 2
+PERIODIC, TRANSMISSIVE = 0, 1
+FP64, FP32_MIXED = 0, 1
+
+ERRORS = {
+    -1: "WCC_E_INVAL", -2: "WCC_E_STATE", -3: "WCC_E_NOMEM", -4: "WCC_E_CUDA",
+    -5: "WCC_E_NONFINITE", -6: "WCC_E_POSITIVITY", -7: "WCC_E_CAPACITY",
+}
+
+
+class WCCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("limiter", ctypes.c_int),
+        ("alpha", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("adv_speed", ctypes.c_double),
+        ("graph_chunk", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
+_lock = threading.Lock()
+_lib = None
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_dp = ctypes.POINTER(ctypes.c_double)
+_SIGS = {
+    "wcc_default_options": (None, [ctypes.POINTER(Options)]),
+    "wcc_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64, ctypes.c_int,
+                                  _dp, ctypes.c_int, ctypes.POINTER(Options)]),
+    "wcc_num_cells": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc_set_initial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "wcc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
+    "wcc_step_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp]),
+    "wcc_get_dofs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "wcc_get_state": (ctypes.c_int, [ctypes.c_void_p, _dp, _i64p, ctypes.POINTER(ctypes.c_int)]),
+    "wcc_get_dt_history": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int64, _i64p]),
+    "wcc_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
+    "wcc_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc_launch_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "wcc_destroy": (None, [ctypes.c_void_p]),
+}
+
+
+def header_functions(path: str = HEADER) -> list[str]:
+    """Names of the functions declared in a public header."""
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(wcc_\w+)\s*\(", text)))
+
+
+def load(path: str = LIB_PATH):
+    """Load libwcc.so (building it first if needed).  Raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(path):
+                from . import build as _build
+                _build.build()
+            if not os.path.exists(path):
+                raise RuntimeError(f"CUDA library not found at {path}; run the build first")
+            lib = ctypes.CDLL(path)
+            for name, (res, args) in _SIGS.items():
+                fn = getattr(lib, name)
+                fn.restype = res
+                fn.argtypes = args
+            _lib = lib
+    return _lib
+
+
+def default_options() -> Options:
+    o = Options()
+    load().wcc_default_options(ctypes.byref(o))
+    return o
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+class Solver:
+    """One WCC problem on the GPU (wraps a wcc_handle).
+
+    ``dofs`` arrays are float64 [cells, nv, P+1] of the paper-scaled
+    derivatives, as in include/wcc.h.  ``stream`` is a raw cudaStream_t
+    handle (e.g. ``torch.cuda.Stream().cuda_stream``) or None."""
+
+    def __init__(self, system: int, N: int, P: int, domain, bc: int, *, precision: int = FP64,
+                 limiter: bool = True, alpha: float = 2.0, eps: float = 1e-40, gamma: float = 1.4,
+                 adv_speed: float = 1.0, graph_chunk: int = 32, stream: int | None = None):
+        self.lib = load()
+        o = default_options()
+        o.precision = precision
+        o.limiter = 1 if limiter else 0
+        o.alpha = alpha
+        o.eps = eps
+        o.gamma = gamma
+        o.adv_speed = adv_speed
+        o.graph_chunk = graph_chunk
+        o.cuda_stream = stream
+        h = ctypes.c_void_p()
+        dom = (ctypes.c_double * 2)(float(domain[0]), float(domain[1]))
+        rc = self.lib.wcc_create(ctypes.byref(h), system, int(N), int(P), dom, bc, ctypes.byref(o))
+        if rc != 0:
+            raise WCCError(rc, self.lib.wcc_last_error(None).decode())
+        self.h = h
+        self.system, self.N, self.P, self.bc = system, int(N), int(P), bc
+        self.nv = 3 if system == EULER else 1
+        self.dx = (float(domain[1]) - float(domain[0])) / int(N)
+
+    def _check(self, rc: int) -> None:
+        if rc != 0:
+            raise WCCError(rc, self.lib.wcc_last_error(self.h).decode())
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.wcc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def num_cells(self) -> int:
+        n = ctypes.c_int64()
+        self._check(self.lib.wcc_num_cells(self.h, ctypes.byref(n)))
+        return n.value
+
+    def set_initial(self, dofs: np.ndarray) -> None:
+        a = np.ascontiguousarray(dofs, dtype=np.float64)
+        self._check(self.lib.wcc_set_initial(self.h, _ptr(a), a.size))
+
+    def set_initial_ptr(self, host_ptr: int, count: int) -> None:
+        """Load from a raw host pointer (e.g. pinned memory)."""
+        self._check(self.lib.wcc_set_initial(self.h, ctypes.c_void_p(host_ptr), int(count)))
+
+    def step(self, nsteps: int, cfl: float) -> None:
+        self._check(self.lib.wcc_step(self.h, int(nsteps), float(cfl)))
+
+    def step_dt(self, dts) -> None:
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(self.lib.wcc_step_dt(self.h, d.size, d.ctypes.data_as(_dp)))
+
+    def get_dofs(self) -> np.ndarray:
+        n = self.num_cells()
+        out = np.empty((n, self.nv, self.P + 1))
+        self._check(self.lib.wcc_get_dofs(self.h, _ptr(out), out.size))
+        return out
+
+    def get_dofs_ptr(self, host_ptr: int, count: int) -> None:
+        self._check(self.lib.wcc_get_dofs(self.h, ctypes.c_void_p(host_ptr), int(count)))
+
+    def state(self):
+        t = ctypes.c_double()
+        s = ctypes.c_int64()
+        p = ctypes.c_int()
+        self._check(self.lib.wcc_get_state(self.h, ctypes.byref(t), ctypes.byref(s), ctypes.byref(p)))
+        return t.value, s.value, p.value
+
+    def dt_history(self) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._check(self.lib.wcc_get_dt_history(self.h, None, 0, ctypes.byref(n)))
+        out = np.empty(n.value)
+        self._check(self.lib.wcc_get_dt_history(self.h, out.ctypes.data_as(_dp), out.size, ctypes.byref(n)))
+        return out
+
+    def synchronize(self) -> None:
+        self._check(self.lib.wcc_synchronize(self.h))
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        self._check(self.lib.wcc_device_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+    def launch_count(self) -> int:
+        b = ctypes.c_int64()
+        self._check(self.lib.wcc_launch_count(self.h, ctypes.byref(b)))
+        return b.value

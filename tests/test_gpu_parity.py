@@ -1,0 +1,155 @@
+"""GPU parity: the FP64 CUDA path (through the C ABI) against the CPU oracle,
+element by element, on the same seeded inputs with the same half-step sizes.
+
+Bound: max |diff| <= 1e-11 x (scale of each variable) after 100 half-steps."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_04347_gb300 import inputs, wcc
+from tests.gpu_common import TOL64, gpu_run, oracle_run, scaled_error
+
+pytestmark = pytest.mark.gpu
+
+TILE = 127  # new cells per CTA
+
+
+def _problem(system, P, N, bc):
+    if system == inputs.ADVECTION:
+        if bc == inputs.PERIODIC:
+            return inputs.advection_sine(N, P)
+        return inputs.advection_polynomial(N, P, [0.2, -0.5, 0.7, 0.1, -0.3][: P + 1])
+    if system == inputs.BURGERS:
+        pr = inputs.burgers_fourier(N, P)
+        if bc == inputs.TRANSMISSIVE:
+            pr = inputs.Problem(pr.system, N, P, pr.x_l, pr.x_r, bc, np.concatenate([pr.q0, pr.q0[:1]]))
+        return pr
+    if bc == inputs.TRANSMISSIVE:
+        return inputs.euler_riemann_seeded(N, P)
+    return inputs.euler_density_wave(N, P)
+
+
+@pytest.mark.parametrize("system", [inputs.ADVECTION, inputs.BURGERS, inputs.EULER])
+@pytest.mark.parametrize("P", [1, 2, 3, 4])
+@pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
+def test_fp64_parity_100_halfsteps(system, P, bc):
+    N = 5 * TILE + 38          # several tiles and a ragged tail
+    pr = _problem(system, P, N, bc)
+    cfl = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2}[P]
+    q, dts, t, parity = gpu_run(pr, 100, cfl)
+    assert len(dts) == 100 and parity == 0
+    ref, tref, _ = oracle_run(pr, dts)
+    assert abs(t - tref) <= 1e-14 * tref
+    assert q.shape == ref.shape
+    assert scaled_error(q, ref) <= TOL64
+
+
+def test_config1_advection_exact_translate():
+    # Advection of sin(pi x) on periodic [0, 2], N = 200, P = 2, limiter off:
+    # dt from the oracle's constant-speed rule so that t = 2 is hit exactly.
+    pr = inputs.advection_sine(200, 2, 0.0, 2.0)
+    dts = oracle.constant_speed_dts(2.0, 0.25 * pr.dx)
+    q, _, t, parity = gpu_run(pr, None, None, limiter=False, dts=dts)
+    ref, _, _ = oracle_run(pr, dts, limiter=False)
+    assert parity == 0 and abs(t - 2.0) < 1e-12
+    assert scaled_error(q, ref) <= TOL64
+    x = inputs.centres(200, 0.0, 2.0, inputs.PERIODIC)
+    l1 = np.mean(np.abs(q[:, 0, 0] - np.sin(math.pi * x)))
+    assert l1 < 5e-7
+
+
+@pytest.mark.parametrize("N", [4, 5, TILE - 1, TILE, TILE + 1, 2 * TILE])
+@pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
+def test_small_and_tile_edge_sizes(N, bc):
+    pr = _problem(inputs.EULER, 3, N, bc)
+    q, dts, _, _ = gpu_run(pr, 24, 0.2)
+    ref, _, _ = oracle_run(pr, dts)
+    assert scaled_error(q, ref) <= TOL64
+
+
+@pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
+def test_odd_number_of_halfsteps_ends_on_half_stage(bc):
+    pr = _problem(inputs.BURGERS, 3, 300, bc)
+    dts = np.full(7, 0.2 * pr.dx / 1.5)
+    q, _, t, parity = gpu_run(pr, None, None, dts=dts)
+    ref, _, rparity = oracle_run(pr, dts)
+    assert parity == 1 == rparity
+    assert q.shape[0] == inputs.num_cells(300, bc, 1)
+    assert scaled_error(q, ref) <= TOL64
+
+
+def test_graph_and_direct_launches_identical():
+    pr = _problem(inputs.EULER, 3, 3000, inputs.TRANSMISSIVE)
+    q1, d1, _, _ = gpu_run(pr, 70, 0.2, graph_chunk=32)
+    q2, d2, _, _ = gpu_run(pr, 70, 0.2, graph_chunk=0)
+    assert np.array_equal(d1, d2)
+    assert np.array_equal(q1, q2)
+
+
+def test_checkpoint_resume_bitwise():
+    pr = _problem(inputs.BURGERS, 2, 1000, inputs.PERIODIC)
+    q_full, dts, _, _ = gpu_run(pr, 40, 0.3)
+    q_half, d_half, _, _ = gpu_run(pr, 20, 0.3)
+    pr2 = inputs.Problem(pr.system, pr.N, pr.P, pr.x_l, pr.x_r, pr.bc, q_half)
+    q_res, d_res, _, _ = gpu_run(pr2, 20, 0.3)
+    assert np.array_equal(np.concatenate([d_half, d_res]), dts)
+    assert np.array_equal(q_res, q_full)
+
+
+def test_conservation_on_gpu():
+    pr = _problem(inputs.EULER, 3, 4096, inputs.PERIODIC)
+    q, _, _, _ = gpu_run(pr, 200, 0.25)
+    w = np.array([1.0, 0.0, 1.0 / 24.0, 0.0])       # cell average of the P = 3 polynomial
+    tot0 = (pr.q0 @ w).sum(axis=0)
+    tot = (q @ w).sum(axis=0)
+    np.testing.assert_allclose(tot, tot0, rtol=1e-12)
+
+
+def test_error_paths():
+    pr = inputs.euler_riemann_seeded(256, 2)
+    bad = pr.q0.copy()
+    bad[10, 0, 0] = -1.0
+    s = wcc.Solver(pr.system, pr.N, pr.P, (0.0, 1.0), pr.bc)
+    with pytest.raises(wcc.WCCError) as ei:
+        s.step(1, 0.2)
+    assert ei.value.code == -2                           # before set_initial
+    with pytest.raises(wcc.WCCError) as ei:
+        s.set_initial(bad)
+    assert ei.value.code == -6                           # positivity
+    bad[10, 0, 0] = float("nan")
+    with pytest.raises(wcc.WCCError) as ei:
+        s.set_initial(bad)
+    assert ei.value.code in (-5, -6)
+    with pytest.raises(wcc.WCCError) as ei:
+        s.set_initial(pr.q0[:-1])
+    assert ei.value.code == -1                           # wrong count
+    s.set_initial(pr.q0)                                  # recovers
+    s.step(4, 0.2)
+    s.synchronize()
+    s.close()
+
+
+def test_full_size_euler_sampled_windows():
+    # The bench workload: Euler, N = 2^22 on [0, 1], P = 3, transmissive,
+    # seeded Riemann data, CFL 0.2, in the bench's launch configuration
+    # (graph chunks of 32).  After k half-steps a cell depends only on the
+    # initial data within k/2 + 1 cells, so the oracle recomputes windows of
+    # the grid one by one.
+    N, P, k = 1 << 22, 3, 64
+    pr = inputs.euler_riemann_seeded(N, P)
+    q, dts, _, parity = gpu_run(pr, k, 0.2)
+    assert parity == 0 and len(dts) == k
+    rng = np.random.default_rng(5)
+    centres = [N // 2, N // 2 - 40, N // 2 + 40, 3, N - 3] + list(rng.integers(100, N - 100, 3))
+    half = k // 2 + 8
+    for c in centres:
+        lo, hi = max(0, c - 2 * half), min(N + 1, c + 2 * half)
+        sub = inputs.Problem(pr.system, hi - lo - 1, P, 0.0, (hi - lo - 1) * pr.dx, pr.bc, pr.q0[lo:hi])
+        ref, _, _ = oracle_run(sub, dts)
+        # compare cells at least `half` away from an artificial window edge
+        a = lo if lo == 0 else lo + half
+        b = hi if hi == N + 1 else hi - half
+        err = scaled_error(q[a:b], ref[a - lo:b - lo])
+        assert err <= TOL64, (c, err)
