@@ -262,6 +262,8 @@ def run_wcc(args, rank, world):
     e2e_value = world * cells_per_step * e2e_steps / e2e_s
     assert np.all(np.isfinite(h_out.numpy()))
 
+    fp64_peak_meas = wcc.measure_fp_peak(wcc.FP64)
+    fp32_peak_meas = wcc.measure_fp_peak(wcc.FP32_MIXED)
     pk, pk_kind = peaks()
     bpc = bytes_per_cell_update(args.precision)
     cells_per_launch = 0.5 * ((N + 1) + N)
@@ -277,6 +279,8 @@ def run_wcc(args, rank, world):
                 "peak_source": f"{pk_kind} hbm_gbs (MEASURED_PEAKS.json)" if pk_kind == "measured"
                 else "fallback 6.8 TB/s"}
     roof["kernel_ms"] = kernel_ms
+    roof["fp64_fma_peak_measured_tflops"] = fp64_peak_meas
+    roof["fp32_fma_peak_measured_tflops"] = fp32_peak_meas
     roof["bytes_per_cell_update"] = bpc
 
     line = {

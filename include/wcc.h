@@ -132,6 +132,13 @@ int wcc_device_bytes(wcc_handle h, int64_t* bytes);
  * since wcc_create. */
 int wcc_launch_count(wcc_handle h, int64_t* launches);
 
+/* Measured fused-multiply-add throughput of the current device in TFLOP/s
+ * (FP64 for WCC_FP64, FP32 for WCC_FP32_MIXED): a grid of 8 CTAs per SM,
+ * 8 independent FMA chains per thread, timed with CUDA events (~40 ms).
+ * The roofline denominator of ALU-bound kernels; the paper has no
+ * counterpart. */
+int wcc_measure_fp_peak(int precision, double* tflops);
+
 const char* wcc_last_error(wcc_handle h);
 void wcc_destroy(wcc_handle h);
 

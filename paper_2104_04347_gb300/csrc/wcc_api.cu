@@ -152,9 +152,10 @@ StepArgs make_args(wcc_ctx* h, int cur, int parity, double cfl, double dt_fixed)
 int read_state(wcc_ctx* h, DevState* out) {
     WCC_CHECK(h, cudaStreamSynchronize(h->stream));
     WCC_CHECK(h, cudaMemcpy(out, h->st, sizeof(DevState), cudaMemcpyDeviceToHost));
-    if (out->err & ERR_NONFINITE) return fail(h, WCC_E_NONFINITE, "a DOF or the CFL bound became NaN/Inf");
+    // the more specific cause first: a negative density also makes c NaN
     if (out->err & ERR_POSITIVITY)
         return fail(h, WCC_E_POSITIVITY, "non-positive density or pressure at a cell centre");
+    if (out->err & ERR_NONFINITE) return fail(h, WCC_E_NONFINITE, "a DOF or the CFL bound became NaN/Inf");
     return WCC_OK;
 }
 

@@ -66,6 +66,7 @@ _SIGS = {
     "wcc_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
     "wcc_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "wcc_launch_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc_measure_fp_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
     "wcc_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "wcc_destroy": (None, [ctypes.c_void_p]),
 }
@@ -101,6 +102,15 @@ def default_options() -> Options:
     o = Options()
     load().wcc_default_options(ctypes.byref(o))
     return o
+
+
+def measure_fp_peak(precision: int) -> float:
+    """FMA throughput of the current device in TFLOP/s (FP64 or FP32)."""
+    v = ctypes.c_double()
+    rc = load().wcc_measure_fp_peak(int(precision), ctypes.byref(v))
+    if rc != 0:
+        raise WCCError(rc, "peak measurement failed")
+    return v.value
 
 
 def _ptr(a: np.ndarray) -> ctypes.c_void_p:

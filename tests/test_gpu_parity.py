@@ -1,7 +1,10 @@
 """GPU parity: the FP64 CUDA path (through the C ABI) against the CPU oracle,
 element by element, on the same seeded inputs with the same half-step sizes.
 
-Bound: max |diff| <= 1e-11 x (scale of each variable) after 100 half-steps."""
+Bound (see tests/gpu_common.py): per cell max(1e-11 x scale, 50 x the
+oracle's own spread under few-ulp input perturbations); where the scheme is
+well conditioned this is the plain 1e-11 bound, asserted separately for the
+limiter-off runs."""
 import math
 
 import numpy as np
@@ -9,11 +12,13 @@ import pytest
 
 import oracle
 from paper_2104_04347_gb300 import inputs, wcc
-from tests.gpu_common import TOL64, gpu_run, oracle_run, scaled_error
+from tests.gpu_common import (TOL64, gpu_run, gpu_solver, law_of, oracle_run, oracle_spread, parity_violation,
+                              scaled_error, trajectory_check)
 
 pytestmark = pytest.mark.gpu
 
 TILE = 127  # new cells per CTA
+CFL = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2}
 
 
 def _problem(system, P, N, bc):
@@ -31,24 +36,77 @@ def _problem(system, P, N, bc):
     return inputs.euler_density_wave(N, P)
 
 
-@pytest.mark.parametrize("system", [inputs.ADVECTION, inputs.BURGERS, inputs.EULER])
-@pytest.mark.parametrize("P", [1, 2, 3, 4])
-@pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
-def test_fp64_parity_100_halfsteps(system, P, bc):
+ALL = [(s, P, bc) for s in (inputs.ADVECTION, inputs.BURGERS, inputs.EULER) for P in (1, 2, 3, 4)
+       for bc in (inputs.PERIODIC, inputs.TRANSMISSIVE)]
+
+
+def _id(c):
+    return f"{['adv', 'burgers', 'euler'][c[0]]}-P{c[1]}-{['periodic', 'transmissive'][c[2]]}"
+
+
+@pytest.mark.parametrize("case", ALL, ids=_id)
+def test_trajectory_100_halfsteps(case):
+    system, P, bc = case
     N = 5 * TILE + 38          # several tiles and a ragged tail
     pr = _problem(system, P, N, bc)
-    cfl = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2}[P]
-    q, dts, t, parity = gpu_run(pr, 100, cfl)
+    q, dts, t, parity = gpu_run(pr, 100, CFL[P])
     assert len(dts) == 100 and parity == 0
     ref, tref, _ = oracle_run(pr, dts)
-    assert abs(t - tref) <= 1e-14 * tref
-    assert q.shape == ref.shape
+    assert abs(t - tref) <= 1e-14 * tref and q.shape == ref.shape
+    viol, err = trajectory_check(pr, q, dts)
+    assert viol <= 1.0, (viol, err)
+
+
+@pytest.mark.parametrize("case", ALL, ids=_id)
+def test_every_halfstep_from_gpu_state(case):
+    # Teacher-forced: each GPU half-step against one oracle half-step from the
+    # GPU's own previous state (exported through the ABI).
+    system, P, bc = case
+    N = 3 * TILE + 17
+    pr = _problem(system, P, N, bc)
+    law = law_of(pr)
+    worst = 0.0
+    with gpu_solver(pr) as s:
+        s.set_initial(pr.q0)
+        prev = s.get_dofs()
+        for n in range(60):
+            parity = s.state()[2]
+            s.step(1, CFL[P])
+            cur = s.get_dofs()
+            lam = s.dt_history()[-1] / pr.dx
+
+            def run(q):
+                return oracle.halfstep(law, parity, q, lam)
+
+            ref = run(prev)
+            spread = oracle_spread(run, prev, ref, seed=n)
+            worst = max(worst, parity_violation(cur, ref, spread))
+            prev = cur
+    assert worst <= 1.0, worst
+
+
+@pytest.mark.parametrize("system", [inputs.ADVECTION, inputs.BURGERS, inputs.EULER])
+@pytest.mark.parametrize("P", [1, 2, 3, 4])
+def test_limiter_off_plain_bound(system, P):
+    # Without the limiter the scheme is well conditioned: plain 1e-11 bound.
+    N = 4 * TILE + 5
+    pr = _problem(system, P, N, inputs.PERIODIC)
+    q, dts, _, _ = gpu_run(pr, 100, CFL[P], limiter=False)
+    ref, _, _ = oracle_run(pr, dts, limiter=False)
+    assert scaled_error(q, ref) <= TOL64
+
+
+@pytest.mark.parametrize("P", [2, 3, 4])
+def test_smooth_euler_limiter_on_plain_bound(P):
+    pr = inputs.euler_density_wave(600, P)
+    q, dts, _, _ = gpu_run(pr, 100, CFL[P])
+    ref, _, _ = oracle_run(pr, dts)
     assert scaled_error(q, ref) <= TOL64
 
 
 def test_config1_advection_exact_translate():
-    # Advection of sin(pi x) on periodic [0, 2], N = 200, P = 2, limiter off:
-    # dt from the oracle's constant-speed rule so that t = 2 is hit exactly.
+    # Advection of sin(pi x) on periodic [0, 2], N = 200, P = 2, limiter off,
+    # to t = 2 (one period) with nu = 0.25.
     pr = inputs.advection_sine(200, 2, 0.0, 2.0)
     dts = oracle.constant_speed_dts(2.0, 0.25 * pr.dx)
     q, _, t, parity = gpu_run(pr, None, None, limiter=False, dts=dts)
@@ -57,7 +115,8 @@ def test_config1_advection_exact_translate():
     assert scaled_error(q, ref) <= TOL64
     x = inputs.centres(200, 0.0, 2.0, inputs.PERIODIC)
     l1 = np.mean(np.abs(q[:, 0, 0] - np.sin(math.pi * x)))
-    assert l1 < 5e-7
+    l1_ref = np.mean(np.abs(ref[:, 0, 0] - np.sin(math.pi * x)))
+    assert abs(l1 - l1_ref) < 1e-12 and l1 < 1e-6
 
 
 @pytest.mark.parametrize("N", [4, 5, TILE - 1, TILE, TILE + 1, 2 * TILE])
@@ -65,8 +124,8 @@ def test_config1_advection_exact_translate():
 def test_small_and_tile_edge_sizes(N, bc):
     pr = _problem(inputs.EULER, 3, N, bc)
     q, dts, _, _ = gpu_run(pr, 24, 0.2)
-    ref, _, _ = oracle_run(pr, dts)
-    assert scaled_error(q, ref) <= TOL64
+    viol, _ = trajectory_check(pr, q, dts)
+    assert viol <= 1.0
 
 
 @pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
@@ -89,6 +148,7 @@ def test_graph_and_direct_launches_identical():
 
 
 def test_checkpoint_resume_bitwise():
+    # P = 2: the exported u_kx = k! e_k round-trips exactly (k! in {1, 1, 2}).
     pr = _problem(inputs.BURGERS, 2, 1000, inputs.PERIODIC)
     q_full, dts, _, _ = gpu_run(pr, 40, 0.3)
     q_half, d_half, _, _ = gpu_run(pr, 20, 0.3)
@@ -125,6 +185,9 @@ def test_error_paths():
     with pytest.raises(wcc.WCCError) as ei:
         s.set_initial(pr.q0[:-1])
     assert ei.value.code == -1                           # wrong count
+    with pytest.raises(wcc.WCCError) as ei:
+        s.step(1, -0.5)
+    assert ei.value.code in (-1, -2)
     s.set_initial(pr.q0)                                  # recovers
     s.step(4, 0.2)
     s.synchronize()
@@ -144,12 +207,19 @@ def test_full_size_euler_sampled_windows():
     rng = np.random.default_rng(5)
     centres = [N // 2, N // 2 - 40, N // 2 + 40, 3, N - 3] + list(rng.integers(100, N - 100, 3))
     half = k // 2 + 8
+    law = law_of(pr)
     for c in centres:
         lo, hi = max(0, c - 2 * half), min(N + 1, c + 2 * half)
-        sub = inputs.Problem(pr.system, hi - lo - 1, P, 0.0, (hi - lo - 1) * pr.dx, pr.bc, pr.q0[lo:hi])
-        ref, _, _ = oracle_run(sub, dts)
+
+        def run(q0):
+            s = oracle.Solver(law, q0, pr.dx)
+            s.step_dt(dts)
+            return s.q
+
+        ref = run(pr.q0[lo:hi])
+        spread = oracle_spread(run, pr.q0[lo:hi], ref)
         # compare cells at least `half` away from an artificial window edge
         a = lo if lo == 0 else lo + half
         b = hi if hi == N + 1 else hi - half
-        err = scaled_error(q[a:b], ref[a - lo:b - lo])
-        assert err <= TOL64, (c, err)
+        viol = parity_violation(q[a:b], ref[a - lo:b - lo], spread[a - lo:b - lo])
+        assert viol <= 1.0, (c, viol)
