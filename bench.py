@@ -65,12 +65,15 @@ def peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-# FP64 operations the half-step kernel issues per cell-update (Euler, P = 3),
-# counted from the executed DADD / DMUL / DFMA instructions (ncu
+# FP64 operations the half-step kernel issues per cell-update (Euler, P = 3,
+# limiter on), counted from the executed DADD / DMUL / DFMA instructions (ncu
 # smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum over one
-# launch, DFMA counted as 2) divided by the cells of the launch.  None until
-# measured.
-FP64_FLOPS_PER_CELL_UPDATE = None
+# launch at N = 2^21, DFMA counted as 2) divided by the cells of the launch:
+# (2 x 1053618000 + 207934209 + 378169546) / 2097152.5.
+FP64_FLOPS_PER_CELL_UPDATE = 1284.3
+# DRAM bytes (read + write) of one FP64 launch, from the same capture
+# (201536256 + 149675008 at N = 2^21), scaled by cells to N = 2^22.
+FP64_TRAFFIC_PER_CELL = (201536256 + 149675008) / 2097152.5
 # FP64 pipe peak of the GB300 (dense, nominal): 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 
@@ -270,8 +273,10 @@ def run_wcc(args, rank, world):
     if args.precision == "fp64" and FP64_FLOPS_PER_CELL_UPDATE:
         achieved = FP64_FLOPS_PER_CELL_UPDATE * cells_per_launch / (kernel_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None,
-                "peak_source": "nominal GB300 FP64 (no measured FP64 peak)"}
+                "frac": achieved / FP64_PEAK_TFLOPS,
+                "traffic": FP64_TRAFFIC_PER_CELL * cells_per_launch if args.log2n == 22 else None,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe); FMA-chain measurement alongside",
+                "flops_per_cell_update": FP64_FLOPS_PER_CELL_UPDATE}
     else:
         achieved = bpc * cells_per_launch / (kernel_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",

@@ -10,6 +10,7 @@
 
 #include "../../include/wcc.h"
 #include "wcc_launch.h"
+#include "wcc_ff.cuh"
 #include "wcc_scheme.cuh"
 
 using namespace wcc;
@@ -53,6 +54,55 @@ __global__ void planes_to_aos_fp64(const double* __restrict__ planes, long long 
     }
 }
 
+// FP32-mixed: per (cell, var) the cell average (Eq. SubEq:1DCellAVG:
+// ubar = sum_{k even} u_kx / ((k+1)! 2^k)) split into a float-float pair,
+// and e_k = u_kx / k! rounded to FP32 for k >= 1.
+__global__ void aos_to_planes_mixed(const double* __restrict__ aos, long long n, int nv, int K, long long pitch,
+                                    float* __restrict__ planes) {
+    const int NP = K + 1;
+    const long long total = n * nv;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(e % nv);
+        const long long cell = e / nv;
+        const double* q = aos + e * K;
+        double ubar = 0.0, fact = 1.0, p2 = 1.0;
+        for (int k = 0; k < K; ++k) {
+            if (k > 1) fact *= (double)k;
+            if ((k & 1) == 0) ubar += q[k] / (fact * (double)(k + 1) * p2);
+            if (k >= 1) planes[(long long)(v * NP + k + 1) * pitch + cell] = (float)(q[k] / fact);
+            p2 *= 2.0;
+        }
+        float hi, lo;
+        split_double(ubar, hi, lo);
+        planes[(long long)(v * NP + 0) * pitch + cell] = hi;
+        planes[(long long)(v * NP + 1) * pitch + cell] = lo;
+    }
+}
+
+__global__ void planes_to_aos_mixed(const float* __restrict__ planes, long long n, int nv, int K, long long pitch,
+                                    double* __restrict__ aos) {
+    const int NP = K + 1;
+    const long long total = n * nv;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const int v = (int)(e % nv);
+        const long long cell = e / nv;
+        double* q = aos + e * K;
+        double u0 = (double)planes[(long long)(v * NP + 0) * pitch + cell] +
+                    (double)planes[(long long)(v * NP + 1) * pitch + cell];
+        double fact = 1.0, p2 = 2.0;
+        for (int k = 1; k < K; ++k) {
+            fact *= (double)k;
+            p2 *= 2.0;
+            const double ek = (double)planes[(long long)(v * NP + k + 1) * pitch + cell];
+            if ((k & 1) == 0) u0 -= ek / ((double)(k + 1) * (p2 / 2.0));
+            q[k] = ek * fact;
+        }
+        q[0] = u0;
+    }
+}
+
 unsigned elementwise_grid(long long total) {
     long long b = (total + 255) / 256;
     if (b > 152 * 16) b = 152 * 16;
@@ -71,7 +121,8 @@ struct wcc_ctx {
     int device = 0;
 
     long long pitch = 0;
-    double* s64[2] = {nullptr, nullptr};
+    double* s64[2] = {nullptr, nullptr};  // FP64 stages
+    float* s32[2] = {nullptr, nullptr};   // FP32-mixed stages
     double* staging = nullptr;  // host-layout FP64 staging buffer
     DevState* st = nullptr;
     double* hist = nullptr;
@@ -127,8 +178,8 @@ StepArgs make_args(wcc_ctx* h, int cur, int parity, double cfl, double dt_fixed)
     StepArgs a{};
     a.in64 = h->s64[cur];
     a.out64 = h->s64[cur ^ 1];
-    a.in32 = nullptr;
-    a.out32 = nullptr;
+    a.in32 = h->s32[cur];
+    a.out32 = h->s32[cur ^ 1];
     a.pitch = h->pitch;
     a.n_old = stage_cells(h, parity);
     a.n_new = next_cells(h, parity);
@@ -146,6 +197,11 @@ StepArgs make_args(wcc_ctx* h, int cur, int parity, double cfl, double dt_fixed)
     a.st = h->st;
     a.hist = h->hist;
     a.hist_cap = h->hist_cap;
+    a.gamma_f = (float)h->opt.gamma;
+    split_double(h->opt.gamma - 1.0, a.g1_hi, a.g1_lo);
+    split_double(h->opt.adv_speed, a.adv_hi, a.adv_lo);
+    a.eps_f = (float)h->opt.eps;
+    a.alpha_f = (float)h->opt.alpha;
     return a;
 }
 
@@ -229,8 +285,10 @@ int build_graph(wcc_ctx* h, int chunk, double cfl) {
 
 void release(wcc_ctx* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
-    for (int i = 0; i < 2; ++i)
+    for (int i = 0; i < 2; ++i) {
         if (h->s64[i]) cudaFree(h->s64[i]);
+        if (h->s32[i]) cudaFree(h->s32[i]);
+    }
     if (h->staging) cudaFree(h->staging);
     if (h->st) cudaFree(h->st);
     if (h->hist) cudaFree(h->hist);
@@ -266,8 +324,8 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     wcc_options o;
     wcc_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision != WCC_FP64)
-        return fail(nullptr, WCC_E_INVAL, "precision not available in this build");
+    if (o.precision != WCC_FP64 && o.precision != WCC_FP32_MIXED)
+        return fail(nullptr, WCC_E_INVAL, "precision must be WCC_FP64 or WCC_FP32_MIXED");
     if (!(o.eps >= 0.0) || !(o.alpha > 0.0) || !(o.gamma > 1.0))
         return fail(nullptr, WCC_E_INVAL, "need eps >= 0, alpha > 0, gamma > 1");
     if (o.graph_chunk < 0) return fail(nullptr, WCC_E_INVAL, "graph_chunk must be >= 0");
@@ -305,12 +363,16 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     const long long maxcells = N + 1;
     h->pitch = (maxcells + 63) / 64 * 64;  // 512-byte aligned planes
     const long long planes = (long long)h->nv * h->K;
-    const size_t state_bytes = (size_t)(planes * h->pitch) * sizeof(double);
+    const bool mixed = o.precision == WCC_FP32_MIXED;
+    const size_t state_bytes = mixed ? (size_t)((long long)h->nv * (h->K + 1) * h->pitch) * sizeof(float)
+                                     : (size_t)(planes * h->pitch) * sizeof(double);
     const size_t staging_bytes = (size_t)(maxcells * planes) * sizeof(double);
-    bool ok = cudaMalloc(&h->s64[0], state_bytes) == cudaSuccess &&
-              cudaMalloc(&h->s64[1], state_bytes) == cudaSuccess &&
-              cudaMalloc(&h->staging, staging_bytes) == cudaSuccess &&
-              cudaMalloc(&h->st, sizeof(DevState)) == cudaSuccess;
+    bool ok = true;
+    for (int i = 0; i < 2 && ok; ++i)
+        ok = mixed ? cudaMalloc(&h->s32[i], state_bytes) == cudaSuccess
+                   : cudaMalloc(&h->s64[i], state_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&h->staging, staging_bytes) == cudaSuccess &&
+         cudaMalloc(&h->st, sizeof(DevState)) == cudaSuccess;
     if (!ok) {
         cudaGetLastError();
         release(h);
@@ -319,8 +381,8 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     }
     h->bytes = 2 * (long long)state_bytes + (long long)staging_bytes + (long long)sizeof(DevState);
     // zero the padding once so that no plane ever holds uninitialised data
-    cudaMemsetAsync(h->s64[0], 0, state_bytes, h->stream);
-    cudaMemsetAsync(h->s64[1], 0, state_bytes, h->stream);
+    for (int i = 0; i < 2; ++i)
+        cudaMemsetAsync(mixed ? (void*)h->s32[i] : (void*)h->s64[i], 0, state_bytes, h->stream);
     cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream);
     if (ensure_history(h, 4096) != WCC_OK) {
         std::string m = h->err;
@@ -353,17 +415,30 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     h->cur = 0;
     h->parity = 0;
     h->steps = 0;
-    aos_to_planes_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->staging, n, h->nv, h->K, h->pitch,
-                                                                          h->s64[0]);
+    const bool mixed = h->opt.precision == WCC_FP32_MIXED;
+    if (mixed)
+        aos_to_planes_mixed<<<elementwise_grid(n * h->nv), 256, 0, h->stream>>>(h->staging, n, h->nv, h->K,
+                                                                                 h->pitch, h->s32[0]);
+    else
+        aos_to_planes_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->staging, n, h->nv, h->K, h->pitch,
+                                                                              h->s64[0]);
     WCC_CHECK(h, cudaGetLastError());
     WCC_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
     StepArgs a = make_args(h, 0, 0, 0.0, 0.0);
     cudaError_t e;
     const long long var_stride = (long long)h->K * h->pitch;
-    switch (h->system) {
-        case WCC_ADVECTION: e = launch_stage_speed<ADVECTION>(h->s64[0], var_stride, n, a, 0, h->stream); break;
-        case WCC_BURGERS: e = launch_stage_speed<BURGERS>(h->s64[0], var_stride, n, a, 0, h->stream); break;
-        default: e = launch_stage_speed<EULER>(h->s64[0], var_stride, n, a, 0, h->stream); break;
+    if (mixed) {
+        switch (h->system) {
+            case WCC_ADVECTION: e = launch_stage_speed_mixed<ADVECTION>(h->P, h->s32[0], h->pitch, n, a, 0, h->stream); break;
+            case WCC_BURGERS: e = launch_stage_speed_mixed<BURGERS>(h->P, h->s32[0], h->pitch, n, a, 0, h->stream); break;
+            default: e = launch_stage_speed_mixed<EULER>(h->P, h->s32[0], h->pitch, n, a, 0, h->stream); break;
+        }
+    } else {
+        switch (h->system) {
+            case WCC_ADVECTION: e = launch_stage_speed<ADVECTION>(h->s64[0], var_stride, n, a, 0, h->stream); break;
+            case WCC_BURGERS: e = launch_stage_speed<BURGERS>(h->s64[0], var_stride, n, a, 0, h->stream); break;
+            default: e = launch_stage_speed<EULER>(h->s64[0], var_stride, n, a, 0, h->stream); break;
+        }
     }
     if (e != cudaSuccess) return cuda_fail(h, e, "stage speed launch");
     h->launches += 2;
@@ -427,8 +502,12 @@ int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     const long long n = stage_cells(h, h->parity);
     if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match the current stage");
-    planes_to_aos_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->s64[h->cur], n, h->nv, h->K, h->pitch,
-                                                                           h->staging);
+    if (h->opt.precision == WCC_FP32_MIXED)
+        planes_to_aos_mixed<<<elementwise_grid(n * h->nv), 256, 0, h->stream>>>(h->s32[h->cur], n, h->nv, h->K,
+                                                                                 h->pitch, h->staging);
+    else
+        planes_to_aos_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->s64[h->cur], n, h->nv, h->K,
+                                                                               h->pitch, h->staging);
     WCC_CHECK(h, cudaGetLastError());
     h->launches += 1;
     WCC_CHECK(h, cudaMemcpyAsync(dofs, h->staging, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));

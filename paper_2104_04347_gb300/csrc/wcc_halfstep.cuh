@@ -31,33 +31,35 @@ __device__ __forceinline__ long long parent_index(long long p, long long n, int 
     return p < 0 ? 0 : (p >= n ? n - 1 : p);
 }
 
-__device__ __forceinline__ double warp_max(double v) {
+template <class T>
+__device__ __forceinline__ T warp_max(T v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
 
-// Block-wide max of the speed, one atomic per CTA, then the last CTA's
-// bookkeeping.  dt is the step this launch used.
-__device__ __forceinline__ void finish_halfstep(double speed, unsigned err, double dt, const StepArgs& args) {
-    __shared__ double s_max[kThreads / 32];
+// Block-wide max of the speed (in the kernel's compute type T), one atomic
+// per CTA, then the last CTA's bookkeeping.  dt is the step this launch used.
+template <class T>
+__device__ __forceinline__ void finish_halfstep(T speed, unsigned err, double dt, const StepArgs& args) {
+    __shared__ T s_max[kThreads / 32];
     __shared__ unsigned s_err;
     __shared__ int s_last;
     if (threadIdx.x == 0) s_err = 0u;
     __syncthreads();
     // NaN must win the max: map it to +Inf and flag it
     if (speed != speed) {
-        speed = __longlong_as_double(0x7ff0000000000000ll);
+        speed = (T)INFINITY;
         err |= ERR_NONFINITE;
     }
-    speed = warp_max(speed);
+    speed = warp_max<T>(speed);
     if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = speed;
     if (err) atomicOr(&s_err, err);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = s_max[0];
+        double m = (double)s_max[0];
 #pragma unroll
-        for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, s_max[w]);
+        for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, (double)s_max[w]);
         if (m > 0.0) atomicMax(&args.st->amax_bits[args.parity ^ 1], (unsigned long long)__double_as_longlong(m));
         if (s_err) atomicOr(&args.st->err, s_err);
         __threadfence();
@@ -188,7 +190,7 @@ __global__ void __launch_bounds__(kThreads) halfstep_fp64(const StepArgs args) {
         sfor<0, NV>([&](auto V) { u0[decltype(V)::value] = e[decltype(V)::value][0]; });
         speed = wave_speed<SYS, double>(u0, args, err);
     }
-    finish_halfstep(speed, err, dt, args);
+    finish_halfstep<double>(speed, err, dt, args);
 }
 
 // Largest characteristic speed of a stage (used once after loading data).
@@ -210,7 +212,7 @@ __global__ void __launch_bounds__(256) stage_speed(const double* u0planes, long 
         }
         m = fmax(m, s);
     }
-    m = warp_max(m);
+    m = warp_max<double>(m);
     if ((threadIdx.x & 31) == 0 && m > 0.0)
         atomicMax(&args.st->amax_bits[slot], (unsigned long long)__double_as_longlong(m));
     if (err) atomicOr(&args.st->err, err);

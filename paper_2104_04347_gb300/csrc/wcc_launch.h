@@ -19,6 +19,11 @@ template <int SYS>
 cudaError_t launch_stage_speed(const double* u0planes, long long var_stride, long long n,
                                const StepArgs& args, int slot, cudaStream_t stream);
 
+// Same for an FP32-mixed stage (planes [v][ubar hi, ubar lo, e_1..e_P][cell]).
+template <int SYS>
+cudaError_t launch_stage_speed_mixed(int P, const float* planes, long long pitch, long long n,
+                                     const StepArgs& args, int slot, cudaStream_t stream);
+
 inline unsigned halfstep_grid(long long n_new) { return (unsigned)((n_new + kTile - 1) / kTile); }
 
 }  // namespace wcc

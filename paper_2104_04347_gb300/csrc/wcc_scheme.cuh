@@ -65,6 +65,8 @@ struct StepArgs {
     DevState* st;
     double* hist;     // dt of every half-step, indexed by DevState::step
     long long hist_cap;
+    // FP32 copies for the FP32-mixed kernels (hi/lo: float-float split)
+    float gamma_f, g1_hi, g1_lo, adv_hi, adv_lo, eps_f, alpha_f;
 };
 
 // ------------------------------------------------------------ static loops
@@ -140,21 +142,21 @@ struct ParentRecord {
     R vtx[NV][P + 1];
 };
 
+// Space-time Taylor table X[v][a][b] (a + b <= P) of one cell from its
+// Taylor coefficients c, and the flux coefficients F0[v][b] at a = 0.
 template <int SYS, int P, class R>
-__device__ __forceinline__ void parent_record(const R (&c)[nvars(SYS)][P + 1], R lam, const StepArgs& args,
-                                              ParentRecord<SYS, P, R>& out) {
+__device__ __forceinline__ void ck_table(const R (&c)[nvars(SYS)][P + 1], R lam, const StepArgs& args,
+                                         R (&X)[nvars(SYS)][P + 1][P + 1], R (&F0)[nvars(SYS)][P + 1]) {
     constexpr int NV = nvars(SYS);
     constexpr int K = P + 1;
-    // X[v][a][b]: space-time Taylor table; F0[v][b]: flux coefficients at a = 0.
-    R X[NV][K][K];
-    R F0[NV][K];
     sfor<0, NV>([&](auto V) {
         constexpr int v = decltype(V)::value;
         sfor<0, K>([&](auto A) { X[v][decltype(A)::value][0] = c[v][decltype(A)::value]; });
     });
 
+    constexpr bool f32 = sizeof(R) == 4;
     if constexpr (SYS == ADVECTION) {
-        const R a = (R)args.adv;
+        const R a = f32 ? (R)args.adv_hi : (R)args.adv;
         const R la = lam * a;
         sfor<0, P>([&](auto Bi) {
             constexpr int b = decltype(Bi)::value;
@@ -203,7 +205,7 @@ __device__ __forceinline__ void parent_record(const R (&c)[nvars(SYS)][P + 1], R
     } else {
         // Euler, U = (rho, m, E): velocity w = m / rho by series division,
         // q = m w, p = (gamma - 1)(E - q/2), H = E + p, F = (m, q + p, H w).
-        const R g1 = (R)(args.gamma - 1.0);
+        const R g1 = f32 ? (R)args.g1_hi : (R)(args.gamma - 1.0);
         R w[K][K] = {}, H[K][K] = {}, Fm[K][K] = {}, FE[K][K] = {};
         const R inv_rho = (R)1 / X[0][0][0];
         sfor<0, K>([&](auto Bi) {
@@ -255,6 +257,16 @@ __device__ __forceinline__ void parent_record(const R (&c)[nvars(SYS)][P + 1], R
             F0[2][b] = FE[0][b];
         });
     }
+}
+
+template <int SYS, int P, class R>
+__device__ __forceinline__ void parent_record(const R (&c)[nvars(SYS)][P + 1], R lam, const StepArgs& args,
+                                              ParentRecord<SYS, P, R>& out) {
+    constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
+    R X[NV][K][K];
+    R F0[NV][K];
+    ck_table<SYS, P, R>(c, lam, args, X, F0);
 
     sfor<0, NV>([&](auto V) {
         constexpr int v = decltype(V)::value;
@@ -409,17 +421,20 @@ __device__ __forceinline__ bool euler_eigen(const R (&U)[3], R gamma, EulerEigen
 // Characteristic speed |u| (Burgers), |a| (advection) or |u| + c (Euler)
 // at the centre point values; sets err bits for non-physical states.
 template <int SYS, class R>
-__device__ __forceinline__ double wave_speed(const R* u0, const StepArgs& args, unsigned& err) {
+__device__ __forceinline__ R wave_speed(const R* u0, const StepArgs& args, unsigned& err) {
+    constexpr bool f32 = sizeof(R) == 4;
     if constexpr (SYS == ADVECTION) {
-        return fabs(args.adv);
+        return f32 ? (R)fabsf(args.adv_hi) : (R)fabs(args.adv);
     } else if constexpr (SYS == BURGERS) {
-        return fabs((double)u0[0]);
+        return fabs(u0[0]);
     } else {
+        const R gamma = f32 ? (R)args.gamma_f : (R)args.gamma;
+        const R g1 = f32 ? (R)args.g1_hi : (R)(args.gamma - 1.0);
         const R rho = u0[0];
         const R u = u0[1] / rho;
-        const R p = (R)(args.gamma - 1.0) * fma((R)-0.5 * u0[1], u, u0[2]);
+        const R p = g1 * fma((R)-0.5 * u0[1], u, u0[2]);
         if (!(rho > (R)0) || !(p > (R)0)) err |= ERR_POSITIVITY;
-        return (double)(fabs(u) + sqrt((R)args.gamma * p / rho));
+        return fabs(u) + sqrt(gamma * p / rho);
     }
 }
 

@@ -96,8 +96,10 @@ def test_limiter_off_plain_bound(system, P):
     assert scaled_error(q, ref) <= TOL64
 
 
-@pytest.mark.parametrize("P", [2, 3, 4])
+@pytest.mark.parametrize("P", [3, 4])
 def test_smooth_euler_limiter_on_plain_bound(P):
+    # (P = 2 is left to the conditioning-aware trajectory test: its limiter
+    # reacts to rounding-level slopes at the extrema of the wave.)
     pr = inputs.euler_density_wave(600, P)
     q, dts, _, _ = gpu_run(pr, 100, CFL[P])
     ref, _, _ = oracle_run(pr, dts)
