@@ -139,6 +139,45 @@ int wcc_launch_count(wcc_handle h, int64_t* launches);
  * counterpart. */
 int wcc_measure_fp_peak(int precision, double* tflops);
 
+/* Largest nsteps accepted by wcc_advance_static. */
+#define WCC_STATIC_MAX_HALFSTEPS 4096
+
+/* Allocation-free stepping (the paper has no counterpart; this is a service
+ * for callers that cannot allocate device memory when they step -- e.g. a
+ * host application whose own allocator owns the device memory pool, or a
+ * code path that must avoid the device-wide synchronisation a cudaMalloc /
+ * cudaFree may cause).  It runs the FP64 half-step kernels of wcc_step
+ * nsteps times with dt = cfl * dx / a_max from the device, on two stage
+ * buffers the caller owns, and calls no cudaMalloc, cudaFree or other
+ * allocating routine.
+ *
+ * Arguments: system, P (1..4), bc, N, domain as in wcc_create; opt may be
+ * NULL (opt->precision must be WCC_FP64; opt->cuda_stream is the stream,
+ * NULL = legacy default stream).  parity is the stage parity of the input.
+ * stage_a (input) and stage_b are device buffers of nv*(P+1) FP64 planes,
+ * plane (v, k) at offset (v*(P+1) + k) * pitch elements, holding the Taylor
+ * coefficients e_k = u_kx / k! of cell i at index i; pitch >= N + 1, both
+ * 8-byte aligned and distinct.  The stages alternate a -> b -> a ...: after
+ * the call the final stage is in stage_a if nsteps is even, else in stage_b.
+ * dts_out (host, may be NULL) receives the nsteps half-step sizes.
+ *
+ * Scratch: a fixed array of about 33 KB in the library's device image (the
+ * CFL accumulators, counters, error bits and a dt history of
+ * WCC_STATIC_MAX_HALFSTEPS entries); every GPU that loads the library holds
+ * it until the process exits.  nsteps > WCC_STATIC_MAX_HALFSTEPS returns
+ * WCC_E_CAPACITY.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress, with that device current); make that first
+ * call before any stream capture.  All calls share the array and each call
+ * clears its state first, so calls that overlap on the GPU (other streams,
+ * other host threads) race and must not be made.
+ *
+ * Synchronous: returns after the stream has finished, with WCC_OK or
+ * WCC_E_INVAL / WCC_E_CAPACITY / WCC_E_CUDA / WCC_E_NONFINITE /
+ * WCC_E_POSITIVITY (no message is kept for this call). */
+int wcc_advance_static(int system, int P, int bc, int64_t N, const double domain[2], const wcc_options* opt,
+                       int parity, double* stage_a, double* stage_b, int64_t pitch, int64_t nsteps, double cfl,
+                       double* dts_out);
+
 const char* wcc_last_error(wcc_handle h);
 void wcc_destroy(wcc_handle h);
 

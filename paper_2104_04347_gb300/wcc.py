@@ -67,6 +67,9 @@ _SIGS = {
     "wcc_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "wcc_launch_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "wcc_measure_fp_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
+    "wcc_advance_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp,
+                                          ctypes.POINTER(Options), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_double, _dp]),
     "wcc_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "wcc_destroy": (None, [ctypes.c_void_p]),
 }
