@@ -1,5 +1,9 @@
 """Benchmark of the 1D WCC half-step on GB300.
 
+Headline: the FP32-mixed path (float-float cell averages); the FP64 path is
+timed in the same run under "variants", and "l1_vs_oracle" gives both paths'
+L1 error against the FP64 oracle on the same workload at N = 2^12.
+
 Workload (one GPU): 1D Euler, gamma = 1.4, N = 2^22 cells on [0, 1], P = 3,
 transmissive boundaries, seeded Riemann data (rho, p ~ U(0.1, 1),
 u ~ U(-0.5, 0.5) on each side of x = 0.5), limiter on, CFL nu = 0.2 (half
@@ -46,9 +50,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wcc", choices=["wcc", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--batch", type=int, default=1, help="also time the 4096-instance batch (1/0)")
     return ap.parse_args()
 
 
@@ -74,6 +79,9 @@ FP64_FLOPS_PER_CELL_UPDATE = 1284.3
 # DRAM bytes (read + write) of one FP64 launch, from the same capture
 # (201536256 + 149675008 at N = 2^21), scaled by cells to N = 2^22.
 FP64_TRAFFIC_PER_CELL = (201536256 + 149675008) / 2097152.5
+# DRAM bytes (read + write) of one FP32-mixed launch per cell; None until
+# captured for the current kernel.
+MIXED_TRAFFIC_PER_CELL = None
 # FP64 pipe peak of the GB300 (dense, nominal): 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 
@@ -189,6 +197,89 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------ GPU
 
 
+def l1_check(log2n_small=12, halfsteps=2000):
+    """L1 error (centre point values, scaled per variable) of both GPU
+    precisions against the FP64 oracle on the bench workload at a small N,
+    each replaying its own realised dt sequence."""
+    import oracle
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    oracle.set_threads(os.cpu_count() or 1)
+    pr = inputs.euler_riemann_seeded(1 << log2n_small, P)
+    law = oracle.make_law(oracle.EULER, P, limiter=True, bc=oracle.TRANSMISSIVE)
+    out = {"workload": f"euler1d-riemann-N2^{log2n_small}-P{P}, {halfsteps} half-steps, cfl {CFL}"}
+    for name, prec in (("mixed", wcc.FP32_MIXED), ("fp64", wcc.FP64)):
+        with wcc.Solver(pr.system, pr.N, P, (pr.x_l, pr.x_r), pr.bc, precision=prec) as s:
+            s.set_initial(pr.q0)
+            s.step(halfsteps, CFL)
+            q = s.get_dofs()
+            dts = s.dt_history()
+        ref = oracle.Solver(law, pr.q0, pr.dx)
+        ref.step_dt(dts)
+        scale = np.max(np.abs(ref.q[:, :, 0]), axis=0)
+        out[name] = float(np.max(np.mean(np.abs(q[:, :, 0] - ref.q[:, :, 0]), axis=0) / scale))
+    return out
+
+
+def time_solver(solver, stream, steps, warmup, barrier):
+    import torch
+    for _ in range(warmup):
+        solver.step(HALFSTEPS_PER_STEP, CFL)
+    solver.synchronize()
+    launches0 = solver.launch_count()
+    barrier()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(stream):
+        ev[0].record(stream)
+        for k in range(steps):
+            solver.step(HALFSTEPS_PER_STEP, CFL)
+            ev[k + 1].record(stream)
+    barrier()
+    solver.synchronize()
+    total_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return total_ms, step_ms, solver.launch_count() - launches0
+
+
+def batch_bench(stream, steps, warmup, p3_rate, barrier):
+    """The batched workload: 4096 independent Euler problems (N log-uniform in
+    [256, 65536], P in {2, 3}, Riemann or density-wave data), FP32-mixed, one
+    persistent launch per half-step in graphs of 32, grid picked by the
+    autotuner.  Returns the batch line and the single-grid comparison."""
+    import torch
+
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    probs = inputs.batch_workload()
+    cells = {2: 0, 3: 0}
+    per_step = 0
+    for p in probs:
+        c0 = inputs.num_cells(p.N, p.bc, 0)
+        c1 = inputs.num_cells(p.N, p.bc, 1)
+        cells[p.P] = cells.get(p.P, 0) + 0.5 * (c0 + c1)
+        per_step += (HALFSTEPS_PER_STEP // 2) * (c0 + c1)
+    with wcc.Batch(probs, graph_chunk=HALFSTEPS_PER_STEP, stream=stream.cuda_stream) as b:
+        b.set_initial()
+        ctas = b.autotune(CFL)
+        total_ms, step_ms, launches = time_solver(b, stream, steps, warmup, barrier)
+        b.synchronize()
+    value = per_step * steps / (total_ms * 1e-3)
+    # single-grid FP32-mixed rate at P = 2 on the same grid shape as the headline
+    pr = inputs.euler_riemann_seeded(1 << 22, 2)
+    with wcc.Solver(pr.system, pr.N, 2, (pr.x_l, pr.x_r), pr.bc, precision=wcc.FP32_MIXED,
+                    graph_chunk=HALFSTEPS_PER_STEP, stream=stream.cuda_stream) as s2:
+        s2.set_initial(pr.q0)
+        t2, _, _ = time_solver(s2, stream, max(2, min(steps, 5)), warmup, barrier)
+    p2_rate = (HALFSTEPS_PER_STEP // 2) * ((pr.N + 1) + pr.N) * max(2, min(steps, 5)) / (t2 * 1e-3)
+    ctot = cells[2] + cells[3]
+    single = 1.0 / ((cells[2] / ctot) / p2_rate + (cells[3] / ctot) / p3_rate)
+    return {"workload": "euler1d-batch-4096-N256..65536-P2/3-riemann/density-wave", "value": value,
+            "unit": "cell-updates/s", "ms_per_step": total_ms / steps, "steps": steps,
+            "cells_per_halfstep": per_step / HALFSTEPS_PER_STEP, "persistent_ctas": ctas,
+            "gpu_launches": launches, "single_grid_same_mix": single, "single_grid_p2": p2_rate,
+            "single_grid_p3": p3_rate, "single_over_batch": single / value}
+
+
 def run_wcc(args, rank, world):
     import torch
 
@@ -202,50 +293,72 @@ def run_wcc(args, rank, world):
         td.init_process_group("nccl", device_id=torch.device("cuda", local))
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
-    prec = wcc.FP64 if args.precision == "fp64" else wcc.FP32_MIXED
-
-    N = 1 << args.log2n
-    pr = inputs.euler_riemann_seeded(N, P)
-    solver = wcc.Solver(pr.system, N, P, (pr.x_l, pr.x_r), pr.bc, precision=prec,
-                        graph_chunk=HALFSTEPS_PER_STEP, stream=stream.cuda_stream)
-    solver.set_initial(pr.q0)
-    ncells = solver.num_cells()           # integer stage: N + 1; half stage: N
-    cells_per_step = (HALFSTEPS_PER_STEP // 2) * ((N + 1) + N)
 
     def barrier():
         if dist:
             torch.distributed.barrier()
         torch.cuda.synchronize()
 
-    for _ in range(args.warmup):
-        solver.step(HALFSTEPS_PER_STEP, CFL)
-    solver.synchronize()
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
 
-    # ---- device-resident timing
-    launches0 = solver.launch_count()
+    N = 1 << args.log2n
+    pr = inputs.euler_riemann_seeded(N, P)
+    cells_per_step = (HALFSTEPS_PER_STEP // 2) * ((N + 1) + N)
+    cells_per_launch = 0.5 * ((N + 1) + N)
+    pk, pk_kind = peaks()
+    precisions = [args.precision] + [p for p in ("mixed", "fp64") if p != args.precision]
+
     clocks = ClockSampler()
     clocks.start()
-    barrier()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    with torch.cuda.stream(stream):
-        ev[0].record(stream)
-        for k in range(args.steps):
-            solver.step(HALFSTEPS_PER_STEP, CFL)
-            ev[k + 1].record(stream)
-    barrier()
+    results = {}
+    headline_solver = None
+    for name in precisions:
+        prec = wcc.FP64 if name == "fp64" else wcc.FP32_MIXED
+        solver = wcc.Solver(pr.system, N, P, (pr.x_l, pr.x_r), pr.bc, precision=prec,
+                            graph_chunk=HALFSTEPS_PER_STEP, stream=stream.cuda_stream)
+        solver.set_initial(pr.q0)
+        steps = args.steps if name == args.precision else max(2, min(args.steps, 5))
+        total_ms, step_ms, launches = time_solver(solver, stream, steps, args.warmup, barrier)
+        total_ms = max_over_ranks(total_ms)
+        kernel_ms = statistics.median(step_ms) / HALFSTEPS_PER_STEP
+        bpc = bytes_per_cell_update(name)
+        res = {"value": world * cells_per_step * steps / (total_ms * 1e-3), "ms_per_step": total_ms / steps,
+               "steps": steps, "kernel_ms": kernel_ms, "gpu_launches": launches}
+        gbs = bpc * cells_per_launch / (kernel_ms * 1e-3) / 1e9
+        hbm = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
+               "frac": gbs / pk["hbm_gbs"], "traffic": None,
+               "peak_source": ("measured hbm_gbs (MEASURED_PEAKS.json)" if pk_kind == "measured"
+                               else "fallback 6.8 TB/s"),
+               "bytes_per_cell_update": bpc, "kernel_ms": kernel_ms}
+        if name == "fp64":
+            tf = FP64_FLOPS_PER_CELL_UPDATE * cells_per_launch / (kernel_ms * 1e-3) / 1e12
+            res["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                               "frac": tf / FP64_PEAK_TFLOPS,
+                               "traffic": FP64_TRAFFIC_PER_CELL * cells_per_launch if args.log2n == 22 else None,
+                               "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe)",
+                               "flops_per_cell_update": FP64_FLOPS_PER_CELL_UPDATE, "kernel_ms": kernel_ms,
+                               "hbm_frac": hbm["frac"]}
+        else:
+            if MIXED_TRAFFIC_PER_CELL and args.log2n == 22:
+                hbm["traffic"] = MIXED_TRAFFIC_PER_CELL * cells_per_launch
+            res["roofline"] = hbm
+        results[name] = res
+        if name == args.precision:
+            headline_solver = solver
+        else:
+            solver.close()
+    if args.batch:
+        results["batch"] = batch_bench(stream, max(2, min(args.steps, 5)), args.warmup,
+                                       results["mixed"]["value"] / world, barrier)
     clk = clocks.stop()
-    solver.synchronize()
-    launches = solver.launch_count() - launches0
-    total_ms = ev[0].elapsed_time(ev[-1])
-    step_ms = [ev[k].elapsed_time(ev[k + 1]) for k in range(args.steps)]
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * cells_per_step * args.steps / (total_ms * 1e-3)
-    kernel_ms = statistics.median(step_ms) / HALFSTEPS_PER_STEP
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers (headline precision)
+    solver = headline_solver
     count = pr.q0.size
     h_in = torch.from_numpy(pr.q0.reshape(-1).copy()).pin_memory()
     h_out = torch.empty(count, dtype=torch.float64).pin_memory()
@@ -257,59 +370,40 @@ def run_wcc(args, rank, world):
         solver.step(HALFSTEPS_PER_STEP, CFL)
         solver.get_dofs_ptr(h_out.data_ptr(), count)
     barrier()
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0)
     e2e_value = world * cells_per_step * e2e_steps / e2e_s
     assert np.all(np.isfinite(h_out.numpy()))
+    solver.close()
 
     fp64_peak_meas = wcc.measure_fp_peak(wcc.FP64)
     fp32_peak_meas = wcc.measure_fp_peak(wcc.FP32_MIXED)
-    pk, pk_kind = peaks()
-    bpc = bytes_per_cell_update(args.precision)
-    cells_per_launch = 0.5 * ((N + 1) + N)
-    if args.precision == "fp64" and FP64_FLOPS_PER_CELL_UPDATE:
-        achieved = FP64_FLOPS_PER_CELL_UPDATE * cells_per_launch / (kernel_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS,
-                "traffic": FP64_TRAFFIC_PER_CELL * cells_per_launch if args.log2n == 22 else None,
-                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe); FMA-chain measurement alongside",
-                "flops_per_cell_update": FP64_FLOPS_PER_CELL_UPDATE}
-    else:
-        achieved = bpc * cells_per_launch / (kernel_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / pk["hbm_gbs"], "traffic": None,
-                "peak_source": f"{pk_kind} hbm_gbs (MEASURED_PEAKS.json)" if pk_kind == "measured"
-                else "fallback 6.8 TB/s"}
-    roof["kernel_ms"] = kernel_ms
+    head = results[args.precision]
+    roof = dict(head["roofline"])
     roof["fp64_fma_peak_measured_tflops"] = fp64_peak_meas
     roof["fp32_fma_peak_measured_tflops"] = fp32_peak_meas
-    roof["bytes_per_cell_update"] = bpc
-
     line = {
-        "metric": METRIC, "value": value, "unit": "cell-updates/s", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "metric": METRIC, "value": head["value"], "unit": "cell-updates/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.precision == "fp64" else "f32+f64",
+        "dtype": "f64" if args.precision == "fp64" else "f32",
         "data": "synthetic (seeded Riemann initial data, splitmix64 seed 2104043471)",
         "config": {"workload": workload_name(args.log2n), "N": N, "P": P, "cells_integer_stage": N + 1,
                    "precision": args.precision, "halfsteps_per_step": HALFSTEPS_PER_STEP, "cfl": CFL,
-                   "limiter": True, "l2": "state > L2 (no flush needed)",
+                   "limiter": True, "l2": "state > L2 (252 / 403 MB per stage), no flush needed",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
         "e2e": {"value": e2e_value, "unit": "cell-updates/s",
                 "h2d_bytes_per_step": int(count * 8), "d2h_bytes_per_step": int(count * 8),
-                "steps": e2e_steps},
-        "gpu_launches": launches,
+                "steps": e2e_steps, "precision": args.precision},
+        "gpu_launches": head["gpu_launches"],
         "clocks": clk,
+        "variants": {k: v for k, v in results.items() if k != args.precision},
     }
     if rank == 0 and world == 1:
+        line["l1_vs_oracle"] = l1_check()
         rate, cores, sample = cpu_oracle_rate(args.log2n, args.cpu_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                                 "sample": sample}
-    solver.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

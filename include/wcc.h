@@ -132,6 +132,50 @@ int wcc_device_bytes(wcc_handle h, int64_t* bytes);
  * since wcc_create. */
 int wcc_launch_count(wcc_handle h, int64_t* launches);
 
+/* ------------------------------------------------------------------ batches
+ * Many independent problems of one conservation law, advanced together: one
+ * persistent kernel launch per half-step walks the tiles of every instance
+ * (cells are flattened across instances, so instances of very different N
+ * share the GPU evenly).  Each instance keeps its own N, P, domain, boundary,
+ * time and dt = cfl * dx_i / a_max,i (the scheme of Sec. 2 applied to each
+ * problem independently).  Batches run in WCC_FP32_MIXED precision only and
+ * hold at most two different degrees P.
+ *
+ * Host layout of a batch: the instances one after another in the user's
+ * order, each as in wcc_set_initial ([cell][var][k] of u_kx, cells of its
+ * current stage: N_i (periodic) or N_i + 1 / N_i (transmissive, integer /
+ * half stage)).  wcc_batch_dof_count gives the total number of doubles. */
+typedef struct wcc_batch_ctx* wcc_batch;
+
+/* count instances; N[count], P[count] (1..4, at most two distinct values),
+ * domains[2*count] (x_L, x_R per instance), bcs[count]; opt may be NULL but
+ * opt->precision must be WCC_FP32_MIXED when given. */
+int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N, const int* P,
+                     const double* domains, const int* bcs, const wcc_options* opt);
+int wcc_batch_dof_count(wcc_batch b, int64_t* count);
+/* Load integer stages of all instances (t = 0); synchronous. */
+int wcc_batch_set_initial(wcc_batch b, const double* dofs, int64_t count);
+/* nsteps half-steps of every instance, each with its own CFL dt; asynchronous. */
+int wcc_batch_step(wcc_batch b, int64_t nsteps, double cfl);
+int wcc_batch_get_dofs(wcc_batch b, double* dofs, int64_t count);
+/* t[count]: the time of every instance (user order). */
+int wcc_batch_get_times(wcc_batch b, double* t, int64_t count);
+int wcc_batch_get_state(wcc_batch b, int64_t* half_steps, int* parity);
+/* Half-step sizes of one instance (user index), as wcc_get_dt_history. */
+int wcc_batch_get_dt_history(wcc_batch b, int64_t instance, double* dts, int64_t cap, int64_t* n);
+/* Persistent grid of the step kernel in CTAs (0: all resident CTAs). */
+int wcc_batch_set_grid(wcc_batch b, int ctas);
+/* Time the candidate grids (1..max resident CTAs per SM, and one CTA per
+ * tile) over a few half-steps of this batch with this CFL number, keep the
+ * fastest, and restore the batch state; *ctas (may be NULL) receives it.
+ * Allocates a temporary copy of the current stage.  Synchronous. */
+int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas);
+int wcc_batch_synchronize(wcc_batch b);
+int wcc_batch_launch_count(wcc_batch b, int64_t* launches);
+int wcc_batch_device_bytes(wcc_batch b, int64_t* bytes);
+const char* wcc_batch_last_error(wcc_batch b);
+void wcc_batch_destroy(wcc_batch b);
+
 /* Measured fused-multiply-add throughput of the current device in TFLOP/s
  * (FP64 for WCC_FP64, FP32 for WCC_FP32_MIXED): a grid of 8 CTAs per SM,
  * 8 independent FMA chains per thread, timed with CUDA events (~40 ms).

@@ -189,7 +189,11 @@ StepArgs make_args(wcc_ctx* h, int cur, int parity, double cfl, double dt_fixed)
     a.alpha_is_two = (h->opt.alpha == 2.0);
     a.dx = h->dx;
     a.cfl = cfl;
+    a.cfl_mode = cfl > 0.0 ? 1 : 0;
+    a.cfl_bits = (unsigned long long)__double_as_longlong_host(cfl);
     a.dt_fixed = dt_fixed;
+    a.lam_fixed = dt_fixed / h->dx;
+    split_double(a.lam_fixed, a.lam_fixed_hi, a.lam_fixed_lo);
     a.adv = h->opt.adv_speed;
     a.gamma = h->opt.gamma;
     a.alpha = h->opt.alpha;

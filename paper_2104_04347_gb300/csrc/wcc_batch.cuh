@@ -1,0 +1,169 @@
+// wcc_batch.cuh -- many independent 1D problems advanced by one persistent
+// launch per half-step (FP32-mixed).
+//
+// The instances of a batch share the conservation law and the options; each
+// has its own N, P, domain, boundary and dt (from its own CFL bound).  Cells
+// are flattened, not instances: every instance is cut into tiles of kTile new
+// cells, the tiles of all instances form one list (prefix table
+// tile_start), and a persistent grid walks the list.  A launch covers two
+// groups of instances, P = PA and P = PB (a batch holds at most two degrees);
+// each group keeps its stages in its own plane buffers with instance
+// offsets.  The tile code is the single-grid kernel's (mixed_tile), so an
+// instance of a batch evolves exactly like the same problem run alone.
+#pragma once
+
+#include "wcc_halfstep_mixed.cuh"
+
+namespace wcc {
+
+struct BatchInstance {
+    long long offset;     // first cell of the instance in its group's planes
+    long long aos_offset[2];  // first double of the instance in the host-layout array of a stage of parity 0 / 1
+    long long cells[2];   // cells of an integer (0) / half (1) stage
+    double dx;
+    int bc;
+    int group;            // 0: P = PA, 1: P = PB
+};
+
+struct BatchArgs {
+    StepArgs phys;                 // physics and options (per-launch fields unused)
+    const BatchInstance* inst;
+    DevState* st;                  // one per instance
+    double* hist;                  // hist[i * hist_cap + step]
+    long long hist_cap;
+    const float* in[2];            // current stage planes of group 0 / 1
+    float* out[2];                 // next stage planes
+    long long pitch[2];
+    const long long* tile_start;   // [ninst + 1] exclusive prefix of tiles per instance
+    long long total_tiles;
+    int ninst;
+    int parity;
+};
+
+// Index i with tile_start[i] <= tile < tile_start[i + 1].
+__device__ __forceinline__ int tile_instance(const long long* tile_start, int n, long long tile) {
+    int lo = 0, hi = n;  // invariant: tile_start[lo] <= tile < tile_start[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (__ldg(tile_start + mid) <= tile) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+template <int SYS, int PA, int PB>
+__global__ void __launch_bounds__(kThreads) batch_mixed(const BatchArgs b) {
+    constexpr int SA = mixed_tile_smem_floats<SYS, PA>();
+    constexpr int SB = mixed_tile_smem_floats<SYS, PB>();
+    __shared__ float rec[SA > SB ? SA : SB];
+    __shared__ int s_inst;
+    for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
+        if (threadIdx.x == 0) s_inst = tile_instance(b.tile_start, b.ninst, tile);
+        __syncthreads();  // also orders the previous tile's last use of rec
+        const int i = s_inst;
+        const BatchInstance I = b.inst[i];
+        DevState* st = b.st + i;
+        const long long first = __ldg(b.tile_start + i);
+        const long long ntiles = __ldg(b.tile_start + i + 1) - first;
+        const StepSize z = cfl_step_size(st, b.phys.cfl_bits, b.phys.cfl, I.dx, b.parity);
+        const int g = I.group;
+        const TileIO io{b.in[g] + I.offset, b.out[g] + I.offset, b.pitch[g], I.cells[b.parity],
+                        I.cells[b.parity ^ 1], (tile - first) * kTile, b.parity, I.bc};
+        float speed = 0.f;
+        unsigned err = 0u;
+        StepArgs ph = b.phys;  // per-instance boundary and mesh width
+        ph.bc = I.bc;
+        ph.dx = I.dx;
+        if (g == 0)
+            mixed_tile<SYS, PA>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
+        else
+            mixed_tile<SYS, PB>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
+        reduce_and_finish<float>(speed, err, z.dt, st, ntiles, b.hist + (long long)i * b.hist_cap, b.hist_cap,
+                                 b.parity, 1, b.phys.cfl, I.dx);
+    }
+}
+
+// Largest characteristic speed of every instance's current stage (after
+// loading data): one thread per cell of the tiles in tile_start (tiles of
+// the current stage), into st[i].amax_bits[parity].
+template <int SYS, int PA, int PB>
+__global__ void __launch_bounds__(kThreads) batch_stage_speed(const BatchArgs b) {
+    for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
+        const int i = tile_instance(b.tile_start, b.ninst, tile);
+        const BatchInstance I = b.inst[i];
+        const long long c = (tile - b.tile_start[i]) * kTile + threadIdx.x;
+        float s = 0.f;
+        unsigned err = 0u;
+        if (threadIdx.x < kTile && c < I.cells[b.parity]) {
+            const int P = I.group == 0 ? PA : PB;
+            const int NP = P + 2;
+            const float* pl = b.in[I.group] + I.offset;
+            const long long pitch = b.pitch[I.group];
+            float u0[nvars(SYS)];
+#pragma unroll
+            for (int v = 0; v < nvars(SYS); ++v) {
+                float corr = 0.f;
+                for (int k = 2; k <= P; k += 2)
+                    corr += pl[(long long)(v * NP + k + 1) * pitch + c] / (float)((k + 1) * (1 << k));
+                u0[v] = (pl[(long long)(v * NP) * pitch + c] + pl[(long long)(v * NP + 1) * pitch + c]) - corr;
+            }
+            StepArgs ph = b.phys;
+            s = wave_speed<SYS, float>(u0, ph, err);
+            if (s != s) {
+                s = INFINITY;
+                err |= ERR_NONFINITE;
+            }
+        }
+        s = warp_max<float>(s);
+        if ((threadIdx.x & 31) == 0 && s > 0.f) {
+            const unsigned long long bits = (unsigned long long)__double_as_longlong((double)s);
+            atomicMax(&b.st[i].amax_bits[b.parity], bits);
+        }
+        if (err) atomicOr(&b.st[i].err, err);
+    }
+}
+
+// Host layout (per instance [cell][var][k] of u_kx, instances back to back in
+// the order of the instance table) <-> group planes, one thread per cell.
+template <int SYS, int PA, int PB>
+__global__ void __launch_bounds__(kThreads) batch_convert(const BatchArgs b, double* aos, int to_planes) {
+    for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
+        const int i = tile_instance(b.tile_start, b.ninst, tile);
+        const BatchInstance I = b.inst[i];
+        const long long c = (tile - b.tile_start[i]) * kTile + threadIdx.x;
+        if (threadIdx.x >= kTile || c >= I.cells[b.parity]) continue;
+        const int P = I.group == 0 ? PA : PB;
+        const int K = P + 1, NP = P + 2, NV = nvars(SYS);
+        float* pl = (to_planes ? b.out[I.group] : const_cast<float*>(b.in[I.group])) + I.offset;
+        const long long pitch = b.pitch[I.group];
+        double* q0 = aos + I.aos_offset[b.parity] + c * NV * K;
+        for (int v = 0; v < NV; ++v) {
+            double* q = q0 + v * K;
+            if (to_planes) {
+                double ubar = 0.0, fact = 1.0, p2 = 1.0;
+                for (int k = 0; k < K; ++k) {
+                    if (k > 1) fact *= (double)k;
+                    if ((k & 1) == 0) ubar += q[k] / (fact * (double)(k + 1) * p2);
+                    if (k >= 1) pl[(long long)(v * NP + k + 1) * pitch + c] = (float)(q[k] / fact);
+                    p2 *= 2.0;
+                }
+                float hi, lo;
+                split_double(ubar, hi, lo);
+                pl[(long long)(v * NP) * pitch + c] = hi;
+                pl[(long long)(v * NP + 1) * pitch + c] = lo;
+            } else {
+                double u0 = (double)pl[(long long)(v * NP) * pitch + c] + (double)pl[(long long)(v * NP + 1) * pitch + c];
+                double fact = 1.0, p2 = 2.0;
+                for (int k = 1; k < K; ++k) {
+                    fact *= (double)k;
+                    p2 *= 2.0;
+                    const double ek = (double)pl[(long long)(v * NP + k + 1) * pitch + c];
+                    if ((k & 1) == 0) u0 -= ek / ((double)(k + 1) * (p2 / 2.0));
+                    q[k] = ek * fact;
+                }
+                q[0] = u0;
+            }
+        }
+    }
+}
+
+}  // namespace wcc

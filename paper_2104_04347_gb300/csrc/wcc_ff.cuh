@@ -72,12 +72,22 @@ __device__ __forceinline__ ff ff_mul(ff a, float b) {
     return fast_two_sum(p.hi, e);
 }
 
-// a / b: one float quotient, its remainder in float-float, one correction.
+// a / b: an approximate float quotient q1, its remainder a - q1 b in
+// float-float, and one correction q2 = remainder / b.hi; the remainder is
+// formed exactly enough that the result keeps ~44 bits even though both
+// quotients use the fast (2 ulp) division.
 __device__ __forceinline__ ff ff_div(ff a, ff b) {
-    const float q1 = __fdiv_rn(a.hi, b.hi);
+    const float q1 = __fdividef(a.hi, b.hi);
     const ff r = ff_sub(a, ff_mul(b, q1));
-    const float q2 = __fdiv_rn(r.hi, b.hi);
+    const float q2 = __fdividef(r.hi, b.hi);
     return fast_two_sum(q1, q2);
+}
+
+// (a - b) rounded to float, for a, b close to each other: the hi parts
+// subtract exactly when they are within a factor of two (Sterbenz), so the
+// difference keeps full FP32 accuracy relative to itself.
+__device__ __forceinline__ float ff_diff(ff a, ff b) {
+    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
 }
 
 // Split a double into a float-float (host or device).

@@ -38,10 +38,47 @@ __device__ __forceinline__ T warp_max(T v) {
     return v;
 }
 
+// Bookkeeping of a solver state after the last CTA of a half-step finished:
+// publish the new stage's bound, clear the slots the next launches
+// accumulate into, record dt, advance t and prepare the next CFL step.
+// FP32 kernels (f32) accumulate the bound in amax_f32.
+__device__ __forceinline__ void finalize_state(DevState* st, bool f32, double dt, double* hist, long long hist_cap,
+                                               int parity, int cfl_mode, double cfl, double dx) {
+    if (f32) {
+        const float fm = __uint_as_float(st->amax_f32[parity ^ 1]);
+        st->amax_bits[parity ^ 1] = (unsigned long long)__double_as_longlong((double)fm);
+        st->amax_f32[parity] = 0u;
+    }
+    // Every CTA of this launch has read amax_bits[parity]; clear it for the
+    // launch after next, which accumulates into it.
+    st->amax_bits[parity] = 0ull;
+    const long long k = st->step;
+    if (k < hist_cap) hist[k] = dt;
+    st->step = k + 1;
+    st->t = st->t + dt;
+    st->blocks_done = 0u;
+    if (not_finite(dt)) st->err |= ERR_NONFINITE;
+    if (cfl_mode) {
+        const double amax = __longlong_as_double((long long)st->amax_bits[parity ^ 1]);
+        const double ndt = cfl * dx / amax;
+        const double nlam = ndt / dx;
+        st->next_dt = ndt;
+        st->next_lam = nlam;
+        split_to_floats(nlam, st->next_lam_hi, st->next_lam_lo);
+        st->next_cfl = cfl;
+    } else {
+        st->next_cfl = 0.0;
+    }
+    __threadfence();
+}
+
 // Block-wide max of the speed (in the kernel's compute type T), one atomic
-// per CTA, then the last CTA's bookkeeping.  dt is the step this launch used.
+// per CTA into st, then count the CTA as done; the CTA that completes the
+// `ctas` of this state does its bookkeeping.  Synchronises the block.
 template <class T>
-__device__ __forceinline__ void finish_halfstep(T speed, unsigned err, double dt, const StepArgs& args) {
+__device__ __forceinline__ void reduce_and_finish(T speed, unsigned err, double dt, DevState* st, long long ctas,
+                                                  double* hist, long long hist_cap, int parity, int cfl_mode,
+                                                  double cfl, double dx) {
     __shared__ T s_max[kThreads / 32];
     __shared__ unsigned s_err;
     __shared__ int s_last;
@@ -57,30 +94,30 @@ __device__ __forceinline__ void finish_halfstep(T speed, unsigned err, double dt
     if (err) atomicOr(&s_err, err);
     __syncthreads();
     if (threadIdx.x == 0) {
-        double m = (double)s_max[0];
+        T m = s_max[0];
 #pragma unroll
-        for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, (double)s_max[w]);
-        if (m > 0.0) atomicMax(&args.st->amax_bits[args.parity ^ 1], (unsigned long long)__double_as_longlong(m));
-        if (s_err) atomicOr(&args.st->err, s_err);
+        for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, s_max[w]);
+        if constexpr (sizeof(T) == 8) {
+            if (m > 0.0) atomicMax(&st->amax_bits[parity ^ 1], (unsigned long long)__double_as_longlong(m));
+        } else {
+            if (m > 0.f) atomicMax(&st->amax_f32[parity ^ 1], __float_as_uint(m));
+        }
+        if (s_err) atomicOr(&st->err, s_err);
         __threadfence();
-        const unsigned done = atomicAdd(&args.st->blocks_done, 1u);
-        s_last = (done == gridDim.x - 1);
+        const unsigned done = atomicAdd(&st->blocks_done, 1u);
+        s_last = (done == (unsigned)(ctas - 1));
     }
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
         __threadfence();
-        DevState* st = args.st;
-        // Every CTA of this launch has read amax_bits[parity]; clear it for
-        // the launch after next, which accumulates into it.
-        st->amax_bits[args.parity] = 0ull;
-        const long long k = st->step;
-        if (k < args.hist_cap) args.hist[k] = dt;
-        st->step = k + 1;
-        st->t = st->t + dt;
-        st->blocks_done = 0u;
-        if (not_finite(dt)) st->err |= ERR_NONFINITE;
-        __threadfence();
+        finalize_state(st, sizeof(T) == 4, dt, hist, hist_cap, parity, cfl_mode, cfl, dx);
     }
+}
+
+template <class T>
+__device__ __forceinline__ void finish_halfstep(T speed, unsigned err, double dt, const StepArgs& args) {
+    reduce_and_finish<T>(speed, err, dt, args.st, (long long)gridDim.x, args.hist, args.hist_cap, args.parity,
+                         args.cfl_mode, args.cfl, args.dx);
 }
 
 template <int SYS, int P>
@@ -93,14 +130,9 @@ __global__ void __launch_bounds__(kThreads) halfstep_fp64(const StepArgs args) {
     const int t = threadIdx.x;
     const long long first_new = (long long)blockIdx.x * kTile;
 
-    double dt;
-    if (args.cfl > 0.0) {
-        const double amax = __longlong_as_double((long long)args.st->amax_bits[args.parity]);
-        dt = args.cfl * args.dx / amax;
-    } else {
-        dt = args.dt_fixed;
-    }
-    const double lam = dt / args.dx;
+    const StepSize z = step_size(args);
+    const double dt = z.dt;
+    const double lam = z.lam;
 
     // ---- phase 1: parent record of parent slot t
     {

@@ -145,44 +145,52 @@ __device__ __forceinline__ void flux_ff(const ff (&u)[nvars(SYS)], const StepArg
     }
 }
 
+// Shared-memory floats one tile of mixed_tile<SYS, P> needs.
+// Where one tile reads and writes (one stage of one grid or batch instance).
+struct TileIO {
+    const float* in32;
+    float* out32;
+    long long pitch;
+    long long n_old;
+    long long n_new;
+    long long first_new;
+    int parity;
+    int bc;
+};
+
 template <int SYS, int P>
-__global__ void __launch_bounds__(kThreads) halfstep_mixed(const StepArgs args) {
+constexpr int mixed_tile_smem_floats() {
+    return nvars(SYS) * (6 + P) * kThreads;
+}
+
+// One tile of the FP32-mixed half-step: parents io.first_new + t - parity
+// (t = 0..kThreads-1) of the stage io.in32, new cells io.first_new + t
+// (t < kTile) of io.out32.  rec: mixed_tile_smem_floats<SYS, P>() floats of
+// shared memory.  Returns each thread's characteristic speed (0 for threads
+// without a new cell) and error bits.  The caller synchronises the block
+// before rec is written again.
+template <int SYS, int P>
+__device__ __forceinline__ void mixed_tile(const TileIO& io, const ff lam, const StepArgs& args, float* rec,
+                                           float& speed, unsigned& err) {
     constexpr int NV = nvars(SYS);
     constexpr int K = P + 1;
     constexpr int NP = P + 2;       // planes per variable: ubar hi, ubar lo, e_1..e_P
     constexpr int RV = 6 + P;       // record per variable: A(2), B(2), v0(2), vtx_1..vtx_P
-    __shared__ float rec[NV * RV][kThreads];
-    __shared__ double s_dt;
-    __shared__ float s_lam[2];
-
     const int t = threadIdx.x;
-    const long long first_new = (long long)blockIdx.x * kTile;
-    if (t == 0) {
-        double dt;
-        if (args.cfl > 0.0) {
-            const double amax = __longlong_as_double((long long)args.st->amax_bits[args.parity]);
-            dt = args.cfl * args.dx / amax;
-        } else {
-            dt = args.dt_fixed;
-        }
-        s_dt = dt;
-        split_double(dt / args.dx, s_lam[0], s_lam[1]);
-    }
-    __syncthreads();
-    const ff lam = ff_make(s_lam[0], s_lam[1]);
+    const long long first_new = io.first_new;
 
     // ---- phase 1: parent record of parent slot t
     {
-        const long long p = parent_index(first_new + t - (args.parity ? 1 : 0), args.n_old, args.bc);
+        const long long p = parent_index(first_new + t - (io.parity ? 1 : 0), io.n_old, io.bc);
         float c[NV][K];
         ff ub[NV], u0[NV];
         sfor<0, NV>([&](auto V) {
             constexpr int v = decltype(V)::value;
-            ub[v].hi = __ldg(args.in32 + (long long)(v * NP + 0) * args.pitch + p);
-            ub[v].lo = __ldg(args.in32 + (long long)(v * NP + 1) * args.pitch + p);
+            ub[v].hi = __ldg(io.in32 + (long long)(v * NP + 0) * io.pitch + p);
+            ub[v].lo = __ldg(io.in32 + (long long)(v * NP + 1) * io.pitch + p);
             sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
-                c[v][k] = __ldg(args.in32 + (long long)(v * NP + k + 1) * args.pitch + p);
+                c[v][k] = __ldg(io.in32 + (long long)(v * NP + k + 1) * io.pitch + p);
             });
             // point value u_0 = ubar - sum_{k even >= 2} e_k / ((k+1) 2^k)  (Eq. 1DCalU)
             float corr = 0.f;
@@ -221,7 +229,7 @@ __global__ void __launch_bounds__(kThreads) halfstep_mixed(const StepArgs args) 
             float vt0 = 0.f;
             sfor<1, K>([&](auto Mi) { vt0 += X[v][0][decltype(Mi)::value]; });
             const ff v0 = ff_add(u0[v], vt0);
-            float* r = &rec[v * RV][0];
+            float* r = rec + v * RV * kThreads;
             r[0 * kThreads + t] = A.hi;
             r[1 * kThreads + t] = A.lo;
             r[2 * kThreads + t] = B.hi;
@@ -240,24 +248,23 @@ __global__ void __launch_bounds__(kThreads) halfstep_mixed(const StepArgs args) 
 
     // ---- phase 2: new cell t from parent slots t (left) and t + 1 (right)
     const long long i = first_new + t;
-    float speed = 0.f;
-    unsigned err = 0u;
-    if (t < kTile && i < args.n_new) {
+    speed = 0.f;
+    if (t < kTile && i < io.n_new) {
         ff ubn[NV];
         float d[NV][K], dl[NV], dr[NV];
         sfor<0, NV>([&](auto V) {
             constexpr int v = decltype(V)::value;
-            const float* r = &rec[v * RV][0];
+            const float* r = rec + v * RV * kThreads;
             const ff A = ff_make(r[0 * kThreads + t], r[1 * kThreads + t]);
             const ff B = ff_make(r[2 * kThreads + t + 1], r[3 * kThreads + t + 1]);
             const ff vL0 = ff_make(r[4 * kThreads + t], r[5 * kThreads + t]);
             const ff vR0 = ff_make(r[4 * kThreads + t + 1], r[5 * kThreads + t + 1]);
             ubn[v] = ff_add(A, B);                          // Eq. SubEq:1DIntegral
-            dl[v] = ff_sub(ubn[v], vL0).hi;
-            dr[v] = ff_sub(vR0, ubn[v]).hi;
+            dl[v] = ff_diff(ubn[v], vL0);
+            dr[v] = ff_diff(vR0, ubn[v]);
             float vL[K], vR[K];
             vL[0] = 0.f;
-            vR[0] = ff_sub(vR0, vL0).hi;
+            vR[0] = ff_diff(vR0, vL0);
             sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
                 vL[k] = r[(5 + k) * kThreads + t];
@@ -296,25 +303,37 @@ __global__ void __launch_bounds__(kThreads) halfstep_mixed(const StepArgs args) 
             }
         }
 
-        bool bad = false;
         float u0[NV];
+        float check = 0.f;   // NaN / Inf in any stored value reaches this sum
         sfor<0, NV>([&](auto V) {
             constexpr int v = decltype(V)::value;
-            bad |= not_finite(ubn[v].hi);
-            __stcs(args.out32 + (long long)(v * NP + 0) * args.pitch + i, ubn[v].hi);
-            __stcs(args.out32 + (long long)(v * NP + 1) * args.pitch + i, ubn[v].lo);
+            check += ubn[v].hi;
+            __stcs(io.out32 + (long long)(v * NP + 0) * io.pitch + i, ubn[v].hi);
+            __stcs(io.out32 + (long long)(v * NP + 1) * io.pitch + i, ubn[v].lo);
             sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
-                bad |= not_finite(d[v][k]);
-                __stcs(args.out32 + (long long)(v * NP + k + 1) * args.pitch + i, d[v][k]);
+                check += d[v][k];
+                __stcs(io.out32 + (long long)(v * NP + k + 1) * io.pitch + i, d[v][k]);
             });
             u0[v] = ubn[v].hi + d[v][0];
         });
-        if (bad) err |= ERR_NONFINITE;
+        if (not_finite(check)) err |= ERR_NONFINITE;
         speed = wave_speed<SYS, float>(u0, args, err);
     }
-    finish_halfstep<float>(speed, err, s_dt, args);
 }
+
+template <int SYS, int P>
+__global__ void __launch_bounds__(kThreads) halfstep_mixed(const StepArgs args) {
+    __shared__ float rec[mixed_tile_smem_floats<SYS, P>()];
+    const StepSize z = step_size(args);
+    const TileIO io{args.in32, args.out32, args.pitch, args.n_old, args.n_new,
+                    (long long)blockIdx.x * kTile, args.parity, args.bc};
+    float speed = 0.f;
+    unsigned err = 0u;
+    mixed_tile<SYS, P>(io, ff_make(z.lam_hi, z.lam_lo), args, rec, speed, err);
+    finish_halfstep<float>(speed, err, z.dt, args);
+}
+
 
 // Largest characteristic speed of a stored FP32-mixed stage.
 template <int SYS, int P>

@@ -24,6 +24,20 @@ template <int SYS>
 cudaError_t launch_stage_speed_mixed(int P, const float* planes, long long pitch, long long n,
                                      const StepArgs& args, int slot, cudaStream_t stream);
 
+struct BatchArgs;
+enum { BATCH_STEP = 0, BATCH_SPEED = 1, BATCH_CONVERT = 2 };
+
+// Batched launches (wcc_batch.cuh) for groups of degree PA <= PB: one
+// half-step (BATCH_STEP), the stage bound after loading (BATCH_SPEED), or the
+// layout conversion (BATCH_CONVERT, to_planes = 1: host layout -> planes).
+template <int SYS>
+cudaError_t launch_batch(int PA, int PB, int kind, const BatchArgs& b, double* aos, int to_planes, unsigned grid,
+                         cudaStream_t stream);
+
+// Resident CTAs per SM of the batched half-step kernel.
+template <int SYS>
+int batch_blocks_per_sm(int PA, int PB);
+
 inline unsigned halfstep_grid(long long n_new) { return (unsigned)((n_new + kTile - 1) / kTile); }
 
 }  // namespace wcc

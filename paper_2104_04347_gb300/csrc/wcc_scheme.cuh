@@ -33,10 +33,21 @@ struct DevState {
     // amax_bits[s]: largest characteristic speed of the stage with parity s,
     // as the bit pattern of a non-negative double (integer max == double max).
     unsigned long long amax_bits[2];
+    // the same bound as FP32 bits, accumulated by the FP32-mixed kernels (an
+    // integer max on the bits of non-negative floats); the last CTA of a
+    // launch converts it into amax_bits.
+    unsigned int amax_f32[2];
     double t;
     long long step;
     unsigned int blocks_done;  // CTAs finished in the running half-step
     unsigned int err;          // ERR_* bits, sticky
+    // dt and lam = dt/dx of the next launch, prepared once by the last CTA of
+    // the current launch for the CFL number next_cfl (a launch with another
+    // CFL number, or the first one after loading data, derives them itself).
+    double next_cfl;
+    double next_dt;
+    double next_lam;
+    float next_lam_hi, next_lam_lo;
 };
 
 // Arguments of one half-step launch.  Plane (v, k) of a stage holds the
@@ -56,8 +67,12 @@ struct StepArgs {
     int limiter;
     int alpha_is_two;
     double dx;
+    int cfl_mode;     // 1: dt from the CFL number (cfl > 0); 0: dt_fixed
+    int pad_;
+    unsigned long long cfl_bits;  // bit pattern of cfl (integer comparison, no FP64 pipe)
     double cfl;       // > 0: dt = cfl dx / amax of the stage being advanced
-    double dt_fixed;  // used when cfl <= 0
+    double dt_fixed;  // used when cfl <= 0, with lam_fixed = dt_fixed / dx
+    double lam_fixed;
     double adv;       // advection speed
     double gamma;
     double alpha;
@@ -67,7 +82,51 @@ struct StepArgs {
     long long hist_cap;
     // FP32 copies for the FP32-mixed kernels (hi/lo: float-float split)
     float gamma_f, g1_hi, g1_lo, adv_hi, adv_lo, eps_f, alpha_f;
+    float lam_fixed_hi, lam_fixed_lo;
 };
+
+// dt and lam of this launch (the same values in every thread).
+struct StepSize {
+    double dt, lam;
+    float lam_hi, lam_lo;
+};
+
+__device__ __forceinline__ void split_to_floats(double d, float& hi, float& lo) {
+    hi = (float)d;
+    lo = (float)(d - (double)hi);
+}
+
+// CFL step of a solver state: the value the previous launch prepared when it
+// was made for the same CFL number, else derived from the stage bound.
+__device__ __forceinline__ StepSize cfl_step_size(const DevState* st, unsigned long long cfl_bits, double cfl,
+                                                  double dx, int parity) {
+    StepSize z;
+    if ((unsigned long long)__double_as_longlong(st->next_cfl) == cfl_bits) {
+        z.dt = st->next_dt;
+        z.lam = st->next_lam;
+        z.lam_hi = st->next_lam_hi;
+        z.lam_lo = st->next_lam_lo;
+    } else {
+        const double amax = __longlong_as_double((long long)st->amax_bits[parity]);
+        z.dt = cfl * dx / amax;
+        z.lam = z.dt / dx;
+        split_to_floats(z.lam, z.lam_hi, z.lam_lo);
+    }
+    return z;
+}
+
+__device__ __forceinline__ StepSize step_size(const StepArgs& args) {
+    StepSize z;
+    if (args.cfl_mode) {
+        z = cfl_step_size(args.st, args.cfl_bits, args.cfl, args.dx, args.parity);
+    } else {
+        z.dt = args.dt_fixed;
+        z.lam = args.lam_fixed;
+        z.lam_hi = args.lam_fixed_hi;
+        z.lam_lo = args.lam_fixed_lo;
+    }
+    return z;
+}
 
 // ------------------------------------------------------------ static loops
 
@@ -116,6 +175,18 @@ __host__ __device__ constexpr double csmooth(int j, int l) {
 }
 
 __host__ __device__ constexpr int nvars(int sys) { return sys == EULER ? 3 : 1; }
+
+// Bit pattern of a double on the host.
+inline long long __double_as_longlong_host(double d) {
+    long long b;
+    __builtin_memcpy(&b, &d, sizeof(b));
+    return b;
+}
+
+// 1/x: correctly rounded division in FP64; the hardware reciprocal with one
+// Newton step (correctly rounded) in FP32.
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
 
 // NaN / Inf test on the exponent bits (integer pipe only).
 __device__ __forceinline__ bool not_finite(double x) {
@@ -207,7 +278,7 @@ __device__ __forceinline__ void ck_table(const R (&c)[nvars(SYS)][P + 1], R lam,
         // q = m w, p = (gamma - 1)(E - q/2), H = E + p, F = (m, q + p, H w).
         const R g1 = f32 ? (R)args.g1_hi : (R)(args.gamma - 1.0);
         R w[K][K] = {}, H[K][K] = {}, Fm[K][K] = {}, FE[K][K] = {};
-        const R inv_rho = (R)1 / X[0][0][0];
+        const R inv_rho = recip(X[0][0][0]);
         sfor<0, K>([&](auto Bi) {
             constexpr int b = decltype(Bi)::value;
             sfor<0, K - b>([&](auto Ai) {
@@ -396,17 +467,25 @@ struct EulerEigen {
 
 template <class R>
 __device__ __forceinline__ bool euler_eigen(const R (&U)[3], R gamma, EulerEigen<R>& E) {
+    constexpr bool f32 = sizeof(R) == 4;
     const R rho = U[0];
-    const R irho = (R)1 / rho;
+    const R irho = recip(rho);
     const R u = U[1] * irho;
     const R g1 = gamma - (R)1;
     const R p = g1 * fma((R)-0.5 * U[1], u, U[2]);
     const R c2 = gamma * p * irho;
     const bool ok = (rho > (R)0) && (p > (R)0);
-    const R c = sqrt(c2);
-    const R ic = (R)1 / c;
+    R c, ic, b1;
+    if constexpr (f32) {
+        ic = rsqrtf(c2);          // the basis only needs FP32 accuracy
+        c = c2 * ic;
+        b1 = g1 * ic * ic;
+    } else {
+        c = sqrt(c2);
+        ic = (R)1 / c;
+        b1 = g1 / c2;
+    }
     const R H = (U[2] + p) * irho;
-    const R b1 = g1 / c2;
     const R b2 = (R)0.5 * b1 * u * u;
     E.Rm[0][0] = (R)1;       E.Rm[0][1] = (R)1;              E.Rm[0][2] = (R)1;
     E.Rm[1][0] = u - c;      E.Rm[1][1] = u;                 E.Rm[1][2] = u + c;
@@ -431,10 +510,19 @@ __device__ __forceinline__ R wave_speed(const R* u0, const StepArgs& args, unsig
         const R gamma = f32 ? (R)args.gamma_f : (R)args.gamma;
         const R g1 = f32 ? (R)args.g1_hi : (R)(args.gamma - 1.0);
         const R rho = u0[0];
-        const R u = u0[1] / rho;
-        const R p = g1 * fma((R)-0.5 * u0[1], u, u0[2]);
-        if (!(rho > (R)0) || !(p > (R)0)) err |= ERR_POSITIVITY;
-        return fabs(u) + sqrt(gamma * p / rho);
+        if constexpr (f32) {
+            const R irho = recip(rho);
+            const R u = u0[1] * irho;
+            const R p = g1 * fma((R)-0.5 * u0[1], u, u0[2]);
+            if (!(rho > (R)0) || !(p > (R)0)) err |= ERR_POSITIVITY;
+            const R c2 = gamma * p * irho;
+            return fabs(u) + c2 * rsqrtf(c2);
+        } else {
+            const R u = u0[1] / rho;
+            const R p = g1 * fma((R)-0.5 * u0[1], u, u0[2]);
+            if (!(rho > (R)0) || !(p > (R)0)) err |= ERR_POSITIVITY;
+            return fabs(u) + sqrt(gamma * p / rho);
+        }
     }
 }
 

@@ -106,6 +106,8 @@ extern "C" int wcc_advance_static(int system, int P, int bc, int64_t N, const do
     a.alpha_is_two = (o.alpha == 2.0);
     a.dx = (domain[1] - domain[0]) / (double)N;
     a.cfl = cfl;
+    a.cfl_mode = 1;
+    a.cfl_bits = (unsigned long long)__double_as_longlong_host(cfl);
     a.adv = o.adv_speed;
     a.gamma = o.gamma;
     a.alpha = o.alpha;

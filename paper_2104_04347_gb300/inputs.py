@@ -212,3 +212,26 @@ def random_smooth_dofs(ncells: int, nv: int, P: int, seed: int, scale: float = 1
     """Uniform random DOFs in [-scale, scale] (for unit-level checks)."""
     rng = np.random.default_rng(seed)
     return rng.uniform(-scale, scale, size=(ncells, nv, P + 1))
+
+
+def batch_workload(count: int = 4096, n_min: int = 256, n_max: int = 65536, degrees=(2, 3),
+                   seed: int = 2104043472) -> list:
+    """Independent 1D Euler problems: N_i = round(exp(U(ln n_min, ln n_max)))
+    (log-uniform), P_i drawn from `degrees` with equal probability, and 50/50
+    either a seeded Riemann problem on [0, 1] (transmissive; its own states,
+    drawn as in riemann_states) or the density wave on periodic [0, 1]."""
+    rng = SplitMix64(seed)
+    out = []
+    lo, hi = math.log(n_min), math.log(n_max)
+    for i in range(count):
+        N = int(round(math.exp(rng.uniform(lo, hi))))
+        P = degrees[int(rng.uniform(0.0, len(degrees)))]
+        if rng.uniform() < 0.5:
+            sub = rng.next_u64()
+            left, right = riemann_states(sub)
+            pr = euler_riemann(N, P, left, right, name=f"riemann-{i}")
+        else:
+            pr = euler_density_wave(N, P)
+            pr.name = f"density-wave-{i}"
+        out.append(pr)
+    return out

@@ -70,6 +70,23 @@ _SIGS = {
     "wcc_advance_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp,
                                           ctypes.POINTER(Options), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_double, _dp]),
+    "wcc_batch_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64, _i64p,
+                                        ctypes.POINTER(ctypes.c_int), _dp, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(Options)]),
+    "wcc_batch_dof_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc_batch_set_initial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "wcc_batch_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
+    "wcc_batch_get_dofs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "wcc_batch_get_times": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int64]),
+    "wcc_batch_get_state": (ctypes.c_int, [ctypes.c_void_p, _i64p, ctypes.POINTER(ctypes.c_int)]),
+    "wcc_batch_get_dt_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp, ctypes.c_int64, _i64p]),
+    "wcc_batch_set_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
+    "wcc_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    "wcc_batch_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
+    "wcc_batch_launch_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc_batch_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc_batch_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "wcc_batch_destroy": (None, [ctypes.c_void_p]),
     "wcc_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "wcc_destroy": (None, [ctypes.c_void_p]),
 }
@@ -225,4 +242,130 @@ class Solver:
     def launch_count(self) -> int:
         b = ctypes.c_int64()
         self._check(self.lib.wcc_launch_count(self.h, ctypes.byref(b)))
+        return b.value
+
+
+class Batch:
+    """Many independent problems advanced together (wraps a wcc_batch).
+
+    ``problems`` is a list of objects with system, N, P, x_l, x_r, bc and q0
+    (e.g. paper_2104_04347_gb300.inputs.Problem); all share the system.
+    Host arrays are the concatenation of the instances' [cells, nv, P+1]."""
+
+    def __init__(self, problems, *, limiter: bool = True, alpha: float = 2.0, eps: float = 1e-40,
+                 gamma: float = 1.4, adv_speed: float = 1.0, graph_chunk: int = 32, stream: int | None = None):
+        self.lib = load()
+        self.problems = list(problems)
+        n = len(self.problems)
+        system = self.problems[0].system
+        o = default_options()
+        o.precision = FP32_MIXED
+        o.limiter = 1 if limiter else 0
+        o.alpha, o.eps, o.gamma, o.adv_speed = alpha, eps, gamma, adv_speed
+        o.graph_chunk = graph_chunk
+        o.cuda_stream = stream
+        Ns = (ctypes.c_int64 * n)(*[p.N for p in self.problems])
+        Ps = (ctypes.c_int * n)(*[p.P for p in self.problems])
+        doms = (ctypes.c_double * (2 * n))(*[v for p in self.problems for v in (p.x_l, p.x_r)])
+        bcs = (ctypes.c_int * n)(*[p.bc for p in self.problems])
+        h = ctypes.c_void_p()
+        rc = self.lib.wcc_batch_create(ctypes.byref(h), system, n, Ns, Ps, doms, bcs, ctypes.byref(o))
+        if rc != 0:
+            raise WCCError(rc, self.lib.wcc_batch_last_error(None).decode())
+        self.h = h
+        self.system = system
+        self.nv = 3 if system == EULER else 1
+        self.count = n
+
+    def _check(self, rc: int) -> None:
+        if rc != 0:
+            raise WCCError(rc, self.lib.wcc_batch_last_error(self.h).decode())
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.wcc_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def dof_count(self) -> int:
+        c = ctypes.c_int64()
+        self._check(self.lib.wcc_batch_dof_count(self.h, ctypes.byref(c)))
+        return c.value
+
+    def set_initial(self, qs=None) -> None:
+        qs = [p.q0 for p in self.problems] if qs is None else qs
+        a = np.ascontiguousarray(np.concatenate([np.asarray(q, dtype=np.float64).reshape(-1) for q in qs]))
+        self._check(self.lib.wcc_batch_set_initial(self.h, _ptr(a), a.size))
+
+    def set_initial_ptr(self, host_ptr: int, count: int) -> None:
+        self._check(self.lib.wcc_batch_set_initial(self.h, ctypes.c_void_p(host_ptr), int(count)))
+
+    def step(self, nsteps: int, cfl: float) -> None:
+        self._check(self.lib.wcc_batch_step(self.h, int(nsteps), float(cfl)))
+
+    def state(self):
+        s = ctypes.c_int64()
+        p = ctypes.c_int()
+        self._check(self.lib.wcc_batch_get_state(self.h, ctypes.byref(s), ctypes.byref(p)))
+        return s.value, p.value
+
+    def get_dofs(self):
+        """List of [cells, nv, P+1] arrays, one per instance."""
+        _, parity = self.state()
+        flat = np.empty(self.dof_count())
+        self._check(self.lib.wcc_batch_get_dofs(self.h, _ptr(flat), flat.size))
+        out, off = [], 0
+        for p in self.problems:
+            cells = p.N if p.bc == PERIODIC else (p.N + 1 if parity == 0 else p.N)
+            n = cells * self.nv * (p.P + 1)
+            out.append(flat[off:off + n].reshape(cells, self.nv, p.P + 1))
+            off += n
+        return out
+
+    def get_dofs_ptr(self, host_ptr: int, count: int) -> None:
+        self._check(self.lib.wcc_batch_get_dofs(self.h, ctypes.c_void_p(host_ptr), int(count)))
+
+    def times(self) -> np.ndarray:
+        t = np.empty(self.count)
+        self._check(self.lib.wcc_batch_get_times(self.h, t.ctypes.data_as(_dp), self.count))
+        return t
+
+    def dt_history(self, instance: int) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._check(self.lib.wcc_batch_get_dt_history(self.h, int(instance), None, 0, ctypes.byref(n)))
+        out = np.empty(n.value)
+        self._check(self.lib.wcc_batch_get_dt_history(self.h, int(instance), out.ctypes.data_as(_dp), out.size,
+                                                      ctypes.byref(n)))
+        return out
+
+    def set_grid(self, ctas: int) -> None:
+        self._check(self.lib.wcc_batch_set_grid(self.h, int(ctas)))
+
+    def autotune(self, cfl: float) -> int:
+        c = ctypes.c_int()
+        self._check(self.lib.wcc_batch_autotune(self.h, float(cfl), ctypes.byref(c)))
+        return c.value
+
+    def synchronize(self) -> None:
+        self._check(self.lib.wcc_batch_synchronize(self.h))
+
+    def launch_count(self) -> int:
+        b = ctypes.c_int64()
+        self._check(self.lib.wcc_batch_launch_count(self.h, ctypes.byref(b)))
+        return b.value
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        self._check(self.lib.wcc_batch_device_bytes(self.h, ctypes.byref(b)))
         return b.value

@@ -96,3 +96,27 @@ def trajectory_check(pr, q_gpu, dts, *, limiter=True, adv_speed=1.0):
     ref = run(pr.q0)
     spread = oracle_spread(run, pr.q0, ref)
     return parity_violation(q_gpu, ref, spread), scaled_error(q_gpu, ref)
+
+
+def fp32_pair_violation(pr, q_a, q_b, dts, *, floor=2e-6, perturb=1e-7, trials=3, seed=0):
+    """Compare two FP32-mixed results of the same problem (e.g. a batch
+    instance and the same problem run alone): per cell
+    |a - b| <= max(floor x scale, 50 x the oracle's spread over `dts` when
+    its inputs are perturbed by `perturb` relative, FP32 rounding level).
+    Returns the largest ratio to that bound (<= 1 passes)."""
+    law = law_of(pr)
+
+    def run(q0):
+        s = oracle.Solver(law, q0, pr.dx)
+        s.step_dt(dts)
+        return s.q
+
+    ref = run(pr.q0)
+    rng = np.random.default_rng(seed)
+    spread = np.zeros_like(ref)
+    for _ in range(trials):
+        qp = pr.q0 * (1.0 + perturb * rng.standard_normal(pr.q0.shape))
+        spread = np.maximum(spread, np.abs(run(qp) - ref))
+    sc = scales(ref)
+    bound = np.maximum(floor * sc[None, :, None], SCATTER_FACTOR * spread)
+    return float(np.max(np.abs(q_a - q_b) / bound))
