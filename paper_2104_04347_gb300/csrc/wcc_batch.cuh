@@ -4,15 +4,16 @@
 // The instances of a batch share the conservation law and the options; each
 // has its own N, P, domain, boundary and dt (from its own CFL bound).  Cells
 // are flattened, not instances: every instance is cut into tiles of kTile new
-// cells, the tiles of all instances form one list (prefix table
-// tile_start), and a persistent grid walks the list.  A launch covers two
+// cells (kTileMixed for the half-step, kTile for the auxiliary kernels), the
+// tiles of all instances form one list (prefix table tile_start), and a
+// persistent grid walks the list.  A launch covers two
 // groups of instances, P = PA and P = PB (a batch holds at most two degrees);
 // each group keeps its stages in its own plane buffers with instance
 // offsets.  The tile code is the single-grid kernel's (mixed_tile), so an
 // instance of a batch evolves exactly like the same problem run alone.
 #pragma once
 
-#include "wcc_halfstep_mixed.cuh"
+#include "wcc_mixed2.cuh"
 
 namespace wcc {
 
@@ -52,9 +53,9 @@ __device__ __forceinline__ int tile_instance(const long long* tile_start, int n,
 
 template <int SYS, int PA, int PB>
 __global__ void __launch_bounds__(kThreads) batch_mixed(const BatchArgs b) {
-    constexpr int SA = mixed_tile_smem_floats<SYS, PA>();
-    constexpr int SB = mixed_tile_smem_floats<SYS, PB>();
-    __shared__ float rec[SA > SB ? SA : SB];
+    constexpr int SA = mixed2_smem_float2<SYS, PA>();
+    constexpr int SB = mixed2_smem_float2<SYS, PB>();
+    __shared__ float2 rec[SA > SB ? SA : SB];
     __shared__ int s_inst;
     for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
         if (threadIdx.x == 0) s_inst = tile_instance(b.tile_start, b.ninst, tile);
@@ -67,16 +68,16 @@ __global__ void __launch_bounds__(kThreads) batch_mixed(const BatchArgs b) {
         const StepSize z = cfl_step_size(st, b.phys.cfl_bits, b.phys.cfl, I.dx, b.parity);
         const int g = I.group;
         const TileIO io{b.in[g] + I.offset, b.out[g] + I.offset, b.pitch[g], I.cells[b.parity],
-                        I.cells[b.parity ^ 1], (tile - first) * kTile, b.parity, I.bc};
+                        I.cells[b.parity ^ 1], (tile - first) * kTileMixed, b.parity, I.bc};
         float speed = 0.f;
         unsigned err = 0u;
         StepArgs ph = b.phys;  // per-instance boundary and mesh width
         ph.bc = I.bc;
         ph.dx = I.dx;
         if (g == 0)
-            mixed_tile<SYS, PA>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
+            mixed_tile2<SYS, PA>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
         else
-            mixed_tile<SYS, PB>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
+            mixed_tile2<SYS, PB>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
         reduce_and_finish<float>(speed, err, z.dt, st, ntiles, b.hist + (long long)i * b.hist_cap, b.hist_cap,
                                  b.parity, 1, b.phys.cfl, I.dx);
     }

@@ -78,7 +78,8 @@ long long cells_of(int bc, long long N, int parity) {
     return parity == 0 ? N + 1 : N;
 }
 
-long long tiles_of(long long cells) { return (cells + kTile - 1) / kTile; }
+long long tiles_of(long long cells) { return (cells + kTile - 1) / kTile; }              // auxiliary kernels
+long long step_tiles_of(long long cells) { return (cells + kTileMixed - 1) / kTileMixed; }  // half-step kernel
 
 BatchArgs make_bargs(wcc_batch_ctx* b, int cur, int parity, double cfl, int kind) {
     BatchArgs a{};
@@ -336,7 +337,7 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
         ts[s].assign(count + 1, 0);
         tc[s].assign(count + 1, 0);
         for (int64_t k = 0; k < count; ++k) {
-            ts[s][k + 1] = ts[s][k] + tiles_of(b->inst[k].cells[s ^ 1]);
+            ts[s][k + 1] = ts[s][k] + step_tiles_of(b->inst[k].cells[s ^ 1]);
             tc[s][k + 1] = tc[s][k] + tiles_of(b->inst[k].cells[s]);
         }
         b->tiles_step[s] = ts[s][count];

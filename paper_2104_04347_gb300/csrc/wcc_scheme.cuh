@@ -15,6 +15,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "wcc_f2.cuh"
+
 namespace wcc {
 
 enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
@@ -225,7 +227,7 @@ __device__ __forceinline__ void ck_table(const R (&c)[nvars(SYS)][P + 1], R lam,
         sfor<0, K>([&](auto A) { X[v][decltype(A)::value][0] = c[v][decltype(A)::value]; });
     });
 
-    constexpr bool f32 = sizeof(R) == 4;
+    constexpr bool f32 = !is_f64<R>;
     if constexpr (SYS == ADVECTION) {
         const R a = f32 ? (R)args.adv_hi : (R)args.adv;
         const R la = lam * a;
@@ -417,39 +419,68 @@ __device__ __forceinline__ void limit_scalar(R (&e)[P + 1], R ubar, R vl, R vr, 
     });
     const R b1 = s1 * s1, b2 = s2 * s2;
     const R eps = (R)args.eps;
-    R wh0, wh1, wh2;
-    if constexpr (P == 1) {
-        // Eq. 1D2ndOrderWeights: (1 / (beta + eps))^alpha
-        R i0 = (R)1 / (b0 + eps), i1 = (R)1 / (b1 + eps), i2 = (R)1 / (b2 + eps);
-        if (args.alpha_is_two) {
-            wh0 = i0 * i0; wh1 = i1 * i1; wh2 = i2 * i2;
+    R w0, w1, w2;
+    if (args.alpha_is_two) {
+        // Multiplied through by the denominators, so that one reciprocal
+        // normalises the weights; w0 = 1 - w1 - w2 is exactly 1 when the
+        // other two vanish.
+        R h0, h1, h2;
+        if constexpr (P == 1) {
+            // Eq. 1D2ndOrderWeights: w_m ~ (beta_m + eps)^-2
+            const R d0 = b0 + eps, d1 = b1 + eps, d2 = b2 + eps;
+            const R p12 = d1 * d2, p02 = d0 * d2, p01 = d0 * d1;
+            h0 = p12 * p12;
+            h1 = p02 * p02;
+            h2 = p01 * p01;
         } else {
-            const R al = (R)args.alpha;
-            wh0 = pow(i0, al); wh1 = pow(i1, al); wh2 = pow(i2, al);
+            // Eq. 1DHighOrderWeights: w0 ~ 1 + (st/d0)^2, w_m ~ (st/d_m)^2
+            R up = e[0], um = e[0];
+            sfor<1, P + 1>([&](auto Ki) {
+                constexpr int k = decltype(Ki)::value;
+                up = fma((R)chalf(k, false), e[k], up);
+                um = fma((R)chalf(k, true), e[k], um);
+            });
+            const R rr = up - vr, rl = um - vl;
+            const R sigma = fma(rr, rr, rl * rl);
+            const R tp = (R)cfact(P) * e[P];
+            const R st = sigma * (tp * tp);
+            const R d0 = fma(b0, b0, eps), d1 = fma(b1, b1, eps), d2 = fma(b2, b2, eps);
+            const R p12 = d1 * d2, p02 = d0 * d2, p01 = d0 * d1;
+            const R s12 = st * p12, s02 = st * p02, s01 = st * p01;
+            h0 = fma(d0 * p12, d0 * p12, s12 * s12);
+            h1 = s02 * s02;
+            h2 = s01 * s01;
         }
+        const R inv = recip(h0 + h1 + h2);
+        w1 = h1 * inv;
+        w2 = h2 * inv;
+        w0 = (R)1 - (w1 + w2);
     } else {
-        // Eq. 1DHighOrderWeights: sigma from the residuals at both vertices,
-        // tau = (u_Px)^2 = (P! e_P)^2.
-        R up = e[0], um = e[0];
-        sfor<1, P + 1>([&](auto Ki) {
-            constexpr int k = decltype(Ki)::value;
-            up = fma((R)chalf(k, false), e[k], up);
-            um = fma((R)chalf(k, true), e[k], um);
-        });
-        const R rr = up - vr, rl = um - vl;
-        const R sigma = fma(rr, rr, rl * rl);
-        const R tp = (R)cfact(P) * e[P];
-        const R st = sigma * (tp * tp);
-        R r0 = st / fma(b0, b0, eps), r1 = st / fma(b1, b1, eps), r2 = st / fma(b2, b2, eps);
-        if (args.alpha_is_two) {
-            wh0 = fma(r0, r0, (R)1); wh1 = r1 * r1; wh2 = r2 * r2;
-        } else {
+        R wh0, wh1, wh2;
+        if constexpr (P == 1) {
             const R al = (R)args.alpha;
-            wh0 = (R)1 + pow(r0, al); wh1 = pow(r1, al); wh2 = pow(r2, al);
+            wh0 = pow((R)1 / (b0 + eps), al); wh1 = pow((R)1 / (b1 + eps), al); wh2 = pow((R)1 / (b2 + eps), al);
+        } else {
+            R up = e[0], um = e[0];
+            sfor<1, P + 1>([&](auto Ki) {
+                constexpr int k = decltype(Ki)::value;
+                up = fma((R)chalf(k, false), e[k], up);
+                um = fma((R)chalf(k, true), e[k], um);
+            });
+            const R rr = up - vr, rl = um - vl;
+            const R sigma = fma(rr, rr, rl * rl);
+            const R tp = (R)cfact(P) * e[P];
+            const R st = sigma * (tp * tp);
+            const R al = (R)args.alpha;
+            wh0 = (R)1 + pow(st / fma(b0, b0, eps), al);
+            wh1 = pow(st / fma(b1, b1, eps), al);
+            wh2 = pow(st / fma(b2, b2, eps), al);
         }
+        const R inv = (R)1 / (wh0 + wh1 + wh2);
+        w1 = wh1 * inv;
+        w2 = wh2 * inv;
+        w0 = (R)1 - (w1 + w2);
     }
-    const R inv = (R)1 / (wh0 + wh1 + wh2);
-    const R w0 = wh0 * inv, w1 = wh1 * inv, w2 = wh2 * inv;
     // Eq. 1DLimitedPolynomial, coefficient by coefficient.
     e[0] = fma(w0, e[0], (w1 + w2) * ubar);
     e[1] = fma(w0, e[1], fma(w1, s1, w2 * s2));
@@ -467,23 +498,23 @@ struct EulerEigen {
 
 template <class R>
 __device__ __forceinline__ bool euler_eigen(const R (&U)[3], R gamma, EulerEigen<R>& E) {
-    constexpr bool f32 = sizeof(R) == 4;
+    constexpr bool f32 = !is_f64<R>;
     const R rho = U[0];
     const R irho = recip(rho);
     const R u = U[1] * irho;
     const R g1 = gamma - (R)1;
     const R p = g1 * fma((R)-0.5 * U[1], u, U[2]);
     const R c2 = gamma * p * irho;
-    const bool ok = (rho > (R)0) && (p > (R)0);
+    const bool ok = all_pos(rho) && all_pos(p);
     R c, ic, b1;
     if constexpr (f32) {
-        ic = rsqrtf(c2);          // the basis only needs FP32 accuracy
+        ic = rsqrt_approx(c2);    // the basis only needs FP32 accuracy
         c = c2 * ic;
         b1 = g1 * ic * ic;
     } else {
         c = sqrt(c2);
         ic = (R)1 / c;
-        b1 = g1 / c2;
+        b1 = g1 * ic * ic;
     }
     const R H = (U[2] + p) * irho;
     const R b2 = (R)0.5 * b1 * u * u;
@@ -501,7 +532,7 @@ __device__ __forceinline__ bool euler_eigen(const R (&U)[3], R gamma, EulerEigen
 // at the centre point values; sets err bits for non-physical states.
 template <int SYS, class R>
 __device__ __forceinline__ R wave_speed(const R* u0, const StepArgs& args, unsigned& err) {
-    constexpr bool f32 = sizeof(R) == 4;
+    constexpr bool f32 = !is_f64<R>;
     if constexpr (SYS == ADVECTION) {
         return f32 ? (R)fabsf(args.adv_hi) : (R)fabs(args.adv);
     } else if constexpr (SYS == BURGERS) {
@@ -514,14 +545,15 @@ __device__ __forceinline__ R wave_speed(const R* u0, const StepArgs& args, unsig
             const R irho = recip(rho);
             const R u = u0[1] * irho;
             const R p = g1 * fma((R)-0.5 * u0[1], u, u0[2]);
-            if (!(rho > (R)0) || !(p > (R)0)) err |= ERR_POSITIVITY;
+            if (!all_pos(rho) || !all_pos(p)) err |= ERR_POSITIVITY;
             const R c2 = gamma * p * irho;
-            return fabs(u) + c2 * rsqrtf(c2);
+            return fabs(u) + c2 * rsqrt_approx(c2);
         } else {
-            const R u = u0[1] / rho;
+            const R irho = (R)1 / rho;
+            const R u = u0[1] * irho;
             const R p = g1 * fma((R)-0.5 * u0[1], u, u0[2]);
-            if (!(rho > (R)0) || !(p > (R)0)) err |= ERR_POSITIVITY;
-            return fabs(u) + sqrt(gamma * p / rho);
+            if (!all_pos(rho) || !all_pos(p)) err |= ERR_POSITIVITY;
+            return fabs(u) + sqrt(gamma * p * irho);
         }
     }
 }
