@@ -74,11 +74,11 @@ def peaks():
 # limiter on), counted from the executed DADD / DMUL / DFMA instructions (ncu
 # smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum over one
 # launch at N = 2^21, DFMA counted as 2) divided by the cells of the launch:
-# (2 x 1053618000 + 207934209 + 378169546) / 2097152.5.
-FP64_FLOPS_PER_CELL_UPDATE = 1284.3
+# (2 x 711549710 + 220517122 + 386508291) / 2097152.5.
+FP64_FLOPS_PER_CELL_UPDATE = 968.0
 # DRAM bytes (read + write) of one FP64 launch, from the same capture
-# (201536256 + 149675008 at N = 2^21), scaled by cells to N = 2^22.
-FP64_TRAFFIC_PER_CELL = (201536256 + 149675008) / 2097152.5
+# (201458688 + 149019904 at N = 2^21), scaled by cells to N = 2^22.
+FP64_TRAFFIC_PER_CELL = (201458688 + 149019904) / 2097152.5
 # DRAM bytes (read + write) of one FP32-mixed launch per cell; None until
 # captured for the current kernel.
 MIXED_TRAFFIC_PER_CELL = None

@@ -36,31 +36,20 @@ struct BatchArgs {
     float* out[2];                 // next stage planes
     long long pitch[2];
     const long long* tile_start;   // [ninst + 1] exclusive prefix of tiles per instance
+    const int* tile_inst;          // [total_tiles] instance of every tile
     long long total_tiles;
     int ninst;
     int parity;
 };
 
-// Index i with tile_start[i] <= tile < tile_start[i + 1].
-__device__ __forceinline__ int tile_instance(const long long* tile_start, int n, long long tile) {
-    int lo = 0, hi = n;  // invariant: tile_start[lo] <= tile < tile_start[hi]
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (__ldg(tile_start + mid) <= tile) lo = mid; else hi = mid;
-    }
-    return lo;
-}
 
 template <int SYS, int PA, int PB>
-__global__ void __launch_bounds__(kThreads) batch_mixed(const BatchArgs b) {
+__global__ void __launch_bounds__(kThreads, kMixedMinCtas) batch_mixed(const BatchArgs b) {
     constexpr int SA = mixed2_smem_float2<SYS, PA>();
     constexpr int SB = mixed2_smem_float2<SYS, PB>();
     __shared__ float2 rec[SA > SB ? SA : SB];
-    __shared__ int s_inst;
     for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
-        if (threadIdx.x == 0) s_inst = tile_instance(b.tile_start, b.ninst, tile);
-        __syncthreads();  // also orders the previous tile's last use of rec
-        const int i = s_inst;
+        const int i = __ldg(b.tile_inst + tile);
         const BatchInstance I = b.inst[i];
         DevState* st = b.st + i;
         const long long first = __ldg(b.tile_start + i);
@@ -89,7 +78,7 @@ __global__ void __launch_bounds__(kThreads) batch_mixed(const BatchArgs b) {
 template <int SYS, int PA, int PB>
 __global__ void __launch_bounds__(kThreads) batch_stage_speed(const BatchArgs b) {
     for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
-        const int i = tile_instance(b.tile_start, b.ninst, tile);
+        const int i = __ldg(b.tile_inst + tile);
         const BatchInstance I = b.inst[i];
         const long long c = (tile - b.tile_start[i]) * kTile + threadIdx.x;
         float s = 0.f;
@@ -128,7 +117,7 @@ __global__ void __launch_bounds__(kThreads) batch_stage_speed(const BatchArgs b)
 template <int SYS, int PA, int PB>
 __global__ void __launch_bounds__(kThreads) batch_convert(const BatchArgs b, double* aos, int to_planes) {
     for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
-        const int i = tile_instance(b.tile_start, b.ninst, tile);
+        const int i = __ldg(b.tile_inst + tile);
         const BatchInstance I = b.inst[i];
         const long long c = (tile - b.tile_start[i]) * kTile + threadIdx.x;
         if (threadIdx.x >= kTile || c >= I.cells[b.parity]) continue;

@@ -40,6 +40,8 @@ struct wcc_batch_ctx {
     long long pitch[2] = {0, 0};
     long long* d_tiles_step[2] = {nullptr, nullptr};  // tiles of the launch from a stage of parity s
     long long* d_tiles_cur[2] = {nullptr, nullptr};   // tiles of a stage of parity s
+    int* d_inst_step[2] = {nullptr, nullptr};         // instance of every step tile
+    int* d_inst_cur[2] = {nullptr, nullptr};          // instance of every auxiliary tile
     long long tiles_step[2] = {0, 0}, tiles_cur[2] = {0, 0};
     long long aos_total[2] = {0, 0};  // doubles of a host-layout stage of parity s
     double* staging = nullptr;
@@ -109,9 +111,11 @@ BatchArgs make_bargs(wcc_batch_ctx* b, int cur, int parity, double cfl, int kind
     }
     if (kind == BATCH_STEP) {
         a.tile_start = b->d_tiles_step[parity];
+        a.tile_inst = b->d_inst_step[parity];
         a.total_tiles = b->tiles_step[parity];
     } else {
         a.tile_start = b->d_tiles_cur[parity];
+        a.tile_inst = b->d_inst_cur[parity];
         a.total_tiles = b->tiles_cur[parity];
     }
     a.ninst = (int)b->count;
@@ -217,6 +221,8 @@ void release(wcc_batch_ctx* b) {
     for (int s = 0; s < 2; ++s) {
         if (b->d_tiles_step[s]) cudaFree(b->d_tiles_step[s]);
         if (b->d_tiles_cur[s]) cudaFree(b->d_tiles_cur[s]);
+        if (b->d_inst_step[s]) cudaFree(b->d_inst_step[s]);
+        if (b->d_inst_cur[s]) cudaFree(b->d_inst_cur[s]);
     }
     if (b->d_inst) cudaFree(b->d_inst);
     if (b->d_st) cudaFree(b->d_st);
@@ -382,9 +388,18 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
     }
     dmalloc((void**)&b->d_inst, sizeof(BatchInstance) * count);
     dmalloc((void**)&b->d_st, sizeof(DevState) * count);
+    std::vector<int> is[2], ic[2];
     for (int s = 0; s < 2; ++s) {
         dmalloc((void**)&b->d_tiles_step[s], sizeof(long long) * (count + 1));
         dmalloc((void**)&b->d_tiles_cur[s], sizeof(long long) * (count + 1));
+        is[s].resize(b->tiles_step[s]);
+        ic[s].resize(b->tiles_cur[s]);
+        for (int64_t k = 0; k < count; ++k) {
+            for (long long t = ts[s][k]; t < ts[s][k + 1]; ++t) is[s][t] = (int)k;
+            for (long long t = tc[s][k]; t < tc[s][k + 1]; ++t) ic[s][t] = (int)k;
+        }
+        dmalloc((void**)&b->d_inst_step[s], sizeof(int) * std::max<long long>(b->tiles_step[s], 1));
+        dmalloc((void**)&b->d_inst_cur[s], sizeof(int) * std::max<long long>(b->tiles_cur[s], 1));
     }
     dmalloc((void**)&b->staging, sizeof(double) * (size_t)std::max(b->aos_total[0], b->aos_total[1]));
     if (!ok) {
@@ -396,7 +411,10 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
     for (int s = 0; s < 2; ++s) {
         cudaMemcpyAsync(b->d_tiles_step[s], ts[s].data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, b->stream);
         cudaMemcpyAsync(b->d_tiles_cur[s], tc[s].data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(b->d_inst_step[s], is[s].data(), sizeof(int) * is[s].size(), cudaMemcpyHostToDevice, b->stream);
+        cudaMemcpyAsync(b->d_inst_cur[s], ic[s].data(), sizeof(int) * ic[s].size(), cudaMemcpyHostToDevice, b->stream);
     }
+    cudaStreamSynchronize(b->stream);  // the host vectors go out of scope
     cudaMemsetAsync(b->d_st, 0, sizeof(DevState) * count, b->stream);
     switch (system) {
         case WCC_ADVECTION: b->max_ctas_per_sm = batch_blocks_per_sm<ADVECTION>(b->PA, b->PB); break;

@@ -18,6 +18,13 @@ namespace wcc {
 
 constexpr int kTileMixed = 2 * kThreads - 1;
 
+// Resident CTAs per SM the FP32-mixed kernels are compiled for (register
+// budget 65536 / (kThreads * kMixedMinCtas) per thread).
+#ifndef WCC_MIXED_MIN_CTAS
+#define WCC_MIXED_MIN_CTAS 5
+#endif
+constexpr int kMixedMinCtas = WCC_MIXED_MIN_CTAS;
+
 // ------------------------------------------------------ float-float pairs
 
 struct ff2 {
@@ -360,7 +367,7 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
 }
 
 template <int SYS, int P>
-__global__ void __launch_bounds__(kThreads) halfstep_mixed2(const StepArgs args) {
+__global__ void __launch_bounds__(kThreads, kMixedMinCtas) halfstep_mixed2(const StepArgs args) {
     __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
     const StepSize z = step_size(args);
     const TileIO io{args.in32, args.out32, args.pitch, args.n_old, args.n_new,
