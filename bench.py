@@ -79,9 +79,10 @@ FP64_FLOPS_PER_CELL_UPDATE = 968.0
 # DRAM bytes (read + write) of one FP64 launch, from the same capture
 # (201458688 + 149019904 at N = 2^21), scaled by cells to N = 2^22.
 FP64_TRAFFIC_PER_CELL = (201458688 + 149019904) / 2097152.5
-# DRAM bytes (read + write) of one FP32-mixed launch per cell; None until
-# captured for the current kernel.
-MIXED_TRAFFIC_PER_CELL = None
+# DRAM bytes (read + write) of one FP32-mixed launch per cell, from an ncu
+# capture of halfstep_mixed2<EULER, 3> at N = 2^21 (125896192 + 79292672),
+# scaled by cells to N = 2^22.
+MIXED_TRAFFIC_PER_CELL = (125896192 + 79292672) / 2097152.5
 # FP64 pipe peak of the GB300 (dense, nominal): 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 
