@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch", type=int, default=1, help="also time the 4096-instance batch (1/0)")
+    ap.add_argument("--sweep", action="store_true", help="precision / convergence sweep (density wave) instead")
+    ap.add_argument("--sweep-max-log2n", type=int, default=16)
     return ap.parse_args()
 
 
@@ -198,6 +200,25 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------ GPU
 
 
+def reduce_over_ranks(x, op, device):
+    """All-reduce one number over the ranks of the default process group
+    (op: "max" or "sum"); the number itself without a group."""
+    import torch
+    import torch.distributed as td
+
+    if not (td.is_available() and td.is_initialized()):
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX if op == "max" else td.ReduceOp.SUM)
+    return float(t.item())
+
+
+def job_throughput(local_units, local_seconds, device):
+    """Whole-job rate of independent replicas: the units all ranks processed
+    divided by the slowest rank's time."""
+    return reduce_over_ranks(local_units, "sum", device) / reduce_over_ranks(local_seconds, "max", device)
+
+
 def l1_check(log2n_small=12, halfsteps=2000):
     """L1 error (centre point values, scaled per variable) of both GPU
     precisions against the FP64 oracle on the bench workload at a small N,
@@ -301,11 +322,7 @@ def run_wcc(args, rank, world):
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(x, "max", dev)
 
     N = 1 << args.log2n
     pr = inputs.euler_riemann_seeded(N, P)
@@ -325,10 +342,11 @@ def run_wcc(args, rank, world):
         solver.set_initial(pr.q0)
         steps = args.steps if name == args.precision else max(2, min(args.steps, 5))
         total_ms, step_ms, launches = time_solver(solver, stream, steps, args.warmup, barrier)
+        value = job_throughput(cells_per_step * steps, total_ms * 1e-3, dev)
         total_ms = max_over_ranks(total_ms)
         kernel_ms = statistics.median(step_ms) / HALFSTEPS_PER_STEP
         bpc = bytes_per_cell_update(name)
-        res = {"value": world * cells_per_step * steps / (total_ms * 1e-3), "ms_per_step": total_ms / steps,
+        res = {"value": value, "ms_per_step": total_ms / steps,
                "steps": steps, "kernel_ms": kernel_ms, "gpu_launches": launches}
         gbs = bpc * cells_per_launch / (kernel_ms * 1e-3) / 1e9
         hbm = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s",
@@ -371,8 +389,7 @@ def run_wcc(args, rank, world):
         solver.step(HALFSTEPS_PER_STEP, CFL)
         solver.get_dofs_ptr(h_out.data_ptr(), count)
     barrier()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e_value = world * cells_per_step * e2e_steps / e2e_s
+    e2e_value = job_throughput(cells_per_step * e2e_steps, time.perf_counter() - t0, dev)
     assert np.all(np.isfinite(h_out.numpy()))
     solver.close()
 
@@ -411,8 +428,67 @@ def run_wcc(args, rank, world):
         torch.distributed.destroy_process_group()
 
 
+def precision_sweep(max_log2n=16):
+    """Smooth Euler density wave rho = 1 + 0.2 sin 2 pi x, u = 1, p = 1,
+    periodic [0, 1], to t = 1, P = 1..4, N = 2^8 .. 2^max_log2n: every
+    precision on the same half-step sizes; L1 of the density point values
+    against the exact solution and against the FP64 path (and the oracle for
+    N <= 2^10), and the measured order.  Prints one JSON line per case and a
+    markdown table."""
+    import math
+
+    import oracle
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    oracle.set_threads(os.cpu_count() or 1)
+    nu = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2}
+    amax = 1.0 + math.sqrt(1.4 / 0.8)
+    names = {wcc.FP64: "fp64", wcc.FP32_MIXED: "fp32-mixed", wcc.FP32: "fp32"}
+    rows = []
+    for P in (1, 2, 3, 4):
+        prev = {}
+        for log2n in range(8, max_log2n + 1):
+            N = 1 << log2n
+            pr = inputs.euler_density_wave(N, P)
+            dts = oracle.constant_speed_dts(1.0, nu[P] * pr.dx / amax)
+            x = inputs.centres(N, 0.0, 1.0, inputs.PERIODIC)
+            exact = 1.0 + 0.2 * np.sin(2 * math.pi * (x - 1.0))
+            res = {}
+            for prec in (wcc.FP64, wcc.FP32_MIXED, wcc.FP32):
+                with wcc.Solver(pr.system, N, P, (0.0, 1.0), pr.bc, precision=prec, limiter=True) as s:
+                    s.set_initial(pr.q0)
+                    t0 = time.perf_counter()
+                    s.step_dt(dts)
+                    q = s.get_dofs()
+                    res[prec] = (q, time.perf_counter() - t0)
+            q64 = res[wcc.FP64][0]
+            ref = None
+            if log2n <= 10:
+                sol = oracle.Solver(oracle.make_law(oracle.EULER, P, limiter=True), pr.q0, pr.dx)
+                sol.step_dt(dts)
+                ref = sol.q
+            for prec, (q, secs) in res.items():
+                e = float(np.mean(np.abs(q[:, 0, 0] - exact)))
+                row = {"P": P, "N": N, "precision": names[prec], "halfsteps": len(dts),
+                       "l1_exact": e, "l1_vs_fp64": float(np.mean(np.abs(q[:, 0, 0] - q64[:, 0, 0]))),
+                       "l1_vs_oracle": None if ref is None else float(np.mean(np.abs(q[:, 0, 0] - ref[:, 0, 0]))),
+                       "order": (math.log2(prev[prec] / e) if prec in prev and e > 0 else None), "seconds": secs}
+                prev[prec] = e
+                rows.append(row)
+                print(json.dumps(row), flush=True)
+    print("| P | N | precision | L1 vs exact | order | L1 vs FP64 | L1 vs oracle |")
+    print("|---|---|---|---|---|---|---|")
+    for r in rows:
+        o = "" if r["order"] is None else f"{r['order']:.2f}"
+        lo = "" if r["l1_vs_oracle"] is None else f"{r['l1_vs_oracle']:.2e}"
+        print(f"| {r['P']} | {r['N']} | {r['precision']} | {r['l1_exact']:.3e} | {o} | {r['l1_vs_fp64']:.2e} | {lo} |")
+
+
 def main():
     args = parse()
+    if args.sweep:
+        precision_sweep(args.sweep_max_log2n)
+        return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":

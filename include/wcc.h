@@ -48,7 +48,12 @@ extern "C" {
 
 enum { WCC_ADVECTION = 0, WCC_BURGERS = 1, WCC_EULER = 2 };
 enum { WCC_BC_PERIODIC = 0, WCC_BC_TRANSMISSIVE = 1 };
-enum { WCC_FP64 = 0, WCC_FP32_MIXED = 1 };
+/* WCC_FP64: everything in double.  WCC_FP32_MIXED: FP32 Taylor coefficients
+ * and FP32 arithmetic, with the cell averages, the leading flux term and the
+ * vertex values in compensated FP32 (float-float).  WCC_FP32: the same
+ * kernel without the compensation (the cell average rounded to one float),
+ * kept to measure what the compensation buys. */
+enum { WCC_FP64 = 0, WCC_FP32_MIXED = 1, WCC_FP32 = 2 };
 
 enum {
     WCC_OK = 0,

@@ -54,11 +54,11 @@ __global__ void planes_to_aos_fp64(const double* __restrict__ planes, long long 
     }
 }
 
-// FP32-mixed: per (cell, var) the cell average (Eq. SubEq:1DCellAVG:
+// FP32-mixed / FP32: per (cell, var) the cell average (Eq. SubEq:1DCellAVG:
 // ubar = sum_{k even} u_kx / ((k+1)! 2^k)) split into a float-float pair,
 // and e_k = u_kx / k! rounded to FP32 for k >= 1.
 __global__ void aos_to_planes_mixed(const double* __restrict__ aos, long long n, int nv, int K, long long pitch,
-                                    float* __restrict__ planes) {
+                                    float* __restrict__ planes, int keep_lo) {
     const int NP = K + 1;
     const long long total = n * nv;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
@@ -76,7 +76,7 @@ __global__ void aos_to_planes_mixed(const double* __restrict__ aos, long long n,
         float hi, lo;
         split_double(ubar, hi, lo);
         planes[(long long)(v * NP + 0) * pitch + cell] = hi;
-        planes[(long long)(v * NP + 1) * pitch + cell] = lo;
+        planes[(long long)(v * NP + 1) * pitch + cell] = keep_lo ? lo : 0.f;  // plain FP32: average rounded once
     }
 }
 
@@ -328,8 +328,8 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     wcc_options o;
     wcc_default_options(&o);
     if (opt) o = *opt;
-    if (o.precision != WCC_FP64 && o.precision != WCC_FP32_MIXED)
-        return fail(nullptr, WCC_E_INVAL, "precision must be WCC_FP64 or WCC_FP32_MIXED");
+    if (o.precision != WCC_FP64 && o.precision != WCC_FP32_MIXED && o.precision != WCC_FP32)
+        return fail(nullptr, WCC_E_INVAL, "precision must be WCC_FP64, WCC_FP32_MIXED or WCC_FP32");
     if (!(o.eps >= 0.0) || !(o.alpha > 0.0) || !(o.gamma > 1.0))
         return fail(nullptr, WCC_E_INVAL, "need eps >= 0, alpha > 0, gamma > 1");
     if (o.graph_chunk < 0) return fail(nullptr, WCC_E_INVAL, "graph_chunk must be >= 0");
@@ -367,7 +367,7 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     const long long maxcells = N + 1;
     h->pitch = (maxcells + 63) / 64 * 64;  // 512-byte aligned planes
     const long long planes = (long long)h->nv * h->K;
-    const bool mixed = o.precision == WCC_FP32_MIXED;
+    const bool mixed = o.precision != WCC_FP64;  // FP32 planes (FP32-mixed and FP32)
     const size_t state_bytes = mixed ? (size_t)((long long)h->nv * (h->K + 1) * h->pitch) * sizeof(float)
                                      : (size_t)(planes * h->pitch) * sizeof(double);
     const size_t staging_bytes = (size_t)(maxcells * planes) * sizeof(double);
@@ -419,10 +419,10 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     h->cur = 0;
     h->parity = 0;
     h->steps = 0;
-    const bool mixed = h->opt.precision == WCC_FP32_MIXED;
+    const bool mixed = h->opt.precision != WCC_FP64;
     if (mixed)
-        aos_to_planes_mixed<<<elementwise_grid(n * h->nv), 256, 0, h->stream>>>(h->staging, n, h->nv, h->K,
-                                                                                 h->pitch, h->s32[0]);
+        aos_to_planes_mixed<<<elementwise_grid(n * h->nv), 256, 0, h->stream>>>(
+            h->staging, n, h->nv, h->K, h->pitch, h->s32[0], h->opt.precision == WCC_FP32_MIXED);
     else
         aos_to_planes_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->staging, n, h->nv, h->K, h->pitch,
                                                                               h->s64[0]);
@@ -506,7 +506,7 @@ int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     const long long n = stage_cells(h, h->parity);
     if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match the current stage");
-    if (h->opt.precision == WCC_FP32_MIXED)
+    if (h->opt.precision != WCC_FP64)
         planes_to_aos_mixed<<<elementwise_grid(n * h->nv), 256, 0, h->stream>>>(h->s32[h->cur], n, h->nv, h->K,
                                                                                  h->pitch, h->staging);
     else

@@ -64,9 +64,9 @@ __global__ void __launch_bounds__(kThreads, kMixedMinCtas) batch_mixed(const Bat
         ph.bc = I.bc;
         ph.dx = I.dx;
         if (g == 0)
-            mixed_tile2<SYS, PA>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
+            mixed_tile2<SYS, PA, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
         else
-            mixed_tile2<SYS, PB>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
+            mixed_tile2<SYS, PB, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
         reduce_and_finish<float>(speed, err, z.dt, st, ntiles, b.hist + (long long)i * b.hist_cap, b.hist_cap,
                                  b.parity, 1, b.phys.cfl, I.dx);
     }

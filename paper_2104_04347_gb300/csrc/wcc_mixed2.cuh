@@ -77,19 +77,45 @@ __device__ __forceinline__ ff2 ff2_div(ff2 a, ff2 b) {
 // (a - b) rounded to a pair of floats, a and b close (Sterbenz on the hi parts)
 __device__ __forceinline__ f2 ff2_diff(ff2 a, ff2 b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
-template <int SYS>
+// Arithmetic on cell-average quantities: float-float (COMP = true, the
+// FP32-mixed precision) or plain FP32 with the low parts kept at zero
+// (COMP = false, the uncompensated FP32 precision used to measure what the
+// compensation buys).
+template <bool COMP>
+struct FF {
+    static __device__ __forceinline__ ff2 add(ff2 a, ff2 b) { return ff2_add(a, b); }
+    static __device__ __forceinline__ ff2 add(ff2 a, f2 b) { return ff2_add(a, b); }
+    static __device__ __forceinline__ ff2 sub(ff2 a, ff2 b) { return ff2_sub(a, b); }
+    static __device__ __forceinline__ ff2 mul(ff2 a, ff2 b) { return ff2_mul(a, b); }
+    static __device__ __forceinline__ ff2 div(ff2 a, ff2 b) { return ff2_div(a, b); }
+    static __device__ __forceinline__ f2 diff(ff2 a, ff2 b) { return ff2_diff(a, b); }
+};
+
+template <>
+struct FF<false> {
+    static __device__ __forceinline__ ff2 mk(f2 h) { return ff2{h, f2(0.f)}; }
+    static __device__ __forceinline__ ff2 add(ff2 a, ff2 b) { return mk(a.hi + b.hi); }
+    static __device__ __forceinline__ ff2 add(ff2 a, f2 b) { return mk(a.hi + b); }
+    static __device__ __forceinline__ ff2 sub(ff2 a, ff2 b) { return mk(a.hi - b.hi); }
+    static __device__ __forceinline__ ff2 mul(ff2 a, ff2 b) { return mk(a.hi * b.hi); }
+    static __device__ __forceinline__ ff2 div(ff2 a, ff2 b) { return mk(fdiv_fast(a.hi, b.hi)); }
+    static __device__ __forceinline__ f2 diff(ff2 a, ff2 b) { return a.hi - b.hi; }
+};
+
+template <int SYS, bool COMP>
 __device__ __forceinline__ void flux_ff2(const ff2 (&u)[nvars(SYS)], const StepArgs& args, ff2 (&f)[nvars(SYS)]) {
+    using A = FF<COMP>;
     if constexpr (SYS == ADVECTION) {
-        f[0] = ff2_mul(u[0], ff2{f2(args.adv_hi), f2(args.adv_lo)});
+        f[0] = A::mul(u[0], ff2{f2(args.adv_hi), f2(COMP ? args.adv_lo : 0.f)});
     } else if constexpr (SYS == BURGERS) {
-        f[0] = ff2_scale(ff2_mul(u[0], u[0]), 0.5f);
+        f[0] = ff2_scale(A::mul(u[0], u[0]), 0.5f);
     } else {
-        const ff2 w = ff2_div(u[1], u[0]);
-        const ff2 q = ff2_mul(u[1], w);
-        const ff2 p = ff2_mul(ff2_add(u[2], ff2_scale(q, -0.5f)), ff2{f2(args.g1_hi), f2(args.g1_lo)});
+        const ff2 w = A::div(u[1], u[0]);
+        const ff2 q = A::mul(u[1], w);
+        const ff2 p = A::mul(A::add(u[2], ff2_scale(q, -0.5f)), ff2{f2(args.g1_hi), f2(COMP ? args.g1_lo : 0.f)});
         f[0] = u[1];
-        f[1] = ff2_add(q, p);
-        f[2] = ff2_mul(ff2_add(u[2], p), w);
+        f[1] = A::add(q, p);
+        f[2] = A::mul(A::add(u[2], p), w);
     }
 }
 
@@ -193,9 +219,10 @@ constexpr int mixed2_smem_float2() {
 // of shared memory.  Returns the larger of the thread's two cell speeds
 // (cells outside the stage count as 0) and error bits; the caller
 // synchronises the block before rec is written again.
-template <int SYS, int P>
+template <int SYS, int P, bool COMP>
 __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, const StepArgs& args, float2* rec,
                                             float& speed, unsigned& err) {
+    using A = FF<COMP>;
     constexpr int NV = nvars(SYS);
     constexpr int K = P + 1;
     constexpr int NP = P + 2;
@@ -203,7 +230,7 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
     constexpr int W = kThreads + 1;  // row width of rec in float2
     const int t = threadIdx.x;
     const long long first_new = io.first_new;
-    const ff2 lam2{f2(lam.hi), f2(lam.lo)};
+    const ff2 lam2{f2(lam.hi), f2(COMP ? lam.lo : 0.f)};
 
     // ---- phase 1: parent records of slots t (lane x) and t + kThreads (lane y)
     {
@@ -217,7 +244,7 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
             const float* p0 = io.in32 + (long long)(v * NP + 0) * io.pitch;
             const float* p1 = io.in32 + (long long)(v * NP + 1) * io.pitch;
             ub[v].hi = f2(__ldg(p0 + pa), __ldg(p0 + pb));
-            ub[v].lo = f2(__ldg(p1 + pa), __ldg(p1 + pb));
+            ub[v].lo = COMP ? f2(__ldg(p1 + pa), __ldg(p1 + pb)) : f2(0.f);
             sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
                 const float* pk = io.in32 + (long long)(v * NP + k + 1) * io.pitch;
@@ -228,13 +255,13 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
                 constexpr int k = decltype(Ki)::value;
                 if constexpr ((k & 1) == 0) corr = fma(f2((float)(1.0 / ((k + 1.0) * cpow2(k)))), c[v][k], corr);
             });
-            u0[v] = ff2_add(ub[v], -corr);
+            u0[v] = A::add(ub[v], -corr);
             c[v][0] = u0[v].hi;
         });
         f2 X[NV][K][K], F0[NV][K];
         ck_table<SYS, P, f2>(c, lam2.hi, args, X, F0);
         ff2 f0[NV];
-        flux_ff2<SYS>(u0, args, f0);
+        flux_ff2<SYS, COMP>(u0, args, f0);
         sfor<0, NV>([&](auto V) {
             constexpr int v = decltype(V)::value;
             f2 fhigh(0.f);
@@ -242,25 +269,25 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
                 constexpr int b = decltype(Bi)::value;
                 fhigh = fma(f2((float)(1.0 / (b + 1.0))), F0[v][b], fhigh);
             });
-            const ff2 fbar = ff2_add(f0[v], fhigh);
+            const ff2 fbar = A::add(f0[v], fhigh);
             f2 dodd(0.f);
             sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
                 if constexpr (k & 1) dodd = fma(f2((float)(1.0 / ((k + 1.0) * cpow2(k)))), c[v][k], dodd);
             });
-            const ff2 g = ff2_add(ff2_mul(fbar, lam2), f2(0.5f) * dodd);
+            const ff2 g = A::add(A::mul(fbar, lam2), f2(0.5f) * dodd);
             const ff2 half_ub = ff2_scale(ub[v], 0.5f);
-            const ff2 A = ff2_add(half_ub, g);
-            const ff2 B = ff2_sub(half_ub, g);
+            const ff2 Ac = A::add(half_ub, g);
+            const ff2 Bc = A::sub(half_ub, g);
             f2 vt0(0.f);
             sfor<1, K>([&](auto Mi) { vt0 += X[v][0][decltype(Mi)::value]; });
-            const ff2 v0 = ff2_add(u0[v], vt0);
+            const ff2 v0 = A::add(u0[v], vt0);
             float2* r = rec + v * RV * W;
             f2 vals[RV];
-            vals[0] = A.hi;
-            vals[1] = A.lo;
-            vals[2] = B.hi;
-            vals[3] = B.lo;
+            vals[0] = Ac.hi;
+            vals[1] = Ac.lo;
+            vals[2] = Bc.hi;
+            vals[3] = Bc.lo;
             vals[4] = v0.hi;
             vals[5] = v0.lo;
             sfor<1, K>([&](auto Ki) {
@@ -291,16 +318,16 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
     sfor<0, NV>([&](auto V) {
         constexpr int v = decltype(V)::value;
         const float2* r = rec + v * RV * W;
-        const ff2 A{f2(r[0 * W + t]), f2(r[1 * W + t])};
-        const ff2 B{f2(r[2 * W + t + 1]), f2(r[3 * W + t + 1])};
+        const ff2 Ac{f2(r[0 * W + t]), f2(r[1 * W + t])};
+        const ff2 Bc{f2(r[2 * W + t + 1]), f2(r[3 * W + t + 1])};
         const ff2 vL0{f2(r[4 * W + t]), f2(r[5 * W + t])};
         const ff2 vR0{f2(r[4 * W + t + 1]), f2(r[5 * W + t + 1])};
-        ubn[v] = ff2_add(A, B);  // Eq. SubEq:1DIntegral
-        dl[v] = ff2_diff(ubn[v], vL0);
-        dr[v] = ff2_diff(vR0, ubn[v]);
+        ubn[v] = A::add(Ac, Bc);  // Eq. SubEq:1DIntegral
+        dl[v] = A::diff(ubn[v], vL0);
+        dr[v] = A::diff(vR0, ubn[v]);
         f2 vL[K], vR[K];
         vL[0] = f2(0.f);
-        vR[0] = ff2_diff(vR0, vL0);
+        vR[0] = A::diff(vR0, vL0);
         sfor<1, K>([&](auto Ki) {
             constexpr int k = decltype(Ki)::value;
             vL[k] = f2(r[(5 + k) * W + t]);
@@ -366,7 +393,7 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
     speed = fmaxf(va ? sp.x() : 0.f, vb ? sp.y() : 0.f);
 }
 
-template <int SYS, int P>
+template <int SYS, int P, bool COMP = true>
 __global__ void __launch_bounds__(kThreads, kMixedMinCtas) halfstep_mixed2(const StepArgs args) {
     __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
     const StepSize z = step_size(args);
@@ -374,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, kMixedMinCtas) halfstep_mixed2(const
                     (long long)blockIdx.x * kTileMixed, args.parity, args.bc};
     float speed = 0.f;
     unsigned err = 0u;
-    mixed_tile2<SYS, P>(io, ff_make(z.lam_hi, z.lam_lo), args, rec, speed, err);
+    mixed_tile2<SYS, P, COMP>(io, ff_make(z.lam_hi, z.lam_lo), args, rec, speed, err);
     finish_halfstep<float>(speed, err, z.dt, args);
 }
 

@@ -21,7 +21,7 @@ namespace wcc {
 
 enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
-enum { PREC_FP64 = 0, PREC_FP32_MIXED = 1 };
+enum { PREC_FP64 = 0, PREC_FP32_MIXED = 1, PREC_FP32 = 2 };
 
 // One CTA stages kThreads parent cells and produces kTile = kThreads - 1 new
 // cells: new cell t of the tile sits between parents t and t + 1.

@@ -19,7 +19,7 @@ HEADER = os.path.join(os.path.dirname(HERE), "include", "wcc.h")
 
 ADVECTION, BURGERS, EULER = 0, 1, 2
 PERIODIC, TRANSMISSIVE = 0, 1
-FP64, FP32_MIXED = 0, 1
+FP64, FP32_MIXED, FP32 = 0, 1, 2
 
 ERRORS = {
     -1: "WCC_E_INVAL", -2: "WCC_E_STATE", -3: "WCC_E_NOMEM", -4: "WCC_E_CUDA",

@@ -120,3 +120,24 @@ def fp32_pair_violation(pr, q_a, q_b, dts, *, floor=2e-6, perturb=1e-7, trials=3
     sc = scales(ref)
     bound = np.maximum(floor * sc[None, :, None], SCATTER_FACTOR * spread)
     return float(np.max(np.abs(q_a - q_b) / bound))
+
+
+def oracle_l1_spread(pr, dts, perturb, *, trials=3, seed=0):
+    """Largest L1 (centre point values, per variable over its scale) by
+    which the oracle's own trajectory over `dts` moves when its inputs are
+    perturbed by `perturb` relative noise."""
+    law = law_of(pr)
+
+    def run(q0):
+        s = oracle.Solver(law, q0, pr.dx)
+        s.step_dt(dts)
+        return s.q
+
+    ref = run(pr.q0)
+    sc = scales(ref)
+    rng = np.random.default_rng(seed)
+    worst = 0.0
+    for _ in range(trials):
+        q = run(pr.q0 * (1.0 + perturb * rng.standard_normal(pr.q0.shape)))
+        worst = max(worst, float(np.max(np.mean(np.abs(q[:, :, 0] - ref[:, :, 0]), axis=0) / sc)))
+    return ref, worst

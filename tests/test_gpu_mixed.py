@@ -117,3 +117,18 @@ def test_mixed_error_paths():
         s.set_initial(pr.q0)
         s.step(10, 0.2)
         s.synchronize()
+
+
+def test_fp32_uncompensated_variant_is_less_accurate():
+    # WCC_FP32 runs the same kernel without the float-float compensation; on
+    # a smooth wave its L1 error against the oracle is far above FP32-mixed's.
+    import math
+    pr = inputs.euler_density_wave(1024, 3)
+    amax = 1.0 + math.sqrt(1.4 / 0.8)
+    dts = oracle.constant_speed_dts(0.25, 0.25 * pr.dx / amax)
+    ref, _, _ = oracle_run(pr, dts)
+    q32, _, _, _ = gpu_run(pr, None, None, dts=dts, precision=wcc.FP32)
+    qm, _, _, _ = gpu_run(pr, None, None, dts=dts, precision=wcc.FP32_MIXED)
+    e32, em = l1_rel(q32, ref), l1_rel(qm, ref)
+    assert e32 < 1e-4
+    assert em < e32 / 20, (em, e32)
