@@ -24,6 +24,23 @@ thread_local std::string g_create_error;
 // Host layout [cell][var][k] of paper-scaled derivatives u_kx  <->  device
 // planes of Taylor coefficients e_k = u_kx / k!.  One thread per element:
 // reads of the host-layout array are coalesced.
+// 1/k! and 1/((k+1) 2^k) for k = 0..4, rounded once to double (the layout
+// conversions multiply by these instead of dividing: FP64 division is slow on
+// this GPU).
+__device__ __forceinline__ double inv_fact_k(int k) {
+    const double t[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+    return t[k];
+}
+__device__ __forceinline__ double fact_k(int k) {
+    const double t[5] = {1.0, 1.0, 2.0, 6.0, 24.0};
+    return t[k];
+}
+// weight of the Taylor coefficient e_k in the cell average (even k)
+__device__ __forceinline__ double avg_weight_k(int k) {
+    const double t[5] = {1.0, 0.0, 1.0 / 12.0, 0.0, 1.0 / 80.0};
+    return t[k];
+}
+
 __global__ void aos_to_planes_fp64(const double* __restrict__ aos, long long n, int nv, int K, long long pitch,
                                    double* __restrict__ planes) {
     const long long total = n * nv * K;
@@ -33,9 +50,7 @@ __global__ void aos_to_planes_fp64(const double* __restrict__ aos, long long n, 
         const long long rest = e / K;
         const int v = (int)(rest % nv);
         const long long cell = rest / nv;
-        double inv_fact = 1.0;
-        for (int j = 2; j <= k; ++j) inv_fact /= (double)j;
-        planes[(long long)(v * K + k) * pitch + cell] = aos[e] * inv_fact;
+        planes[(long long)(v * K + k) * pitch + cell] = aos[e] * inv_fact_k(k);
     }
 }
 
@@ -48,15 +63,13 @@ __global__ void planes_to_aos_fp64(const double* __restrict__ planes, long long 
         const long long rest = e / K;
         const int v = (int)(rest % nv);
         const long long cell = rest / nv;
-        double fact = 1.0;
-        for (int j = 2; j <= k; ++j) fact *= (double)j;
-        aos[e] = planes[(long long)(v * K + k) * pitch + cell] * fact;
+        aos[e] = planes[(long long)(v * K + k) * pitch + cell] * fact_k(k);
     }
 }
 
 // FP32-mixed / FP32: per (cell, var) the cell average (Eq. SubEq:1DCellAVG:
-// ubar = sum_{k even} u_kx / ((k+1)! 2^k)) split into a float-float pair,
-// and e_k = u_kx / k! rounded to FP32 for k >= 1.
+// ubar = sum_{k even} u_kx / ((k+1)! 2^k) = sum_{k even} e_k / ((k+1) 2^k))
+// split into a float-float pair, and e_k = u_kx / k! rounded to FP32 for k >= 1.
 __global__ void aos_to_planes_mixed(const double* __restrict__ aos, long long n, int nv, int K, long long pitch,
                                     float* __restrict__ planes, int keep_lo) {
     const int NP = K + 1;
@@ -66,12 +79,11 @@ __global__ void aos_to_planes_mixed(const double* __restrict__ aos, long long n,
         const int v = (int)(e % nv);
         const long long cell = e / nv;
         const double* q = aos + e * K;
-        double ubar = 0.0, fact = 1.0, p2 = 1.0;
-        for (int k = 0; k < K; ++k) {
-            if (k > 1) fact *= (double)k;
-            if ((k & 1) == 0) ubar += q[k] / (fact * (double)(k + 1) * p2);
-            if (k >= 1) planes[(long long)(v * NP + k + 1) * pitch + cell] = (float)(q[k] / fact);
-            p2 *= 2.0;
+        double ubar = q[0];
+        for (int k = 1; k < K; ++k) {
+            const double ek = q[k] * inv_fact_k(k);
+            if ((k & 1) == 0) ubar = fma(ek, avg_weight_k(k), ubar);
+            planes[(long long)(v * NP + k + 1) * pitch + cell] = (float)ek;
         }
         float hi, lo;
         split_double(ubar, hi, lo);
@@ -80,27 +92,45 @@ __global__ void aos_to_planes_mixed(const double* __restrict__ aos, long long n,
     }
 }
 
+// One thread per output double (consecutive threads write consecutive
+// doubles: coalesced, which matters when the destination is host memory).
 __global__ void planes_to_aos_mixed(const float* __restrict__ planes, long long n, int nv, int K, long long pitch,
                                     double* __restrict__ aos) {
     const int NP = K + 1;
-    const long long total = n * nv;
+    const long long total = n * nv * K;
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
          e += (long long)gridDim.x * blockDim.x) {
-        const int v = (int)(e % nv);
-        const long long cell = e / nv;
-        double* q = aos + e * K;
-        double u0 = (double)planes[(long long)(v * NP + 0) * pitch + cell] +
-                    (double)planes[(long long)(v * NP + 1) * pitch + cell];
-        double fact = 1.0, p2 = 2.0;
-        for (int k = 1; k < K; ++k) {
-            fact *= (double)k;
-            p2 *= 2.0;
-            const double ek = (double)planes[(long long)(v * NP + k + 1) * pitch + cell];
-            if ((k & 1) == 0) u0 -= ek / ((double)(k + 1) * (p2 / 2.0));
-            q[k] = ek * fact;
+        const int k = (int)(e % K);
+        const long long rest = e / K;
+        const int v = (int)(rest % nv);
+        const long long cell = rest / nv;
+        double out;
+        if (k == 0) {
+            out = (double)planes[(long long)(v * NP + 0) * pitch + cell] +
+                  (double)planes[(long long)(v * NP + 1) * pitch + cell];
+            for (int j = 2; j < K; j += 2)
+                out = fma(-(double)planes[(long long)(v * NP + j + 1) * pitch + cell], avg_weight_k(j), out);
+        } else {
+            out = (double)planes[(long long)(v * NP + k + 1) * pitch + cell] * fact_k(k);
         }
-        q[0] = u0;
+        aos[e] = out;
     }
+}
+
+// Device view of a caller's host buffer: the buffer itself when it is pinned
+// and mapped into the device address space (the conversion kernels then read
+// or write it directly), else nullptr (staging copy).
+const void* mapped_host_view(const void* p) {
+#if defined(WCC_ZERO_COPY) && WCC_ZERO_COPY == 0
+    return nullptr;
+#endif
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
+    return nullptr;
 }
 
 unsigned elementwise_grid(long long total) {
@@ -415,16 +445,21 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     if (!dofs) return fail(h, WCC_E_INVAL, "dofs is NULL");
     const long long n = stage_cells(h, 0);
     if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match cells*nv*(P+1) of an integer stage");
-    WCC_CHECK(h, cudaMemcpyAsync(h->staging, dofs, (size_t)count * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+    const double* src = static_cast<const double*>(mapped_host_view(dofs));
+    if (!src) {
+        WCC_CHECK(h, cudaMemcpyAsync(h->staging, dofs, (size_t)count * sizeof(double), cudaMemcpyHostToDevice,
+                                     h->stream));
+        src = h->staging;
+    }
     h->cur = 0;
     h->parity = 0;
     h->steps = 0;
     const bool mixed = h->opt.precision != WCC_FP64;
     if (mixed)
         aos_to_planes_mixed<<<elementwise_grid(n * h->nv), 256, 0, h->stream>>>(
-            h->staging, n, h->nv, h->K, h->pitch, h->s32[0], h->opt.precision == WCC_FP32_MIXED);
+            src, n, h->nv, h->K, h->pitch, h->s32[0], h->opt.precision == WCC_FP32_MIXED);
     else
-        aos_to_planes_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->staging, n, h->nv, h->K, h->pitch,
+        aos_to_planes_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(src, n, h->nv, h->K, h->pitch,
                                                                               h->s64[0]);
     WCC_CHECK(h, cudaGetLastError());
     WCC_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
@@ -506,15 +541,20 @@ int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     const long long n = stage_cells(h, h->parity);
     if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match the current stage");
+    double* dst = static_cast<double*>(const_cast<void*>(mapped_host_view(dofs)));
+    const bool direct = dst != nullptr;
+    if (!direct) dst = h->staging;
     if (h->opt.precision != WCC_FP64)
-        planes_to_aos_mixed<<<elementwise_grid(n * h->nv), 256, 0, h->stream>>>(h->s32[h->cur], n, h->nv, h->K,
-                                                                                 h->pitch, h->staging);
+        planes_to_aos_mixed<<<elementwise_grid(count), 256, 0, h->stream>>>(h->s32[h->cur], n, h->nv, h->K,
+                                                                            h->pitch, dst);
     else
         planes_to_aos_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->s64[h->cur], n, h->nv, h->K,
-                                                                               h->pitch, h->staging);
+                                                                               h->pitch, dst);
     WCC_CHECK(h, cudaGetLastError());
     h->launches += 1;
-    WCC_CHECK(h, cudaMemcpyAsync(dofs, h->staging, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    if (!direct)
+        WCC_CHECK(h, cudaMemcpyAsync(dofs, h->staging, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost,
+                                     h->stream));
     DevState s;
     return read_state(h, &s);
 }

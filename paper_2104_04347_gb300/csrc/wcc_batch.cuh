@@ -44,7 +44,7 @@ struct BatchArgs {
 
 
 template <int SYS, int PA, int PB>
-__global__ void __launch_bounds__(kThreads, kMixedMinCtas) batch_mixed(const BatchArgs b) {
+__global__ void __launch_bounds__(kThreadsMixed, kMixedMinCtas) batch_mixed(const BatchArgs b) {
     constexpr int SA = mixed2_smem_float2<SYS, PA>();
     constexpr int SB = mixed2_smem_float2<SYS, PB>();
     __shared__ float2 rec[SA > SB ? SA : SB];
@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(kThreads, kMixedMinCtas) batch_mixed(const Bat
             mixed_tile2<SYS, PA, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
         else
             mixed_tile2<SYS, PB, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
-        reduce_and_finish<float>(speed, err, z.dt, st, ntiles, b.hist + (long long)i * b.hist_cap, b.hist_cap,
+        reduce_and_finish<float, kThreadsMixed>(speed, err, z.dt, st, ntiles, b.hist + (long long)i * b.hist_cap, b.hist_cap,
                                  b.parity, 1, b.phys.cfl, I.dx);
     }
 }
@@ -128,13 +128,17 @@ __global__ void __launch_bounds__(kThreads) batch_convert(const BatchArgs b, dou
         double* q0 = aos + I.aos_offset[b.parity] + c * NV * K;
         for (int v = 0; v < NV; ++v) {
             double* q = q0 + v * K;
+            // 1/k!, k! and the cell-average weights 1/((k+1) 2^k) as constants
+            // (no FP64 division)
+            const double inv_fact[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+            const double fact[5] = {1.0, 1.0, 2.0, 6.0, 24.0};
+            const double avg_w[5] = {1.0, 0.0, 1.0 / 12.0, 0.0, 1.0 / 80.0};
             if (to_planes) {
-                double ubar = 0.0, fact = 1.0, p2 = 1.0;
-                for (int k = 0; k < K; ++k) {
-                    if (k > 1) fact *= (double)k;
-                    if ((k & 1) == 0) ubar += q[k] / (fact * (double)(k + 1) * p2);
-                    if (k >= 1) pl[(long long)(v * NP + k + 1) * pitch + c] = (float)(q[k] / fact);
-                    p2 *= 2.0;
+                double ubar = q[0];
+                for (int k = 1; k < K; ++k) {
+                    const double ek = q[k] * inv_fact[k];
+                    if ((k & 1) == 0) ubar = fma(ek, avg_w[k], ubar);
+                    pl[(long long)(v * NP + k + 1) * pitch + c] = (float)ek;
                 }
                 float hi, lo;
                 split_double(ubar, hi, lo);
@@ -142,13 +146,10 @@ __global__ void __launch_bounds__(kThreads) batch_convert(const BatchArgs b, dou
                 pl[(long long)(v * NP + 1) * pitch + c] = lo;
             } else {
                 double u0 = (double)pl[(long long)(v * NP) * pitch + c] + (double)pl[(long long)(v * NP + 1) * pitch + c];
-                double fact = 1.0, p2 = 2.0;
                 for (int k = 1; k < K; ++k) {
-                    fact *= (double)k;
-                    p2 *= 2.0;
                     const double ek = (double)pl[(long long)(v * NP + k + 1) * pitch + c];
-                    if ((k & 1) == 0) u0 -= ek / ((double)(k + 1) * (p2 / 2.0));
-                    q[k] = ek * fact;
+                    if ((k & 1) == 0) u0 = fma(-ek, avg_w[k], u0);
+                    q[k] = ek * fact[k];
                 }
                 q[0] = u0;
             }

@@ -35,6 +35,7 @@ struct f2 {
 };
 
 __device__ __forceinline__ f2 operator+(f2 a, f2 b) { return f2(__fadd2_rn(a.v, b.v)); }
+// (negations fold into the paired add as operand modifiers)
 __device__ __forceinline__ f2 operator-(f2 a) { return f2(-a.v.x, -a.v.y); }
 __device__ __forceinline__ f2 operator-(f2 a, f2 b) { return f2(__fadd2_rn(a.v, make_float2(-b.v.x, -b.v.y))); }
 __device__ __forceinline__ f2 operator*(f2 a, f2 b) { return f2(__fmul2_rn(a.v, b.v)); }
@@ -42,10 +43,22 @@ __device__ __forceinline__ f2& operator+=(f2& a, f2 b) { a = a + b; return a; }
 __device__ __forceinline__ f2& operator-=(f2& a, f2 b) { a = a - b; return a; }
 __device__ __forceinline__ f2& operator*=(f2& a, f2 b) { a = a * b; return a; }
 __device__ __forceinline__ f2 fma(f2 a, f2 b, f2 c) { return f2(__ffma2_rn(a.v, b.v, c.v)); }
-__device__ __forceinline__ f2 recip(f2 a) { return f2(__frcp_rn(a.v.x), __frcp_rn(a.v.y)); }
+// Estimate of 1/a in each lane from the special-function unit (relative error
+// about 2^-23): enough for quantities that only need FP32 accuracy.  For
+// normal a only (densities); a subnormal a gives inf.
+__device__ __forceinline__ f2 rcp_approx(f2 a) { return f2(__fdividef(1.f, a.v.x), __fdividef(1.f, a.v.y)); }
+// 1/a to within an ulp: the estimate refined by one Newton-Raphson step,
+// r + r (1 - a r), in paired instructions.
+__device__ __forceinline__ f2 recip(f2 a) {
+    const f2 r = rcp_approx(a);
+    return fma(r, fma(-a, r, f2(1.f)), r);
+}
 __device__ __forceinline__ f2 fabs(f2 a) { return f2(fabsf(a.v.x), fabsf(a.v.y)); }
 __device__ __forceinline__ f2 fmin(f2 a, f2 b) { return f2(fminf(a.v.x, b.v.x), fminf(a.v.y, b.v.y)); }
 __device__ __forceinline__ f2 fmax(f2 a, f2 b) { return f2(fmaxf(a.v.x, b.v.x), fmaxf(a.v.y, b.v.y)); }
+// a / b lane by lane.  Not a * (1/b): the limiter divides numbers that may
+// both be subnormal (its epsilon defaults to 1e-40), whose reciprocal
+// overflows although the quotient does not.
 __device__ __forceinline__ f2 fdiv_fast(f2 a, f2 b) {
     return f2(__fdividef(a.v.x, b.v.x), __fdividef(a.v.y, b.v.y));
 }

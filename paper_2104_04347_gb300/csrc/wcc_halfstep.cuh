@@ -75,11 +75,11 @@ __device__ __forceinline__ void finalize_state(DevState* st, bool f32, double dt
 // Block-wide max of the speed (in the kernel's compute type T), one atomic
 // per CTA into st, then count the CTA as done; the CTA that completes the
 // `ctas` of this state does its bookkeeping.  Synchronises the block.
-template <class T>
+template <class T, int NT = kThreads>
 __device__ __forceinline__ void reduce_and_finish(T speed, unsigned err, double dt, DevState* st, long long ctas,
                                                   double* hist, long long hist_cap, int parity, int cfl_mode,
                                                   double cfl, double dx) {
-    __shared__ T s_max[kThreads / 32];
+    __shared__ T s_max[NT / 32];
     __shared__ unsigned s_err;
     __shared__ int s_last;
     if (threadIdx.x == 0) s_err = 0u;
@@ -96,7 +96,7 @@ __device__ __forceinline__ void reduce_and_finish(T speed, unsigned err, double 
     if (threadIdx.x == 0) {
         T m = s_max[0];
 #pragma unroll
-        for (int w = 1; w < kThreads / 32; ++w) m = fmax(m, s_max[w]);
+        for (int w = 1; w < NT / 32; ++w) m = fmax(m, s_max[w]);
         if constexpr (sizeof(T) == 8) {
             if (m > 0.0) atomicMax(&st->amax_bits[parity ^ 1], (unsigned long long)__double_as_longlong(m));
         } else {
@@ -114,10 +114,10 @@ __device__ __forceinline__ void reduce_and_finish(T speed, unsigned err, double 
     }
 }
 
-template <class T>
+template <class T, int NT = kThreads>
 __device__ __forceinline__ void finish_halfstep(T speed, unsigned err, double dt, const StepArgs& args) {
-    reduce_and_finish<T>(speed, err, dt, args.st, (long long)gridDim.x, args.hist, args.hist_cap, args.parity,
-                         args.cfl_mode, args.cfl, args.dx);
+    reduce_and_finish<T, NT>(speed, err, dt, args.st, (long long)gridDim.x, args.hist, args.hist_cap, args.parity,
+                             args.cfl_mode, args.cfl, args.dx);
 }
 
 template <int SYS, int P>

@@ -1,29 +1,65 @@
-// wcc_mixed2.cuh -- the FP32-mixed half-step with two cells per thread.
+// wcc_mixed2.cuh -- the FP32-mixed half-step (no FP64 instruction in the
+// per-cell work), two cells per thread.
 //
-// Same arithmetic as the scalar FP32-mixed formulation (float-float cell
-// averages, leading flux and vertex values; FP32 for the rest; limiter in
-// deviation form), but every thread carries a pair of cells in the two lanes
-// of the paired FP32 instructions: lane x works on parent t / new cell t of
-// the tile, lane y on parent t + kThreads / new cell t + kThreads.  A tile
-// has 2 kThreads parents and kTileMixed = 2 kThreads - 1 new cells.  Parent
-// records are stored interleaved ((slot t, slot t + kThreads) at index t) so
-// that a new cell's two parents are one 64-bit shared-memory load each.
+// Storage per variable: the cell average ubar as a float-float pair (two FP32
+// planes, hi and lo) and the Taylor coefficients e_1..e_P as FP32 planes
+// (e_k = dx^k u^(k) / k!; the scaled form keeps them in range).  Arithmetic:
+//   * float-float (compensated FP32) where a result is a small difference of
+//     O(1) quantities or must conserve: the leading flux term f(u_0), each
+//     parent's share A = ubar / 2 + lam fbar + dodd / 2 of its average, the
+//     new cell average A[left] + (ubar - A)[right] (Eq. SubEq:1DIntegral);
+//   * FP32 for everything else: the Cauchy-Kovalewski table, the higher flux
+//     and vertex terms, derivatives, the limiter.  The vertex values enter
+//     only as ubar - u_{i-1/2}, u_{i+1/2} - ubar (Eqs. SubEq:1DU12,
+//     1DHighOrderWeights) and e_1, each formed from Sterbenz-exact
+//     differences of float-float averages plus FP32 deviations.
+// Because the limited polynomial keeps the cell average (Eq.
+// 1DLimitedPolynomial), the limiter works on deviations from ubar only and
+// never rounds ubar; sums of ubar telescope up to float-float rounding.  The
+// limiter weights are evaluated in a scale-free form (ratios to the smallest
+// denominator), so the tiny epsilon of the paper neither overflows nor
+// underflows FP32.
+//
+// Every thread carries a pair of cells in the two lanes of the paired FP32
+// instructions: lane x works on parent t / new cell t of the tile, lane y on
+// parent t + kThreadsMixed / new cell t + kThreadsMixed.  A tile has
+// 2 kThreadsMixed parents and kTileMixed = 2 kThreadsMixed - 1 new cells.
+// Parent records are stored interleaved ((slot t, slot t + kThreadsMixed) at
+// index t) so that a new cell's two parents are one 64-bit shared-memory load
+// each.
 #pragma once
 
 #include "wcc_f2.cuh"
 #include "wcc_ff.cuh"
-#include "wcc_halfstep_mixed.cuh"
+#include "wcc_halfstep.cuh"
 
 namespace wcc {
 
-constexpr int kTileMixed = 2 * kThreads - 1;
+// Threads per CTA of the FP32-mixed kernels (two cells each).
+#ifndef WCC_MIXED_THREADS
+#define WCC_MIXED_THREADS 128
+#endif
+constexpr int kThreadsMixed = WCC_MIXED_THREADS;
+constexpr int kTileMixed = 2 * kThreadsMixed - 1;
 
 // Resident CTAs per SM the FP32-mixed kernels are compiled for (register
-// budget 65536 / (kThreads * kMixedMinCtas) per thread).
+// budget 65536 / (kThreadsMixed * kMixedMinCtas) per thread).
 #ifndef WCC_MIXED_MIN_CTAS
 #define WCC_MIXED_MIN_CTAS 5
 #endif
 constexpr int kMixedMinCtas = WCC_MIXED_MIN_CTAS;
+
+// Where one tile reads and writes (one stage of one grid or batch instance).
+struct TileIO {
+    const float* in32;
+    float* out32;
+    long long pitch;
+    long long n_old;
+    long long n_new;
+    long long first_new;
+    int parity;
+    int bc;
+};
 
 // ------------------------------------------------------ float-float pairs
 
@@ -54,6 +90,13 @@ __device__ __forceinline__ ff2 ff2_add(ff2 a, f2 b) {
     return fast_two_sum2(s.hi, s.lo + a.lo);
 }
 
+// a + b where b is itself only FP32-accurate: Fast2Sum in place of TwoSum.
+// When |b| > |a.hi| the low bits lost are below ulp(b), within b's own error.
+__device__ __forceinline__ ff2 ff2_add_fp32(ff2 a, f2 b) {
+    const ff2 s = fast_two_sum2(a.hi, b);
+    return fast_two_sum2(s.hi, s.lo + a.lo);
+}
+
 __device__ __forceinline__ ff2 ff2_neg(ff2 a) { return ff2{-a.hi, -a.lo}; }
 __device__ __forceinline__ ff2 ff2_sub(ff2 a, ff2 b) { return ff2_add(a, ff2_neg(b)); }
 __device__ __forceinline__ ff2 ff2_scale(ff2 a, float pow2) { return ff2{a.hi * f2(pow2), a.lo * f2(pow2)}; }
@@ -64,14 +107,17 @@ __device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
     return fast_two_sum2(p, fma(a.hi, b.lo, fma(a.lo, b.hi, e)));
 }
 
+// a / b for a normal b (a density): q1 = a.hi / b.hi, then the remainder
+// a - b q1 -- its leading part a.hi - b.hi q1 is exact (q1 is close to the
+// quotient, Sterbenz) and only needs FP32 accuracy -- divided by b.hi for
+// the correction q2.  One reciprocal estimate serves both quotients.
 __device__ __forceinline__ ff2 ff2_div(ff2 a, ff2 b) {
-    const f2 q1 = fdiv_fast(a.hi, b.hi);
+    const f2 rb = rcp_approx(b.hi);
+    const f2 q1 = a.hi * rb;
     const f2 p = b.hi * q1;
-    const f2 e = fma(b.hi, q1, -p);
-    const ff2 bq = fast_two_sum2(p, fma(b.lo, q1, e));
-    const ff2 r = ff2_sub(a, bq);
-    const f2 q2 = fdiv_fast(r.hi, b.hi);
-    return fast_two_sum2(q1, q2);
+    const f2 e = fma(b.hi, q1, -p);  // b.hi q1 = p + e exactly
+    const f2 rem = (a.hi - p) + (a.lo - fma(b.lo, q1, e));
+    return fast_two_sum2(q1, rem * rb);
 }
 
 // (a - b) rounded to a pair of floats, a and b close (Sterbenz on the hi parts)
@@ -84,7 +130,7 @@ __device__ __forceinline__ f2 ff2_diff(ff2 a, ff2 b) { return (a.hi - b.hi) + (a
 template <bool COMP>
 struct FF {
     static __device__ __forceinline__ ff2 add(ff2 a, ff2 b) { return ff2_add(a, b); }
-    static __device__ __forceinline__ ff2 add(ff2 a, f2 b) { return ff2_add(a, b); }
+    static __device__ __forceinline__ ff2 add(ff2 a, f2 b) { return ff2_add_fp32(a, b); }
     static __device__ __forceinline__ ff2 sub(ff2 a, ff2 b) { return ff2_sub(a, b); }
     static __device__ __forceinline__ ff2 mul(ff2 a, ff2 b) { return ff2_mul(a, b); }
     static __device__ __forceinline__ ff2 div(ff2 a, ff2 b) { return ff2_div(a, b); }
@@ -101,6 +147,19 @@ struct FF<false> {
     static __device__ __forceinline__ ff2 div(ff2 a, ff2 b) { return mk(fdiv_fast(a.hi, b.hi)); }
     static __device__ __forceinline__ f2 diff(ff2 a, ff2 b) { return a.hi - b.hi; }
 };
+
+// Cell average minus centre value of the Taylor polynomial with coefficients
+// c[1..P] (Eq. 1DPolynomial_Space integrated over the cell): sum over even
+// k >= 2 of c_k / ((k + 1) 2^k).
+template <int P>
+__device__ __forceinline__ f2 average_minus_centre(const f2 (&c)[P + 1]) {
+    f2 s(0.f);
+    sfor<2, P + 1>([&](auto Ki) {
+        constexpr int k = decltype(Ki)::value;
+        if constexpr ((k & 1) == 0) s = fma(f2((float)(1.0 / ((k + 1.0) * cpow2(k)))), c[k], s);
+    });
+    return s;
+}
 
 template <int SYS, bool COMP>
 __device__ __forceinline__ void flux_ff2(const ff2 (&u)[nvars(SYS)], const StepArgs& args, ff2 (&f)[nvars(SYS)]) {
@@ -121,8 +180,11 @@ __device__ __forceinline__ void flux_ff2(const ff2 (&u)[nvars(SYS)], const StepA
 
 // ------------------------------------------------------ limiter, paired
 
-// Normalised weights in scale-free form (see weights_hi_f32); w0 is formed as
-// 1 - w1 - w2 so that it is exactly 1 whenever the other two vanish.
+// Normalised weights for P >= 2 (Eq. 1DHighOrderWeights), scale-free:
+// w0 ~ 1 + (st/d0)^alpha, w_m ~ (st/d_m)^alpha with d = beta^2 + eps, all
+// multiplied through by (d_min/st)^alpha, so every ratio is at most 1 (st = 0
+// makes the first ratio +inf, clamped to 1e18).  w0 is formed as 1 - w1 - w2
+// so that it is exactly 1 whenever the other two vanish.
 __device__ __forceinline__ void weights_hi_f2(f2 b0, f2 b1, f2 b2, f2 st, const StepArgs& args, f2& w0, f2& w1,
                                               f2& w2) {
     const f2 eps(args.eps_f), tiny(1.4e-45f);
@@ -147,6 +209,8 @@ __device__ __forceinline__ void weights_hi_f2(f2 b0, f2 b1, f2 b2, f2 st, const 
     w0 = f2(1.f) - (w1 + w2);
 }
 
+// Normalised weights for P = 1 (Eq. 1D2ndOrderWeights): w_m proportional to
+// (1 / (beta_m + eps))^alpha, evaluated as ((beta_min + eps) / (beta_m + eps))^alpha <= 1.
 __device__ __forceinline__ void weights_p1_f2(f2 b0, f2 b1, f2 b2, const StepArgs& args, f2& w0, f2& w1, f2& w2) {
     const f2 eps(args.eps_f), tiny(1.4e-45f);
     const f2 d0 = fmax(b0 + eps, tiny), d1 = fmax(b1 + eps, tiny), d2 = fmax(b2 + eps, tiny);
@@ -169,7 +233,9 @@ __device__ __forceinline__ void weights_p1_f2(f2 b0, f2 b1, f2 b2, const StepArg
     w0 = f2(1.f) - (w1 + w2);
 }
 
-// Limiter of Sec. 2.2 in deviation form (see limit_deviation_f32), paired.
+// Limiter of Sec. 2.2 in deviation form, paired.  d[0] = u_0(centre) - ubar,
+// d[1..P] = Taylor coefficients; dl = ubar - u_{i-1/2}, dr = u_{i+1/2} - ubar.
+// On return d holds the same quantities of the limited polynomial.
 template <int P>
 __device__ __forceinline__ void limit_deviation_f2(f2 (&d)[P + 1], f2 dl, f2 dr, const StepArgs& args) {
     const f2 s1 = f2(2.f) * dl, s2 = f2(2.f) * dr;
@@ -206,15 +272,63 @@ __device__ __forceinline__ void limit_deviation_f2(f2 (&d)[P + 1], f2 dl, f2 dr,
     sfor<2, P + 1>([&](auto Ki) { d[decltype(Ki)::value] *= w0; });
 }
 
+// ------------------------------------------------------ Euler characteristics, paired
+
+// Eigenvectors of the Euler flux Jacobian at a state (the L and R of
+// euler_eigen, Sec. 4) kept as the scalars their products need:
+//   L d = (X - Y, d_0 - 2 X, X + Y),  X = (b1/2) (u^2/2 d_0 - u d_1 + d_2),
+//                                     Y = (1/(2c)) (d_1 - u d_0),
+//   R w = (s + w_1, u (s + w_1) + m, H s + u m + u^2/2 w_1),
+//         s = w_0 + w_2,  m = c (w_2 - w_0),
+// with b1 = (gamma - 1) / c^2 and H = (E + p) / rho.  Eight paired
+// instructions per product and seven pairs of registers for the basis.
+struct EulerChar2 {
+    f2 u, nu, hu2, c, H, b1h, ich;
+
+    __device__ __forceinline__ void left(f2 d0, f2 d1, f2 d2, f2 (&w)[3]) const {
+        const f2 X = b1h * fma(nu, d1, fma(hu2, d0, d2));
+        const f2 Y = ich * fma(nu, d0, d1);
+        w[0] = X - Y;
+        w[1] = fma(f2(-2.f), X, d0);
+        w[2] = X + Y;
+    }
+    __device__ __forceinline__ void right(f2 w0, f2 w1, f2 w2, f2& d0, f2& d1, f2& d2) const {
+        const f2 s = w0 + w2;
+        const f2 m = c * (w2 - w0);
+        d0 = s + w1;
+        d1 = fma(u, d0, m);
+        d2 = fma(H, s, fma(u, m, hu2 * w1));
+    }
+};
+
+// Basis at the conserved state U; false for a non-positive density or
+// pressure.  Same arithmetic as euler_eigen for the scalars it shares.
+__device__ __forceinline__ bool euler_char(const f2 (&U)[3], f2 gamma, EulerChar2& E) {
+    const f2 irho = recip(U[0]);
+    const f2 u = U[1] * irho;
+    const f2 g1 = gamma - f2(1.f);
+    const f2 p = g1 * fma(f2(-0.5f) * U[1], u, U[2]);
+    const f2 c2 = gamma * p * irho;
+    const f2 ic = rsqrt_approx(c2);
+    E.u = u;
+    E.nu = -u;
+    E.hu2 = f2(0.5f) * u * u;
+    E.c = c2 * ic;
+    E.H = (U[2] + p) * irho;
+    E.b1h = f2(0.5f) * g1 * ic * ic;
+    E.ich = f2(0.5f) * ic;
+    return all_pos(U[0]) && all_pos(p);
+}
+
 // ------------------------------------------------------ the paired tile
 
 template <int SYS, int P>
 constexpr int mixed2_smem_float2() {
-    return nvars(SYS) * (6 + P) * (kThreads + 1);
+    return nvars(SYS) * (5 + P) * (kThreadsMixed + 1);
 }
 
 // One tile of the FP32-mixed half-step, two cells per thread: parents
-// io.first_new + s - parity for slots s = 0..2 kThreads - 1, new cells
+// io.first_new + s - parity for slots s = 0..2 kThreadsMixed - 1, new cells
 // io.first_new + c for c = 0..kTileMixed - 1.  rec: mixed2_smem_float2 float2
 // of shared memory.  Returns the larger of the thread's two cell speeds
 // (cells outside the stage count as 0) and error bits; the caller
@@ -226,17 +340,17 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
     constexpr int NV = nvars(SYS);
     constexpr int K = P + 1;
     constexpr int NP = P + 2;
-    constexpr int RV = 6 + P;
-    constexpr int W = kThreads + 1;  // row width of rec in float2
+    constexpr int RV = 5 + P;
+    constexpr int W = kThreadsMixed + 1;  // row width of rec in float2
     const int t = threadIdx.x;
     const long long first_new = io.first_new;
     const ff2 lam2{f2(lam.hi), f2(COMP ? lam.lo : 0.f)};
 
-    // ---- phase 1: parent records of slots t (lane x) and t + kThreads (lane y)
+    // ---- phase 1: parent records of slots t (lane x) and t + kThreadsMixed (lane y)
     {
         const long long base = first_new + t - (io.parity ? 1 : 0);
         const long long pa = parent_index(base, io.n_old, io.bc);
-        const long long pb = parent_index(base + kThreads, io.n_old, io.bc);
+        const long long pb = parent_index(base + kThreadsMixed, io.n_old, io.bc);
         f2 c[NV][K];
         ff2 ub[NV], u0[NV];
         sfor<0, NV>([&](auto V) {
@@ -250,18 +364,24 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
                 const float* pk = io.in32 + (long long)(v * NP + k + 1) * io.pitch;
                 c[v][k] = f2(__ldg(pk + pa), __ldg(pk + pb));
             });
-            f2 corr(0.f);
-            sfor<2, K>([&](auto Ki) {
-                constexpr int k = decltype(Ki)::value;
-                if constexpr ((k & 1) == 0) corr = fma(f2((float)(1.0 / ((k + 1.0) * cpow2(k)))), c[v][k], corr);
-            });
-            u0[v] = A::add(ub[v], -corr);
+            u0[v] = A::add(ub[v], -average_minus_centre<P>(c[v]));
             c[v][0] = u0[v].hi;
         });
         f2 X[NV][K][K], F0[NV][K];
         ck_table<SYS, P, f2>(c, lam2.hi, args, X, F0);
         ff2 f0[NV];
         flux_ff2<SYS, COMP>(u0, args, f0);
+        // Record of the parent (Eqs. Cal1DFlux, SubEq:1DCellAVGR/L,
+        // SubEq:Cal_1D_Derivatives_4): its cell average ubar and
+        //   A   = ubar / 2 + g,  g = lam fbar + dodd / 2, the part of ubar that
+        //         goes to the new cell on its right (float-float; the new cell
+        //         on its left gets B = ubar - A, so the scheme stays
+        //         conservative to float-float rounding),
+        //   dev = v_0 - ubar, the centre value at the new time level minus the
+        //         cell average,
+        //   and the higher vertex coefficients sum_m X[k][m], k >= 1.
+        // g is lam f(u_0) in float-float plus the FP32 rest
+        // h = lam (fbar - f(u_0)) + dodd / 2.
         sfor<0, NV>([&](auto V) {
             constexpr int v = decltype(V)::value;
             f2 fhigh(0.f);
@@ -269,69 +389,70 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
                 constexpr int b = decltype(Bi)::value;
                 fhigh = fma(f2((float)(1.0 / (b + 1.0))), F0[v][b], fhigh);
             });
-            const ff2 fbar = A::add(f0[v], fhigh);
             f2 dodd(0.f);
             sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
                 if constexpr (k & 1) dodd = fma(f2((float)(1.0 / ((k + 1.0) * cpow2(k)))), c[v][k], dodd);
             });
-            const ff2 g = A::add(A::mul(fbar, lam2), f2(0.5f) * dodd);
-            const ff2 half_ub = ff2_scale(ub[v], 0.5f);
-            const ff2 Ac = A::add(half_ub, g);
-            const ff2 Bc = A::sub(half_ub, g);
+            const f2 h = fma(lam2.hi, fhigh, f2(0.5f) * dodd);
+            const ff2 Ac = A::add(ff2_scale(ub[v], 0.5f), A::add(A::mul(f0[v], lam2), h));
             f2 vt0(0.f);
             sfor<1, K>([&](auto Mi) { vt0 += X[v][0][decltype(Mi)::value]; });
-            const ff2 v0 = A::add(u0[v], vt0);
             float2* r = rec + v * RV * W;
             f2 vals[RV];
-            vals[0] = Ac.hi;
-            vals[1] = Ac.lo;
-            vals[2] = Bc.hi;
-            vals[3] = Bc.lo;
-            vals[4] = v0.hi;
-            vals[5] = v0.lo;
+            vals[0] = ub[v].hi;
+            vals[1] = ub[v].lo;
+            vals[2] = Ac.hi;
+            vals[3] = Ac.lo;
+            vals[4] = vt0 - average_minus_centre<P>(c[v]);
             sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
                 f2 s = X[v][k][0];
                 sfor<1, K - k>([&](auto Mi) { s += X[v][k][decltype(Mi)::value]; });
-                vals[5 + k] = s;
+                vals[4 + k] = s;
             });
             sfor<0, RV>([&](auto Ri) {
                 constexpr int row = decltype(Ri)::value;
-                r[row * W + t] = vals[row].v;
-                // slot kThreads (lane y of thread 0) is also the right parent of
-                // new cell kThreads - 1 (lane x of the last thread); its y lane
-                // repeats the value so that the unused lane sees real data
-                if (t == 0) r[row * W + kThreads] = make_float2(vals[row].y(), vals[row].y());
+                if constexpr (COMP || (row != 1 && row != 3)) {
+                    r[row * W + t] = vals[row].v;
+                    // slot kThreadsMixed (lane y of thread 0) is also the right parent of
+                    // new cell kThreadsMixed - 1 (lane x of the last thread); its y lane
+                    // repeats the value so that the unused lane sees real data
+                    if (t == 0) r[row * W + kThreadsMixed] = make_float2(vals[row].y(), vals[row].y());
+                }
             });
         });
     }
     __syncthreads();
 
-    // ---- phase 2: new cells t (lane x) and t + kThreads (lane y)
+    // ---- phase 2: new cells t (lane x) and t + kThreadsMixed (lane y)
     const long long ia = first_new + t;
-    const long long ib = first_new + kThreads + t;
+    const long long ib = first_new + kThreadsMixed + t;
     const bool va = ia < io.n_new;
-    const bool vb = (t < kThreads - 1) && ib < io.n_new;
+    const bool vb = (t < kThreadsMixed - 1) && ib < io.n_new;
     ff2 ubn[NV];
     f2 d[NV][K], dl[NV], dr[NV];
     sfor<0, NV>([&](auto V) {
         constexpr int v = decltype(V)::value;
         const float2* r = rec + v * RV * W;
-        const ff2 Ac{f2(r[0 * W + t]), f2(r[1 * W + t])};
-        const ff2 Bc{f2(r[2 * W + t + 1]), f2(r[3 * W + t + 1])};
-        const ff2 vL0{f2(r[4 * W + t]), f2(r[5 * W + t])};
-        const ff2 vR0{f2(r[4 * W + t + 1]), f2(r[5 * W + t + 1])};
-        ubn[v] = A::add(Ac, Bc);  // Eq. SubEq:1DIntegral
-        dl[v] = A::diff(ubn[v], vL0);
-        dr[v] = A::diff(vR0, ubn[v]);
+        const f2 zero(0.f);
+        const ff2 uL{f2(r[0 * W + t]), COMP ? f2(r[1 * W + t]) : zero};
+        const ff2 uR{f2(r[0 * W + t + 1]), COMP ? f2(r[1 * W + t + 1]) : zero};
+        const ff2 AL{f2(r[2 * W + t]), COMP ? f2(r[3 * W + t]) : zero};
+        const ff2 AR{f2(r[2 * W + t + 1]), COMP ? f2(r[3 * W + t + 1]) : zero};
+        const f2 eL(r[4 * W + t]), eR(r[4 * W + t + 1]);
+        ubn[v] = A::add(AL, A::sub(uR, AR));  // Eq. SubEq:1DIntegral: A_L + B_R
+        // vertex values v_L = ubar_L + dev_L, v_R = ubar_R + dev_R, taken
+        // relative to the new average through differences of close numbers
+        dl[v] = A::diff(ubn[v], uL) - eL;  // ubar_new - v_L
+        dr[v] = A::diff(uR, ubn[v]) + eR;  // v_R - ubar_new
         f2 vL[K], vR[K];
         vL[0] = f2(0.f);
-        vR[0] = A::diff(vR0, vL0);
+        vR[0] = A::diff(uR, uL) + (eR - eL);
         sfor<1, K>([&](auto Ki) {
             constexpr int k = decltype(Ki)::value;
-            vL[k] = f2(r[(5 + k) * W + t]);
-            vR[k] = f2(r[(5 + k) * W + t + 1]);
+            vL[k] = f2(r[(4 + k) * W + t]);
+            vR[k] = f2(r[(4 + k) * W + t + 1]);
         });
         derivatives_and_point_value<P, f2>(f2(0.f), vL, vR, d[v]);
     });
@@ -341,25 +462,26 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
             limit_deviation_f2<P>(d[0], dl[0], dr[0], args);
         } else {
             f2 ubf[3] = {ubn[0].hi, ubn[1].hi, ubn[2].hi};
-            EulerEigen<f2> E;
-            if (!euler_eigen<f2>(ubf, f2(args.gamma_f), E)) err |= ERR_POSITIVITY;
+            EulerChar2 E;
+            if (!euler_char(ubf, f2(args.gamma_f), E)) err |= ERR_POSITIVITY;
             f2 cd[3][K], cdl[3], cdr[3];
+            E.left(dl[0], dl[1], dl[2], cdl);
+            E.left(dr[0], dr[1], dr[2], cdr);
+            sfor<0, K>([&](auto Ki) {
+                constexpr int k = decltype(Ki)::value;
+                f2 w[3];
+                E.left(d[0][k], d[1][k], d[2][k], w);
+                cd[0][k] = w[0];
+                cd[1][k] = w[1];
+                cd[2][k] = w[2];
+            });
             sfor<0, 3>([&](auto Ii) {
                 constexpr int rr = decltype(Ii)::value;
-                cdl[rr] = fma(E.L[rr][0], dl[0], fma(E.L[rr][1], dl[1], E.L[rr][2] * dl[2]));
-                cdr[rr] = fma(E.L[rr][0], dr[0], fma(E.L[rr][1], dr[1], E.L[rr][2] * dr[2]));
-                sfor<0, K>([&](auto Ki) {
-                    constexpr int k = decltype(Ki)::value;
-                    cd[rr][k] = fma(E.L[rr][0], d[0][k], fma(E.L[rr][1], d[1][k], E.L[rr][2] * d[2][k]));
-                });
                 limit_deviation_f2<P>(cd[rr], cdl[rr], cdr[rr], args);
             });
-            sfor<0, 3>([&](auto Vi) {
-                constexpr int v = decltype(Vi)::value;
-                sfor<0, K>([&](auto Ki) {
-                    constexpr int k = decltype(Ki)::value;
-                    d[v][k] = fma(E.Rm[v][0], cd[0][k], fma(E.Rm[v][1], cd[1][k], E.Rm[v][2] * cd[2][k]));
-                });
+            sfor<0, K>([&](auto Ki) {
+                constexpr int k = decltype(Ki)::value;
+                E.right(cd[0][k], cd[1][k], cd[2][k], d[0][k], d[1][k], d[2][k]);
             });
         }
     }
@@ -394,7 +516,7 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
 }
 
 template <int SYS, int P, bool COMP = true>
-__global__ void __launch_bounds__(kThreads, kMixedMinCtas) halfstep_mixed2(const StepArgs args) {
+__global__ void __launch_bounds__(kThreadsMixed, kMixedMinCtas) halfstep_mixed2(const StepArgs args) {
     __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
     const StepSize z = step_size(args);
     const TileIO io{args.in32, args.out32, args.pitch, args.n_old, args.n_new,
@@ -402,7 +524,39 @@ __global__ void __launch_bounds__(kThreads, kMixedMinCtas) halfstep_mixed2(const
     float speed = 0.f;
     unsigned err = 0u;
     mixed_tile2<SYS, P, COMP>(io, ff_make(z.lam_hi, z.lam_lo), args, rec, speed, err);
-    finish_halfstep<float>(speed, err, z.dt, args);
+    finish_halfstep<float, kThreadsMixed>(speed, err, z.dt, args);
+}
+
+// Largest characteristic speed of a stored FP32-mixed stage.
+template <int SYS, int P>
+__global__ void __launch_bounds__(256) stage_speed_mixed(const float* planes, long long pitch, long long n,
+                                                          StepArgs args, int slot) {
+    constexpr int NV = nvars(SYS);
+    constexpr int NP = P + 2;
+    double m = 0.0;
+    unsigned err = 0u;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        float u0[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            float corr = 0.f;
+#pragma unroll
+            for (int k = 2; k <= P; k += 2)
+                corr += planes[(long long)(v * NP + k + 1) * pitch + i] / (float)((k + 1) * (1 << k));
+            u0[v] = (planes[(long long)(v * NP) * pitch + i] + planes[(long long)(v * NP + 1) * pitch + i]) - corr;
+        }
+        double s = (double)wave_speed<SYS, float>(u0, args, err);
+        if (s != s) {
+            s = __longlong_as_double(0x7ff0000000000000ll);
+            err |= ERR_NONFINITE;
+        }
+        m = fmax(m, s);
+    }
+    m = warp_max<double>(m);
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(&args.st->amax_bits[slot], (unsigned long long)__double_as_longlong(m));
+    if (err) atomicOr(&args.st->err, err);
 }
 
 }  // namespace wcc
