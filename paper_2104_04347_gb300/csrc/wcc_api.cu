@@ -22,8 +22,10 @@ thread_local std::string g_create_error;
 // ------------------------------------------------ layout conversion kernels
 
 // Host layout [cell][var][k] of paper-scaled derivatives u_kx  <->  device
-// planes of Taylor coefficients e_k = u_kx / k!.  One thread per element:
-// reads of the host-layout array are coalesced.
+// planes of Taylor coefficients e_k = u_kx / k!.  Each CTA converts a tile of
+// kConvCells cells through shared memory: the host-layout side of the tile is
+// one contiguous run of doubles and the plane side one run per plane, so both
+// global sides are coalesced.
 // 1/k! and 1/((k+1) 2^k) for k = 0..4, rounded once to double (the layout
 // conversions multiply by these instead of dividing: FP64 division is slow on
 // this GPU).
@@ -41,103 +43,126 @@ __device__ __forceinline__ double avg_weight_k(int k) {
     return t[k];
 }
 
-__global__ void aos_to_planes_fp64(const double* __restrict__ aos, long long n, int nv, int K, long long pitch,
-                                   double* __restrict__ planes) {
-    const long long total = n * nv * K;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % K);
-        const long long rest = e / K;
-        const int v = (int)(rest % nv);
-        const long long cell = rest / nv;
-        planes[(long long)(v * K + k) * pitch + cell] = aos[e] * inv_fact_k(k);
+constexpr int kConvCells = 128;                 // cells per tile
+constexpr int kConvThreads = 256;
+constexpr int kConvMaxElems = kConvCells * 3 * 5;  // nv <= 3, K <= 5
+
+// Copies cells [c0, c0 + m) of the host-layout array to / from smem.
+__device__ __forceinline__ void tile_load(const double* __restrict__ aos, long long c0, int m, int row,
+                                          double* sm) {
+    const double* src = aos + c0 * row;
+    for (int i = threadIdx.x; i < m * row; i += kConvThreads) sm[i] = src[i];
+}
+__device__ __forceinline__ void tile_store(double* __restrict__ aos, long long c0, int m, int row,
+                                           const double* sm) {
+    double* dst = aos + c0 * row;
+    for (int i = threadIdx.x; i < m * row; i += kConvThreads) dst[i] = sm[i];
+}
+
+__global__ void __launch_bounds__(kConvThreads) aos_to_planes_fp64(const double* __restrict__ aos, long long n,
+                                                                   int nv, int K, long long pitch,
+                                                                   double* __restrict__ planes) {
+    __shared__ double sm[kConvMaxElems];
+    const int row = nv * K;
+    for (long long c0 = (long long)blockIdx.x * kConvCells; c0 < n; c0 += (long long)gridDim.x * kConvCells) {
+        const int m = (int)min((long long)kConvCells, n - c0);
+        tile_load(aos, c0, m, row, sm);
+        __syncthreads();
+        // element (plane q = v K + k, cell c): consecutive threads, consecutive cells
+        for (int i = threadIdx.x; i < kConvCells * row; i += kConvThreads) {
+            const int c = i % kConvCells, q = i / kConvCells;
+            if (c < m) planes[(long long)q * pitch + c0 + c] = sm[c * row + q] * inv_fact_k(q % K);
+        }
+        __syncthreads();
     }
 }
 
-__global__ void planes_to_aos_fp64(const double* __restrict__ planes, long long n, int nv, int K, long long pitch,
-                                   double* __restrict__ aos) {
-    const long long total = n * nv * K;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % K);
-        const long long rest = e / K;
-        const int v = (int)(rest % nv);
-        const long long cell = rest / nv;
-        aos[e] = planes[(long long)(v * K + k) * pitch + cell] * fact_k(k);
+__global__ void __launch_bounds__(kConvThreads) planes_to_aos_fp64(const double* __restrict__ planes, long long n,
+                                                                   int nv, int K, long long pitch,
+                                                                   double* __restrict__ aos) {
+    __shared__ double sm[kConvMaxElems];
+    const int row = nv * K;
+    for (long long c0 = (long long)blockIdx.x * kConvCells; c0 < n; c0 += (long long)gridDim.x * kConvCells) {
+        const int m = (int)min((long long)kConvCells, n - c0);
+        for (int i = threadIdx.x; i < kConvCells * row; i += kConvThreads) {
+            const int c = i % kConvCells, q = i / kConvCells;
+            if (c < m) sm[c * row + q] = planes[(long long)q * pitch + c0 + c] * fact_k(q % K);
+        }
+        __syncthreads();
+        tile_store(aos, c0, m, row, sm);
+        __syncthreads();
     }
 }
 
 // FP32-mixed / FP32: per (cell, var) the cell average (Eq. SubEq:1DCellAVG:
 // ubar = sum_{k even} u_kx / ((k+1)! 2^k) = sum_{k even} e_k / ((k+1) 2^k))
 // split into a float-float pair, and e_k = u_kx / k! rounded to FP32 for k >= 1.
-__global__ void aos_to_planes_mixed(const double* __restrict__ aos, long long n, int nv, int K, long long pitch,
-                                    float* __restrict__ planes, int keep_lo) {
+__global__ void __launch_bounds__(kConvThreads) aos_to_planes_mixed(const double* __restrict__ aos, long long n,
+                                                                    int nv, int K, long long pitch,
+                                                                    float* __restrict__ planes, int keep_lo) {
+    __shared__ double sm[kConvMaxElems];
     const int NP = K + 1;
-    const long long total = n * nv;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int v = (int)(e % nv);
-        const long long cell = e / nv;
-        const double* q = aos + e * K;
-        double ubar = q[0];
-        for (int k = 1; k < K; ++k) {
-            const double ek = q[k] * inv_fact_k(k);
-            if ((k & 1) == 0) ubar = fma(ek, avg_weight_k(k), ubar);
-            planes[(long long)(v * NP + k + 1) * pitch + cell] = (float)ek;
+    const int row = nv * K;
+    for (long long c0 = (long long)blockIdx.x * kConvCells; c0 < n; c0 += (long long)gridDim.x * kConvCells) {
+        const int m = (int)min((long long)kConvCells, n - c0);
+        tile_load(aos, c0, m, row, sm);
+        __syncthreads();
+        for (int i = threadIdx.x; i < kConvCells * nv; i += kConvThreads) {
+            const int c = i % kConvCells, v = i / kConvCells;
+            if (c >= m) continue;
+            const double* q = sm + c * row + v * K;
+            const long long cell = c0 + c;
+            double ubar = q[0];
+            for (int k = 1; k < K; ++k) {
+                const double ek = q[k] * inv_fact_k(k);
+                if ((k & 1) == 0) ubar = fma(ek, avg_weight_k(k), ubar);
+                planes[(long long)(v * NP + k + 1) * pitch + cell] = (float)ek;
+            }
+            float hi, lo;
+            split_double(ubar, hi, lo);
+            planes[(long long)(v * NP + 0) * pitch + cell] = hi;
+            planes[(long long)(v * NP + 1) * pitch + cell] = keep_lo ? lo : 0.f;  // plain FP32: rounded once
         }
-        float hi, lo;
-        split_double(ubar, hi, lo);
-        planes[(long long)(v * NP + 0) * pitch + cell] = hi;
-        planes[(long long)(v * NP + 1) * pitch + cell] = keep_lo ? lo : 0.f;  // plain FP32: average rounded once
+        __syncthreads();
     }
 }
 
-// One thread per output double (consecutive threads write consecutive
-// doubles: coalesced, which matters when the destination is host memory).
-__global__ void planes_to_aos_mixed(const float* __restrict__ planes, long long n, int nv, int K, long long pitch,
-                                    double* __restrict__ aos) {
+__global__ void __launch_bounds__(kConvThreads) planes_to_aos_mixed(const float* __restrict__ planes, long long n,
+                                                                    int nv, int K, long long pitch,
+                                                                    double* __restrict__ aos) {
+    __shared__ double sm[kConvMaxElems];
     const int NP = K + 1;
-    const long long total = n * nv * K;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(e % K);
-        const long long rest = e / K;
-        const int v = (int)(rest % nv);
-        const long long cell = rest / nv;
-        double out;
-        if (k == 0) {
-            out = (double)planes[(long long)(v * NP + 0) * pitch + cell] +
-                  (double)planes[(long long)(v * NP + 1) * pitch + cell];
-            for (int j = 2; j < K; j += 2)
-                out = fma(-(double)planes[(long long)(v * NP + j + 1) * pitch + cell], avg_weight_k(j), out);
-        } else {
-            out = (double)planes[(long long)(v * NP + k + 1) * pitch + cell] * fact_k(k);
+    const int row = nv * K;
+    for (long long c0 = (long long)blockIdx.x * kConvCells; c0 < n; c0 += (long long)gridDim.x * kConvCells) {
+        const int m = (int)min((long long)kConvCells, n - c0);
+        for (int i = threadIdx.x; i < kConvCells * nv; i += kConvThreads) {
+            const int c = i % kConvCells, v = i / kConvCells;
+            if (c >= m) continue;
+            const long long cell = c0 + c;
+            double* q = sm + c * row + v * K;
+            double u0 = (double)planes[(long long)(v * NP + 0) * pitch + cell] +
+                        (double)planes[(long long)(v * NP + 1) * pitch + cell];
+            for (int k = 1; k < K; ++k) {
+                const double ek = (double)planes[(long long)(v * NP + k + 1) * pitch + cell];
+                if ((k & 1) == 0) u0 = fma(-ek, avg_weight_k(k), u0);
+                q[k] = ek * fact_k(k);
+            }
+            q[0] = u0;
         }
-        aos[e] = out;
+        __syncthreads();
+        tile_store(aos, c0, m, row, sm);
+        __syncthreads();
     }
 }
 
-// Device view of a caller's host buffer: the buffer itself when it is pinned
-// and mapped into the device address space (the conversion kernels then read
-// or write it directly), else nullptr (staging copy).
-const void* mapped_host_view(const void* p) {
-#if defined(WCC_ZERO_COPY) && WCC_ZERO_COPY == 0
-    return nullptr;
-#endif
-    cudaPointerAttributes a;
-    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
-        cudaGetLastError();
-        return nullptr;
-    }
-    if (a.type == cudaMemoryTypeHost && a.devicePointer) return a.devicePointer;
-    return nullptr;
-}
-
-unsigned elementwise_grid(long long total) {
-    long long b = (total + 255) / 256;
-    if (b > 152 * 16) b = 152 * 16;
+// Tiles of the conversion kernels: one per kConvCells cells, at most 8 CTAs
+// per SM of a 152-SM GPU (the kernels stride over the rest).
+unsigned conv_grid(long long n) {
+    long long b = (n + kConvCells - 1) / kConvCells;
+    if (b > 152 * 8) b = 152 * 8;
     return (unsigned)(b < 1 ? 1 : b);
 }
+
 
 }  // namespace
 
@@ -445,21 +470,20 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     if (!dofs) return fail(h, WCC_E_INVAL, "dofs is NULL");
     const long long n = stage_cells(h, 0);
     if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match cells*nv*(P+1) of an integer stage");
-    const double* src = static_cast<const double*>(mapped_host_view(dofs));
-    if (!src) {
-        WCC_CHECK(h, cudaMemcpyAsync(h->staging, dofs, (size_t)count * sizeof(double), cudaMemcpyHostToDevice,
-                                     h->stream));
-        src = h->staging;
-    }
+    // host -> device staging by a copy engine (overlaps kernels of other
+    // streams), then the layout conversion on the device
+    WCC_CHECK(h, cudaMemcpyAsync(h->staging, dofs, (size_t)count * sizeof(double), cudaMemcpyHostToDevice,
+                                 h->stream));
+    const double* src = h->staging;
     h->cur = 0;
     h->parity = 0;
     h->steps = 0;
     const bool mixed = h->opt.precision != WCC_FP64;
     if (mixed)
-        aos_to_planes_mixed<<<elementwise_grid(n * h->nv), 256, 0, h->stream>>>(
+        aos_to_planes_mixed<<<conv_grid(n), kConvThreads, 0, h->stream>>>(
             src, n, h->nv, h->K, h->pitch, h->s32[0], h->opt.precision == WCC_FP32_MIXED);
     else
-        aos_to_planes_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(src, n, h->nv, h->K, h->pitch,
+        aos_to_planes_fp64<<<conv_grid(n), kConvThreads, 0, h->stream>>>(src, n, h->nv, h->K, h->pitch,
                                                                               h->s64[0]);
     WCC_CHECK(h, cudaGetLastError());
     WCC_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
@@ -541,20 +565,16 @@ int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     const long long n = stage_cells(h, h->parity);
     if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match the current stage");
-    double* dst = static_cast<double*>(const_cast<void*>(mapped_host_view(dofs)));
-    const bool direct = dst != nullptr;
-    if (!direct) dst = h->staging;
     if (h->opt.precision != WCC_FP64)
-        planes_to_aos_mixed<<<elementwise_grid(count), 256, 0, h->stream>>>(h->s32[h->cur], n, h->nv, h->K,
-                                                                            h->pitch, dst);
+        planes_to_aos_mixed<<<conv_grid(n), kConvThreads, 0, h->stream>>>(h->s32[h->cur], n, h->nv, h->K, h->pitch,
+                                                                         h->staging);
     else
-        planes_to_aos_fp64<<<elementwise_grid(count), 256, 0, h->stream>>>(h->s64[h->cur], n, h->nv, h->K,
-                                                                               h->pitch, dst);
+        planes_to_aos_fp64<<<conv_grid(n), kConvThreads, 0, h->stream>>>(h->s64[h->cur], n, h->nv, h->K, h->pitch,
+                                                                        h->staging);
     WCC_CHECK(h, cudaGetLastError());
     h->launches += 1;
-    if (!direct)
-        WCC_CHECK(h, cudaMemcpyAsync(dofs, h->staging, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost,
-                                     h->stream));
+    WCC_CHECK(h, cudaMemcpyAsync(dofs, h->staging, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost,
+                                 h->stream));
     DevState s;
     return read_state(h, &s);
 }
