@@ -140,9 +140,10 @@ FP64_FLOPS_PER_CELL_UPDATE = 968.0
 # (201458688 + 149019904 at N = 2^21), scaled by cells to N = 2^22.
 FP64_TRAFFIC_PER_CELL = (201458688 + 149019904) / 2097152.5
 # DRAM bytes (read + write) of one FP32-mixed launch per cell, from an ncu
-# capture of halfstep_mixed2<EULER, 3> at N = 2^21 (125896192 + 79292672),
-# scaled by cells to N = 2^22.
-MIXED_TRAFFIC_PER_CELL = (125896192 + 79292672) / 2097152.5
+# capture of halfstep_mixed2<EULER, 3> at N = 2^21 (125919744 + 78400000; the
+# kernel with A-records and the compact characteristic projection), scaled by
+# cells to N = 2^22.
+MIXED_TRAFFIC_PER_CELL = (125919744 + 78400000) / 2097152.5
 # FP64 pipe peak of the GB300 (dense, nominal): 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 

@@ -10,6 +10,7 @@
 
 #include "../../include/wcc.h"
 #include "wcc_launch.h"
+#include "wcc_convert.cuh"
 #include "wcc_ff.cuh"
 #include "wcc_scheme.cuh"
 
@@ -35,11 +36,6 @@ __device__ __forceinline__ double inv_fact_k(int k) {
 }
 __device__ __forceinline__ double fact_k(int k) {
     const double t[5] = {1.0, 1.0, 2.0, 6.0, 24.0};
-    return t[k];
-}
-// weight of the Taylor coefficient e_k in the cell average (even k)
-__device__ __forceinline__ double avg_weight_k(int k) {
-    const double t[5] = {1.0, 0.0, 1.0 / 12.0, 0.0, 1.0 / 80.0};
     return t[k];
 }
 
@@ -95,13 +91,15 @@ __global__ void __launch_bounds__(kConvThreads) planes_to_aos_fp64(const double*
 }
 
 // FP32-mixed / FP32: per (cell, var) the cell average (Eq. SubEq:1DCellAVG:
-// ubar = sum_{k even} u_kx / ((k+1)! 2^k) = sum_{k even} e_k / ((k+1) 2^k))
-// split into a float-float pair, and e_k = u_kx / k! rounded to FP32 for k >= 1.
+// ubar = sum_{k even} u_kx / ((k+1)! 2^k)) as a float-float pair (plain FP32
+// keeps only its rounded hi part) and e_k = u_kx / k! in FP32 for k >= 1;
+// FP32 and integer arithmetic only (wcc_convert.cuh).
+template <int K>
 __global__ void __launch_bounds__(kConvThreads) aos_to_planes_mixed(const double* __restrict__ aos, long long n,
-                                                                    int nv, int K, long long pitch,
+                                                                    int nv, long long pitch,
                                                                     float* __restrict__ planes, int keep_lo) {
     __shared__ double sm[kConvMaxElems];
-    const int NP = K + 1;
+    constexpr int NP = K + 1;
     const int row = nv * K;
     for (long long c0 = (long long)blockIdx.x * kConvCells; c0 < n; c0 += (long long)gridDim.x * kConvCells) {
         const int m = (int)min((long long)kConvCells, n - c0);
@@ -110,49 +108,65 @@ __global__ void __launch_bounds__(kConvThreads) aos_to_planes_mixed(const double
         for (int i = threadIdx.x; i < kConvCells * nv; i += kConvThreads) {
             const int c = i % kConvCells, v = i / kConvCells;
             if (c >= m) continue;
-            const double* q = sm + c * row + v * K;
-            const long long cell = c0 + c;
-            double ubar = q[0];
-            for (int k = 1; k < K; ++k) {
-                const double ek = q[k] * inv_fact_k(k);
-                if ((k & 1) == 0) ubar = fma(ek, avg_weight_k(k), ubar);
-                planes[(long long)(v * NP + k + 1) * pitch + cell] = (float)ek;
-            }
-            float hi, lo;
-            split_double(ubar, hi, lo);
-            planes[(long long)(v * NP + 0) * pitch + cell] = hi;
-            planes[(long long)(v * NP + 1) * pitch + cell] = keep_lo ? lo : 0.f;  // plain FP32: rounded once
+            float e[K];
+            const ff u = host_to_mixed<K>(sm + c * row + v * K, e);
+            float* pl = planes + (long long)(v * NP) * pitch + c0 + c;
+            pl[0] = u.hi;
+            pl[pitch] = keep_lo ? u.lo : 0.f;
+#pragma unroll
+            for (int k = 1; k < K; ++k) pl[(long long)(k + 1) * pitch] = e[k];
         }
         __syncthreads();
     }
 }
 
+template <int K>
 __global__ void __launch_bounds__(kConvThreads) planes_to_aos_mixed(const float* __restrict__ planes, long long n,
-                                                                    int nv, int K, long long pitch,
+                                                                    int nv, long long pitch,
                                                                     double* __restrict__ aos) {
     __shared__ double sm[kConvMaxElems];
-    const int NP = K + 1;
+    constexpr int NP = K + 1;
     const int row = nv * K;
     for (long long c0 = (long long)blockIdx.x * kConvCells; c0 < n; c0 += (long long)gridDim.x * kConvCells) {
         const int m = (int)min((long long)kConvCells, n - c0);
         for (int i = threadIdx.x; i < kConvCells * nv; i += kConvThreads) {
             const int c = i % kConvCells, v = i / kConvCells;
             if (c >= m) continue;
-            const long long cell = c0 + c;
-            double* q = sm + c * row + v * K;
-            double u0 = (double)planes[(long long)(v * NP + 0) * pitch + cell] +
-                        (double)planes[(long long)(v * NP + 1) * pitch + cell];
-            for (int k = 1; k < K; ++k) {
-                const double ek = (double)planes[(long long)(v * NP + k + 1) * pitch + cell];
-                if ((k & 1) == 0) u0 = fma(-ek, avg_weight_k(k), u0);
-                q[k] = ek * fact_k(k);
-            }
-            q[0] = u0;
+            const float* pl = planes + (long long)(v * NP) * pitch + c0 + c;
+            float e[K];
+#pragma unroll
+            for (int k = 1; k < K; ++k) e[k] = pl[(long long)(k + 1) * pitch];
+            mixed_to_host<K>(ff{pl[0], pl[pitch]}, e, sm + c * row + v * K);
         }
         __syncthreads();
         tile_store(aos, c0, m, row, sm);
         __syncthreads();
     }
+}
+
+// Launch helpers: K = P + 1 as a template argument.
+cudaError_t launch_aos_to_planes_mixed(int K, unsigned grid, cudaStream_t s, const double* aos, long long n, int nv,
+                                       long long pitch, float* planes, int keep_lo) {
+    switch (K) {
+        case 2: aos_to_planes_mixed<2><<<grid, kConvThreads, 0, s>>>(aos, n, nv, pitch, planes, keep_lo); break;
+        case 3: aos_to_planes_mixed<3><<<grid, kConvThreads, 0, s>>>(aos, n, nv, pitch, planes, keep_lo); break;
+        case 4: aos_to_planes_mixed<4><<<grid, kConvThreads, 0, s>>>(aos, n, nv, pitch, planes, keep_lo); break;
+        case 5: aos_to_planes_mixed<5><<<grid, kConvThreads, 0, s>>>(aos, n, nv, pitch, planes, keep_lo); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_planes_to_aos_mixed(int K, unsigned grid, cudaStream_t s, const float* planes, long long n, int nv,
+                                       long long pitch, double* aos) {
+    switch (K) {
+        case 2: planes_to_aos_mixed<2><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
+        case 3: planes_to_aos_mixed<3><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
+        case 4: planes_to_aos_mixed<4><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
+        case 5: planes_to_aos_mixed<5><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
 }
 
 // Tiles of the conversion kernels: one per kConvCells cells, at most 8 CTAs
@@ -479,13 +493,14 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     h->parity = 0;
     h->steps = 0;
     const bool mixed = h->opt.precision != WCC_FP64;
-    if (mixed)
-        aos_to_planes_mixed<<<conv_grid(n), kConvThreads, 0, h->stream>>>(
-            src, n, h->nv, h->K, h->pitch, h->s32[0], h->opt.precision == WCC_FP32_MIXED);
-    else
+    if (mixed) {
+        WCC_CHECK(h, launch_aos_to_planes_mixed(h->K, conv_grid(n), h->stream, src, n, h->nv, h->pitch, h->s32[0],
+                                                h->opt.precision == WCC_FP32_MIXED));
+    } else {
         aos_to_planes_fp64<<<conv_grid(n), kConvThreads, 0, h->stream>>>(src, n, h->nv, h->K, h->pitch,
                                                                               h->s64[0]);
-    WCC_CHECK(h, cudaGetLastError());
+        WCC_CHECK(h, cudaGetLastError());
+    }
     WCC_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
     StepArgs a = make_args(h, 0, 0, 0.0, 0.0);
     cudaError_t e;
@@ -565,13 +580,14 @@ int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     const long long n = stage_cells(h, h->parity);
     if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match the current stage");
-    if (h->opt.precision != WCC_FP64)
-        planes_to_aos_mixed<<<conv_grid(n), kConvThreads, 0, h->stream>>>(h->s32[h->cur], n, h->nv, h->K, h->pitch,
-                                                                         h->staging);
-    else
+    if (h->opt.precision != WCC_FP64) {
+        WCC_CHECK(h, launch_planes_to_aos_mixed(h->K, conv_grid(n), h->stream, h->s32[h->cur], n, h->nv, h->pitch,
+                                                h->staging));
+    } else {
         planes_to_aos_fp64<<<conv_grid(n), kConvThreads, 0, h->stream>>>(h->s64[h->cur], n, h->nv, h->K, h->pitch,
                                                                         h->staging);
-    WCC_CHECK(h, cudaGetLastError());
+        WCC_CHECK(h, cudaGetLastError());
+    }
     h->launches += 1;
     WCC_CHECK(h, cudaMemcpyAsync(dofs, h->staging, (size_t)count * sizeof(double), cudaMemcpyDeviceToHost,
                                  h->stream));

@@ -13,6 +13,7 @@
 // instance of a batch evolves exactly like the same problem run alone.
 #pragma once
 
+#include "wcc_convert.cuh"
 #include "wcc_mixed2.cuh"
 
 namespace wcc {
@@ -114,6 +115,29 @@ __global__ void __launch_bounds__(kThreads) batch_stage_speed(const BatchArgs b)
 
 // Host layout (per instance [cell][var][k] of u_kx, instances back to back in
 // the order of the instance table) <-> group planes, one thread per cell.
+// One cell (all variables) of a group's planes <-> its host-layout DOFs q
+// ([var][k]), with the conversions of wcc_convert.cuh.
+template <int K>
+__device__ __forceinline__ void convert_cell(double* q, float* pl, long long pitch, long long c, int nv,
+                                             int to_planes) {
+    constexpr int NP = K + 1;
+    for (int v = 0; v < nv; ++v) {
+        float* p = pl + (long long)(v * NP) * pitch + c;
+        float e[K];
+        if (to_planes) {
+            const ff u = host_to_mixed<K>(q + v * K, e);
+            p[0] = u.hi;
+            p[pitch] = u.lo;
+#pragma unroll
+            for (int k = 1; k < K; ++k) p[(long long)(k + 1) * pitch] = e[k];
+        } else {
+#pragma unroll
+            for (int k = 1; k < K; ++k) e[k] = p[(long long)(k + 1) * pitch];
+            mixed_to_host<K>(ff{p[0], p[pitch]}, e, q + v * K);
+        }
+    }
+}
+
 template <int SYS, int PA, int PB>
 __global__ void __launch_bounds__(kThreads) batch_convert(const BatchArgs b, double* aos, int to_planes) {
     for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
@@ -122,38 +146,14 @@ __global__ void __launch_bounds__(kThreads) batch_convert(const BatchArgs b, dou
         const long long c = (tile - b.tile_start[i]) * kTile + threadIdx.x;
         if (threadIdx.x >= kTile || c >= I.cells[b.parity]) continue;
         const int P = I.group == 0 ? PA : PB;
-        const int K = P + 1, NP = P + 2, NV = nvars(SYS);
+        const int K = P + 1, NV = nvars(SYS);
         float* pl = (to_planes ? b.out[I.group] : const_cast<float*>(b.in[I.group])) + I.offset;
         const long long pitch = b.pitch[I.group];
         double* q0 = aos + I.aos_offset[b.parity] + c * NV * K;
-        for (int v = 0; v < NV; ++v) {
-            double* q = q0 + v * K;
-            // 1/k!, k! and the cell-average weights 1/((k+1) 2^k) as constants
-            // (no FP64 division)
-            const double inv_fact[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
-            const double fact[5] = {1.0, 1.0, 2.0, 6.0, 24.0};
-            const double avg_w[5] = {1.0, 0.0, 1.0 / 12.0, 0.0, 1.0 / 80.0};
-            if (to_planes) {
-                double ubar = q[0];
-                for (int k = 1; k < K; ++k) {
-                    const double ek = q[k] * inv_fact[k];
-                    if ((k & 1) == 0) ubar = fma(ek, avg_w[k], ubar);
-                    pl[(long long)(v * NP + k + 1) * pitch + c] = (float)ek;
-                }
-                float hi, lo;
-                split_double(ubar, hi, lo);
-                pl[(long long)(v * NP) * pitch + c] = hi;
-                pl[(long long)(v * NP + 1) * pitch + c] = lo;
-            } else {
-                double u0 = (double)pl[(long long)(v * NP) * pitch + c] + (double)pl[(long long)(v * NP + 1) * pitch + c];
-                for (int k = 1; k < K; ++k) {
-                    const double ek = (double)pl[(long long)(v * NP + k + 1) * pitch + c];
-                    if ((k & 1) == 0) u0 = fma(-ek, avg_w[k], u0);
-                    q[k] = ek * fact[k];
-                }
-                q[0] = u0;
-            }
-        }
+        if (I.group == 0)
+            convert_cell<PA + 1>(q0, pl, pitch, c, NV, to_planes);
+        else
+            convert_cell<PB + 1>(q0, pl, pitch, c, NV, to_planes);
     }
 }
 

@@ -1,0 +1,111 @@
+// wcc_convert.cuh -- per-value conversions between the host layout (FP64
+// paper-scaled derivatives u_kx) and the FP32-mixed device planes (cell
+// average as a float-float pair, Taylor coefficients e_k = u_kx / k! in FP32),
+// written with FP32 and integer instructions only.
+//
+// GB300 executes FP64 arithmetic and FP64 <-> FP32 conversions at about 1/64
+// of the FP32 rate, and a plain double-based conversion keeps its FP64 pipe
+// busy for longer than the memory traffic takes.  Here instead:
+//   * a double is split into floats hi + lo by integer operations on its bits
+//     (hi = the leading 24 significant bits, lo = the remaining 29 bits
+//     rounded to FP32);
+//   * a float times a small integer (k!) is turned into a double exactly by
+//     multiplying the 24-bit significand as an integer;
+//   * the constant factors 1/k!, 1/((k+1)! 2^k) and 1/((k+1) 2^k) are applied
+//     as float-float products, so the cell average keeps float-float accuracy
+//     (a few units of 2^-48).
+// Values outside the range where these are exact (zero aside: subnormal,
+// tiny, huge, inf, NaN) take the hardware conversion, which is rare.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wcc_ff.cuh"
+
+namespace wcc {
+
+// A float-float constant: hi + lo rounds x to about 48 bits.
+struct ffc {
+    float hi, lo;
+};
+__host__ __device__ constexpr ffc ffc_of(double x) { return ffc{(float)x, (float)(x - (double)(float)x)}; }
+
+// 1/k!, k = 0..4
+__host__ __device__ constexpr ffc inv_fact_c(int k) {
+    return k == 2 ? ffc_of(0.5) : k == 3 ? ffc_of(1.0 / 6.0) : k == 4 ? ffc_of(1.0 / 24.0) : ffc_of(1.0);
+}
+// k!, k = 0..4
+__host__ __device__ constexpr unsigned fact_u(int k) { return k == 2 ? 2u : k == 3 ? 6u : k == 4 ? 24u : 1u; }
+// weight of u_kx in the cell average, 1/((k+1)! 2^k) (Eq. SubEq:1DCellAVG; even k >= 2)
+__host__ __device__ constexpr ffc avg_from_u_c(int k) { return k == 2 ? ffc_of(1.0 / 24.0) : ffc_of(1.0 / 1920.0); }
+// weight of e_k in the cell average, 1/((k+1) 2^k) (even k >= 2)
+__host__ __device__ constexpr ffc avg_from_e_c(int k) { return k == 2 ? ffc_of(1.0 / 12.0) : ffc_of(1.0 / 80.0); }
+
+__device__ __forceinline__ ff ff_mul_c(ff a, ffc c) { return ff_mul(a, ff{c.hi, c.lo}); }
+
+// d = hi + lo: hi = d truncated to 24 significant bits, lo = the remaining
+// bits rounded to FP32 (|lo| < ulp(hi)); integer operations only for
+// 2^-74 <= |d| < 2^128 and for zero.
+__device__ __forceinline__ ff split_double_bits(double d) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+    if ((b << 1) == 0ull) return ff{__uint_as_float(sign), 0.f};
+    const int e = (int)((b >> 52) & 0x7ffull) - 1023;
+    if (e < -74 || e > 127) {
+        ff r;
+        split_double(d, r.hi, r.lo);
+        return r;
+    }
+    const unsigned long long mant = b & ((1ull << 52) - 1ull);
+    const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));
+    // lo = +-rest * 2^(e - 52): rest (< 2^29) rounded to FP32, times a power of two
+    const unsigned rest = (unsigned)(mant & ((1ull << 29) - 1ull));
+    const float scale = __uint_as_float(sign | ((unsigned)(e - 52 + 127) << 23));
+    return ff{hi, __uint2float_rn(rest) * scale};
+}
+
+// f * m exactly as a double, for an integer 1 <= m <= 24: the 24-bit
+// significand times m (< 2^29) renormalised with integer operations.
+__device__ __forceinline__ double float_times_uint_exact(float f, unsigned m) {
+    const unsigned u = __float_as_uint(f);
+    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));  // +-0
+    const unsigned ex = (u >> 23) & 0xffu;
+    if (ex == 0u || ex == 0xffu) return (double)f * (double)m;  // subnormal, inf, NaN
+    const unsigned long long n = (unsigned long long)((u & 0x7fffffu) | 0x800000u) * m;
+    const int lead = 63 - __clzll((long long)n);  // 23..28
+    const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                    ((unsigned long long)(lead + (int)ex - 150 + 1023) << 52) |
+                                    ((n << (52 - lead)) & ((1ull << 52) - 1ull));
+    return __longlong_as_double((long long)bits);
+}
+
+// The host-layout DOFs q[0..K-1] of one (cell, variable) -> the device
+// values: the cell average ubar = sum over even k of q_k / ((k+1)! 2^k) as a
+// float-float (normalised), and e_k = q_k / k! rounded to FP32, k >= 1.
+template <int K>
+__device__ __forceinline__ ff host_to_mixed(const double* q, float (&e)[K]) {
+    ff u = split_double_bits(q[0]);
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+        const ff qk = split_double_bits(q[k]);
+        e[k] = ff_mul_c(qk, inv_fact_c(k)).hi;
+        if ((k & 1) == 0) u = ff_add(u, ff_mul_c(qk, avg_from_u_c(k)));
+    }
+    return fast_two_sum(u.hi, u.lo);
+}
+
+// The device values of one (cell, variable) -> host-layout DOFs: q_k = e_k k!
+// (exact), q_0 = ubar - sum over even k of e_k / ((k+1) 2^k) (float-float,
+// then one FP64 add to form the double).
+template <int K>
+__device__ __forceinline__ void mixed_to_host(ff ubar, const float (&e)[K], double* q) {
+    ff u = ubar;
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+        q[k] = float_times_uint_exact(e[k], fact_u(k));
+        if ((k & 1) == 0) u = ff_sub(u, ff_mul_c(ff{e[k], 0.f}, avg_from_e_c(k)));
+    }
+    q[0] = float_times_uint_exact(u.hi, 1u) + float_times_uint_exact(u.lo, 1u);
+}
+
+}  // namespace wcc
