@@ -134,11 +134,11 @@ def peaks():
 # limiter on), counted from the executed DADD / DMUL / DFMA instructions (ncu
 # smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum over one
 # launch at N = 2^21, DFMA counted as 2) divided by the cells of the launch:
-# (2 x 711549710 + 220517122 + 386508291) / 2097152.5.
-FP64_FLOPS_PER_CELL_UPDATE = 968.0
+# (2 x 692675342 + 306816515 + 163894018) / 2097152.5.
+FP64_FLOPS_PER_CELL_UPDATE = 885.04
 # DRAM bytes (read + write) of one FP64 launch, from the same capture
-# (201458688 + 149019904 at N = 2^21), scaled by cells to N = 2^22.
-FP64_TRAFFIC_PER_CELL = (201458688 + 149019904) / 2097152.5
+# (201425408 + 149216768 at N = 2^21), scaled by cells to N = 2^22.
+FP64_TRAFFIC_PER_CELL = (201425408 + 149216768) / 2097152.5
 # DRAM bytes (read + write) of one FP32-mixed launch per cell, from an ncu
 # capture of halfstep_mixed2<EULER, 3> at N = 2^21 (125919744 + 78400000; the
 # kernel with A-records and the compact characteristic projection), scaled by

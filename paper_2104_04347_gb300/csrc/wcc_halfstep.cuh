@@ -184,26 +184,27 @@ __global__ void __launch_bounds__(kThreads) halfstep_fp64(const StepArgs args) {
                 limit_scalar<P, double>(e[0], ubar[0], vl[0], vr[0], args);
             } else {
                 // Sec. 4: limit characteristic variables L(ubar) U, map back with R(ubar).
-                EulerEigen<double> E;
-                if (!euler_eigen<double>(ubar, args.gamma, E)) err |= ERR_POSITIVITY;
+                EulerChar<double> E;
+                if (!euler_char<double>(ubar, args.gamma, E)) err |= ERR_POSITIVITY;
                 double ce[3][K], cub[3], cvl[3], cvr[3];
+                E.left(ubar[0], ubar[1], ubar[2], cub);
+                E.left(vl[0], vl[1], vl[2], cvl);
+                E.left(vr[0], vr[1], vr[2], cvr);
+                sfor<0, K>([&](auto Ki) {
+                    constexpr int k = decltype(Ki)::value;
+                    double w[3];
+                    E.left(e[0][k], e[1][k], e[2][k], w);
+                    ce[0][k] = w[0];
+                    ce[1][k] = w[1];
+                    ce[2][k] = w[2];
+                });
                 sfor<0, 3>([&](auto Ii) {
                     constexpr int r = decltype(Ii)::value;
-                    cub[r] = E.L[r][0] * ubar[0] + E.L[r][1] * ubar[1] + E.L[r][2] * ubar[2];
-                    cvl[r] = E.L[r][0] * vl[0] + E.L[r][1] * vl[1] + E.L[r][2] * vl[2];
-                    cvr[r] = E.L[r][0] * vr[0] + E.L[r][1] * vr[1] + E.L[r][2] * vr[2];
-                    sfor<0, K>([&](auto Ki) {
-                        constexpr int k = decltype(Ki)::value;
-                        ce[r][k] = E.L[r][0] * e[0][k] + E.L[r][1] * e[1][k] + E.L[r][2] * e[2][k];
-                    });
                     limit_scalar<P, double>(ce[r], cub[r], cvl[r], cvr[r], args);
                 });
-                sfor<0, 3>([&](auto Vi) {
-                    constexpr int v = decltype(Vi)::value;
-                    sfor<0, K>([&](auto Ki) {
-                        constexpr int k = decltype(Ki)::value;
-                        e[v][k] = E.Rm[v][0] * ce[0][k] + E.Rm[v][1] * ce[1][k] + E.Rm[v][2] * ce[2][k];
-                    });
+                sfor<0, K>([&](auto Ki) {
+                    constexpr int k = decltype(Ki)::value;
+                    E.right(ce[0][k], ce[1][k], ce[2][k], e[0][k], e[1][k], e[2][k]);
                 });
             }
         }

@@ -180,6 +180,25 @@ __device__ __forceinline__ void flux_ff2(const ff2 (&u)[nvars(SYS)], const StepA
 
 // ------------------------------------------------------ limiter, paired
 
+// Reciprocal estimate of each lane from the special-function unit (relative
+// error about 2^-23), for normal or infinite inputs (0 gives +inf).
+__device__ __forceinline__ f2 rcp_est(f2 a) {
+    float rx, ry;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rx) : "f"(a.v.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(ry) : "f"(a.v.y));
+    return f2(rx, ry);
+}
+
+// The weights' denominators d = beta^2 + eps (beta + eps at P = 1) are
+// formed scaled by 2^32, which is exact, with eps' = max(eps, 2^-149) so that
+// d > 0.  The paper's eps = 1e-40 is subnormal in FP32; scaled, every d is a
+// normal number, so each ratio a / d is one reciprocal estimate per lane and
+// a paired multiply (for normal d the same value as a / d unscaled: the
+// estimate of x 2^k is the estimate of x times 2^-k).
+__device__ __forceinline__ f2 scaled_eps(const StepArgs& args) {
+    return f2(fmaxf(args.eps_f, 1.4e-45f) * 4294967296.f);
+}
+
 // Normalised weights for P >= 2 (Eq. 1DHighOrderWeights), scale-free:
 // w0 ~ 1 + (st/d0)^alpha, w_m ~ (st/d_m)^alpha with d = beta^2 + eps, all
 // multiplied through by (d_min/st)^alpha, so every ratio is at most 1 (st = 0
@@ -187,11 +206,12 @@ __device__ __forceinline__ void flux_ff2(const ff2 (&u)[nvars(SYS)], const StepA
 // so that it is exactly 1 whenever the other two vanish.
 __device__ __forceinline__ void weights_hi_f2(f2 b0, f2 b1, f2 b2, f2 st, const StepArgs& args, f2& w0, f2& w1,
                                               f2& w2) {
-    const f2 eps(args.eps_f), tiny(1.4e-45f);
-    const f2 d0 = fmax(fma(b0, b0, eps), tiny), d1 = fmax(fma(b1, b1, eps), tiny), d2 = fmax(fma(b2, b2, eps), tiny);
+    const f2 eps = scaled_eps(args), s16(65536.f), s32(4294967296.f);
+    const f2 c0 = b0 * s16, c1 = b1 * s16, c2 = b2 * s16;
+    const f2 d0 = fma(c0, c0, eps), d1 = fma(c1, c1, eps), d2 = fma(c2, c2, eps);  // d 2^32
     const f2 dmin = fmin(d0, fmin(d1, d2));
-    const f2 q0 = fdiv_fast(dmin, d0), q1 = fdiv_fast(dmin, d1), q2 = fdiv_fast(dmin, d2);
-    const f2 z = fmin(fdiv_fast(dmin, st), f2(1e18f));  // st = 0 gives +inf -> 1e18
+    const f2 q0 = dmin * rcp_est(d0), q1 = dmin * rcp_est(d1), q2 = dmin * rcp_est(d2);
+    const f2 z = fmin(dmin * rcp_est(st * s32), f2(1e18f));  // st = 0 gives +inf -> 1e18
     f2 h0, h1, h2;
     if (args.alpha_is_two) {
         h0 = fma(z, z, q0 * q0);
@@ -203,7 +223,7 @@ __device__ __forceinline__ void weights_hi_f2(f2 b0, f2 b1, f2 b2, f2 st, const 
         h1 = f2(__powf(q1.x(), al), __powf(q1.y(), al));
         h2 = f2(__powf(q2.x(), al), __powf(q2.y(), al));
     }
-    const f2 inv = fdiv_fast(f2(1.f), h0 + h1 + h2);
+    const f2 inv = rcp_est(h0 + h1 + h2);  // the sum is at least 1 (the ratio of d_min)
     w1 = h1 * inv;
     w2 = h2 * inv;
     w0 = f2(1.f) - (w1 + w2);
@@ -212,10 +232,10 @@ __device__ __forceinline__ void weights_hi_f2(f2 b0, f2 b1, f2 b2, f2 st, const 
 // Normalised weights for P = 1 (Eq. 1D2ndOrderWeights): w_m proportional to
 // (1 / (beta_m + eps))^alpha, evaluated as ((beta_min + eps) / (beta_m + eps))^alpha <= 1.
 __device__ __forceinline__ void weights_p1_f2(f2 b0, f2 b1, f2 b2, const StepArgs& args, f2& w0, f2& w1, f2& w2) {
-    const f2 eps(args.eps_f), tiny(1.4e-45f);
-    const f2 d0 = fmax(b0 + eps, tiny), d1 = fmax(b1 + eps, tiny), d2 = fmax(b2 + eps, tiny);
+    const f2 eps = scaled_eps(args), s32(4294967296.f);
+    const f2 d0 = fma(b0, s32, eps), d1 = fma(b1, s32, eps), d2 = fma(b2, s32, eps);  // d 2^32
     const f2 dmin = fmin(d0, fmin(d1, d2));
-    const f2 q0 = fdiv_fast(dmin, d0), q1 = fdiv_fast(dmin, d1), q2 = fdiv_fast(dmin, d2);
+    const f2 q0 = dmin * rcp_est(d0), q1 = dmin * rcp_est(d1), q2 = dmin * rcp_est(d2);
     f2 h0, h1, h2;
     if (args.alpha_is_two) {
         h0 = q0 * q0;
@@ -227,7 +247,7 @@ __device__ __forceinline__ void weights_p1_f2(f2 b0, f2 b1, f2 b2, const StepArg
         h1 = f2(__powf(q1.x(), al), __powf(q1.y(), al));
         h2 = f2(__powf(q2.x(), al), __powf(q2.y(), al));
     }
-    const f2 inv = fdiv_fast(f2(1.f), h0 + h1 + h2);
+    const f2 inv = rcp_est(h0 + h1 + h2);  // at least 1
     w1 = h1 * inv;
     w2 = h2 * inv;
     w0 = f2(1.f) - (w1 + w2);
@@ -270,54 +290,6 @@ __device__ __forceinline__ void limit_deviation_f2(f2 (&d)[P + 1], f2 dl, f2 dr,
     d[0] *= w0;
     d[1] = fma(w0, d[1], fma(w1, s1, w2 * s2));
     sfor<2, P + 1>([&](auto Ki) { d[decltype(Ki)::value] *= w0; });
-}
-
-// ------------------------------------------------------ Euler characteristics, paired
-
-// Eigenvectors of the Euler flux Jacobian at a state (the L and R of
-// euler_eigen, Sec. 4) kept as the scalars their products need:
-//   L d = (X - Y, d_0 - 2 X, X + Y),  X = (b1/2) (u^2/2 d_0 - u d_1 + d_2),
-//                                     Y = (1/(2c)) (d_1 - u d_0),
-//   R w = (s + w_1, u (s + w_1) + m, H s + u m + u^2/2 w_1),
-//         s = w_0 + w_2,  m = c (w_2 - w_0),
-// with b1 = (gamma - 1) / c^2 and H = (E + p) / rho.  Eight paired
-// instructions per product and seven pairs of registers for the basis.
-struct EulerChar2 {
-    f2 u, nu, hu2, c, H, b1h, ich;
-
-    __device__ __forceinline__ void left(f2 d0, f2 d1, f2 d2, f2 (&w)[3]) const {
-        const f2 X = b1h * fma(nu, d1, fma(hu2, d0, d2));
-        const f2 Y = ich * fma(nu, d0, d1);
-        w[0] = X - Y;
-        w[1] = fma(f2(-2.f), X, d0);
-        w[2] = X + Y;
-    }
-    __device__ __forceinline__ void right(f2 w0, f2 w1, f2 w2, f2& d0, f2& d1, f2& d2) const {
-        const f2 s = w0 + w2;
-        const f2 m = c * (w2 - w0);
-        d0 = s + w1;
-        d1 = fma(u, d0, m);
-        d2 = fma(H, s, fma(u, m, hu2 * w1));
-    }
-};
-
-// Basis at the conserved state U; false for a non-positive density or
-// pressure.  Same arithmetic as euler_eigen for the scalars it shares.
-__device__ __forceinline__ bool euler_char(const f2 (&U)[3], f2 gamma, EulerChar2& E) {
-    const f2 irho = recip(U[0]);
-    const f2 u = U[1] * irho;
-    const f2 g1 = gamma - f2(1.f);
-    const f2 p = g1 * fma(f2(-0.5f) * U[1], u, U[2]);
-    const f2 c2 = gamma * p * irho;
-    const f2 ic = rsqrt_approx(c2);
-    E.u = u;
-    E.nu = -u;
-    E.hu2 = f2(0.5f) * u * u;
-    E.c = c2 * ic;
-    E.H = (U[2] + p) * irho;
-    E.b1h = f2(0.5f) * g1 * ic * ic;
-    E.ich = f2(0.5f) * ic;
-    return all_pos(U[0]) && all_pos(p);
 }
 
 // ------------------------------------------------------ the paired tile
@@ -462,8 +434,8 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
             limit_deviation_f2<P>(d[0], dl[0], dr[0], args);
         } else {
             f2 ubf[3] = {ubn[0].hi, ubn[1].hi, ubn[2].hi};
-            EulerChar2 E;
-            if (!euler_char(ubf, f2(args.gamma_f), E)) err |= ERR_POSITIVITY;
+            EulerChar<f2> E;
+            if (!euler_char<f2>(ubf, f2(args.gamma_f), E)) err |= ERR_POSITIVITY;
             f2 cd[3][K], cdl[3], cdr[3];
             E.left(dl[0], dl[1], dl[2], cdl);
             E.left(dr[0], dr[1], dr[2], cdr);
