@@ -34,14 +34,32 @@ __host__ __device__ constexpr ffc ffc_of(double x) { return ffc{(float)x, (float
 __host__ __device__ constexpr ffc inv_fact_c(int k) {
     return k == 2 ? ffc_of(0.5) : k == 3 ? ffc_of(1.0 / 6.0) : k == 4 ? ffc_of(1.0 / 24.0) : ffc_of(1.0);
 }
-// k!, k = 0..4
-__host__ __device__ constexpr unsigned fact_u(int k) { return k == 2 ? 2u : k == 3 ? 6u : k == 4 ? 24u : 1u; }
 // weight of u_kx in the cell average, 1/((k+1)! 2^k) (Eq. SubEq:1DCellAVG; even k >= 2)
 __host__ __device__ constexpr ffc avg_from_u_c(int k) { return k == 2 ? ffc_of(1.0 / 24.0) : ffc_of(1.0 / 1920.0); }
 // weight of e_k in the cell average, 1/((k+1) 2^k) (even k >= 2)
 __host__ __device__ constexpr ffc avg_from_e_c(int k) { return k == 2 ? ffc_of(1.0 / 12.0) : ffc_of(1.0 / 80.0); }
 
 __device__ __forceinline__ ff ff_mul_c(ff a, ffc c) { return ff_mul(a, ff{c.hi, c.lo}); }
+
+// The rare cases, kept out of line: inlined, the compiler would predicate
+// them into every call, and their FP64 instructions would occupy the FP64
+// pipe even when predicated off.
+__device__ __noinline__ ff split_double_hw(double d) {
+    ff r;
+    split_double(d, r.hi, r.lo);
+    return r;
+}
+__device__ __noinline__ double float_times_hw(float f, double m) { return (double)f * m; }
+
+// n < 2^29 rounded to the nearest float, without an integer-to-float
+// conversion instruction (those run on the FP64 pipe of this GPU): each
+// 23-bit part is read exactly as (2^23 + part) - 2^23, and one FMA joins them
+// with a single rounding.
+__device__ __forceinline__ float uint29_to_float(unsigned n) {
+    const float lo = __uint_as_float(0x4B000000u | (n & 0x7fffffu)) - 8388608.f;
+    const float hi = __uint_as_float(0x4B000000u | (n >> 23)) - 8388608.f;
+    return fmaf(hi, 8388608.f, lo);
+}
 
 // d = hi + lo: hi = d truncated to 24 significant bits, lo = the remaining
 // bits rounded to FP32 (|lo| < ulp(hi)); integer operations only for
@@ -51,28 +69,27 @@ __device__ __forceinline__ ff split_double_bits(double d) {
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
     if ((b << 1) == 0ull) return ff{__uint_as_float(sign), 0.f};
     const int e = (int)((b >> 52) & 0x7ffull) - 1023;
-    if (e < -74 || e > 127) {
-        ff r;
-        split_double(d, r.hi, r.lo);
-        return r;
-    }
+    if (e < -74 || e > 127) return split_double_hw(d);
     const unsigned long long mant = b & ((1ull << 52) - 1ull);
     const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));
     // lo = +-rest * 2^(e - 52): rest (< 2^29) rounded to FP32, times a power of two
     const unsigned rest = (unsigned)(mant & ((1ull << 29) - 1ull));
     const float scale = __uint_as_float(sign | ((unsigned)(e - 52 + 127) << 23));
-    return ff{hi, __uint2float_rn(rest) * scale};
+    return ff{hi, uint29_to_float(rest) * scale};
 }
 
-// f * m exactly as a double, for an integer 1 <= m <= 24: the 24-bit
-// significand times m (< 2^29) renormalised with integer operations.
-__device__ __forceinline__ double float_times_uint_exact(float f, unsigned m) {
+// f * M exactly as a double, for an integer 1 <= M <= 24: the 24-bit
+// significand times M (< 2^29) renormalised with integer operations (its
+// leading bit is 23 + floor(log2 M) or one above).
+template <unsigned M>
+__device__ __forceinline__ double float_times_exact(float f) {
+    constexpr int L0 = 23 + (M >= 16 ? 4 : M >= 8 ? 3 : M >= 4 ? 2 : M >= 2 ? 1 : 0);
     const unsigned u = __float_as_uint(f);
     if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));  // +-0
     const unsigned ex = (u >> 23) & 0xffu;
-    if (ex == 0u || ex == 0xffu) return (double)f * (double)m;  // subnormal, inf, NaN
-    const unsigned long long n = (unsigned long long)((u & 0x7fffffu) | 0x800000u) * m;
-    const int lead = 63 - __clzll((long long)n);  // 23..28
+    if (ex == 0u || ex == 0xffu) return float_times_hw(f, (double)M);  // subnormal, inf, NaN
+    const unsigned long long n = (unsigned long long)((u & 0x7fffffu) | 0x800000u) * M;
+    const int lead = L0 + (int)(n >> (L0 + 1));  // n < 2^(L0 + 2)
     const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
                                     ((unsigned long long)(lead + (int)ex - 150 + 1023) << 52) |
                                     ((n << (52 - lead)) & ((1ull << 52) - 1ull));
@@ -102,10 +119,11 @@ __device__ __forceinline__ void mixed_to_host(ff ubar, const float (&e)[K], doub
     ff u = ubar;
 #pragma unroll
     for (int k = 1; k < K; ++k) {
-        q[k] = float_times_uint_exact(e[k], fact_u(k));
+        q[k] = k == 2 ? float_times_exact<2>(e[k]) : k == 3 ? float_times_exact<6>(e[k])
+               : k == 4 ? float_times_exact<24>(e[k]) : float_times_exact<1>(e[k]);
         if ((k & 1) == 0) u = ff_sub(u, ff_mul_c(ff{e[k], 0.f}, avg_from_e_c(k)));
     }
-    q[0] = float_times_uint_exact(u.hi, 1u) + float_times_uint_exact(u.lo, 1u);
+    q[0] = float_times_exact<1>(u.hi) + float_times_exact<1>(u.lo);
 }
 
 }  // namespace wcc

@@ -505,7 +505,7 @@ __global__ void __launch_bounds__(256) stage_speed_mixed(const float* planes, lo
                                                           StepArgs args, int slot) {
     constexpr int NV = nvars(SYS);
     constexpr int NP = P + 2;
-    double m = 0.0;
+    float m = 0.f;  // the largest float speed, converted once (same value as a max over doubles)
     unsigned err = 0u;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x) {
@@ -518,16 +518,16 @@ __global__ void __launch_bounds__(256) stage_speed_mixed(const float* planes, lo
                 corr += planes[(long long)(v * NP + k + 1) * pitch + i] / (float)((k + 1) * (1 << k));
             u0[v] = (planes[(long long)(v * NP) * pitch + i] + planes[(long long)(v * NP + 1) * pitch + i]) - corr;
         }
-        double s = (double)wave_speed<SYS, float>(u0, args, err);
+        float s = wave_speed<SYS, float>(u0, args, err);
         if (s != s) {
-            s = __longlong_as_double(0x7ff0000000000000ll);
+            s = INFINITY;
             err |= ERR_NONFINITE;
         }
-        m = fmax(m, s);
+        m = fmaxf(m, s);
     }
-    m = warp_max<double>(m);
-    if ((threadIdx.x & 31) == 0 && m > 0.0)
-        atomicMax(&args.st->amax_bits[slot], (unsigned long long)__double_as_longlong(m));
+    m = warp_max<float>(m);
+    if ((threadIdx.x & 31) == 0 && m > 0.f)
+        atomicMax(&args.st->amax_bits[slot], (unsigned long long)__double_as_longlong((double)m));
     if (err) atomicOr(&args.st->err, err);
 }
 
