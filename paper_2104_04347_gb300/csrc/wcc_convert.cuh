@@ -44,12 +44,12 @@ __device__ __forceinline__ ff ff_mul_c(ff a, ffc c) { return ff_mul(a, ff{c.hi, 
 // The rare cases, kept out of line: inlined, the compiler would predicate
 // them into every call, and their FP64 instructions would occupy the FP64
 // pipe even when predicated off.
-__device__ __noinline__ ff split_double_hw(double d) {
+static __device__ __noinline__ ff split_double_hw(double d) {
     ff r;
     split_double(d, r.hi, r.lo);
     return r;
 }
-__device__ __noinline__ double float_times_hw(float f, double m) { return (double)f * m; }
+static __device__ __noinline__ double float_times_hw(float f, double m) { return (double)f * m; }
 
 // n < 2^29 rounded to the nearest float, without an integer-to-float
 // conversion instruction (those run on the FP64 pipe of this GPU): each
