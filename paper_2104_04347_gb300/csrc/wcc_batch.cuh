@@ -45,7 +45,9 @@ struct BatchArgs {
 
 
 template <int SYS, int PA, int PB>
-__global__ void __launch_bounds__(kThreadsMixed, kMixedMinCtas) batch_mixed(const BatchArgs b) {
+__global__ void __launch_bounds__(kThreadsMixed, (mixed_min_ctas<PA>() < mixed_min_ctas<PB>() ? mixed_min_ctas<PA>()
+                                                                                            : mixed_min_ctas<PB>()))
+    batch_mixed(const BatchArgs b) {
     constexpr int SA = mixed2_smem_float2<SYS, PA>();
     constexpr int SB = mixed2_smem_float2<SYS, PB>();
     __shared__ float2 rec[SA > SB ? SA : SB];

@@ -43,11 +43,17 @@ constexpr int kThreadsMixed = WCC_MIXED_THREADS;
 constexpr int kTileMixed = 2 * kThreadsMixed - 1;
 
 // Resident CTAs per SM the FP32-mixed kernels are compiled for (register
-// budget 65536 / (kThreadsMixed * kMixedMinCtas) per thread).
-#ifndef WCC_MIXED_MIN_CTAS
-#define WCC_MIXED_MIN_CTAS 5
+// budget 65536 / (kThreadsMixed * CTAs) per thread): the most that still
+// compiles without spills (measured on GB300, Euler): 7 for P <= 2, 6 for
+// P = 3, 5 for P = 4.  WCC_MIXED_MIN_CTAS overrides it for every P.
+template <int P>
+constexpr int mixed_min_ctas() {
+#ifdef WCC_MIXED_MIN_CTAS
+    return WCC_MIXED_MIN_CTAS;
+#else
+    return P <= 2 ? 7 : P == 3 ? 6 : 5;
 #endif
-constexpr int kMixedMinCtas = WCC_MIXED_MIN_CTAS;
+}
 
 // Where one tile reads and writes (one stage of one grid or batch instance).
 struct TileIO {
@@ -323,26 +329,60 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
         const long long base = first_new + t - (io.parity ? 1 : 0);
         const long long pa = parent_index(base, io.n_old, io.bc);
         const long long pb = parent_index(base + kThreadsMixed, io.n_old, io.bc);
+        // record row `row` of variable v for this thread's slots; slot
+        // kThreadsMixed (lane y of thread 0) is also the right parent of new
+        // cell kThreadsMixed - 1 (lane x of the last thread), whose y lane
+        // repeats the value so that the unused lane sees real data
+        auto put = [&](int v, int row, f2 x) {
+            float2* r = rec + v * RV * W + row * W;
+            r[t] = x.v;
+            if (t == 0) r[kThreadsMixed] = make_float2(x.y(), x.y());
+        };
+        auto get = [&](int v, int row) { return f2(rec[v * RV * W + row * W + t]); };
+        // For P >= 3, ubar and lam f(u_0) wait in their record rows (0-1 and
+        // 2-3) while the Cauchy-Kovalewski table holds the registers; for
+        // lower P they fit in registers, which is faster.
+        constexpr bool kPark = P >= 3;
         f2 c[NV][K];
-        ff2 ub[NV], u0[NV];
-        sfor<0, NV>([&](auto V) {
-            constexpr int v = decltype(V)::value;
-            const float* p0 = io.in32 + (long long)(v * NP + 0) * io.pitch;
-            const float* p1 = io.in32 + (long long)(v * NP + 1) * io.pitch;
-            ub[v].hi = f2(__ldg(p0 + pa), __ldg(p0 + pb));
-            ub[v].lo = COMP ? f2(__ldg(p1 + pa), __ldg(p1 + pb)) : f2(0.f);
-            sfor<1, K>([&](auto Ki) {
-                constexpr int k = decltype(Ki)::value;
-                const float* pk = io.in32 + (long long)(v * NP + k + 1) * io.pitch;
-                c[v][k] = f2(__ldg(pk + pa), __ldg(pk + pb));
+        ff2 ub_r[NV], lf_r[NV];
+        {
+            ff2 u0[NV];
+            sfor<0, NV>([&](auto V) {
+                constexpr int v = decltype(V)::value;
+                const float* p0 = io.in32 + (long long)(v * NP + 0) * io.pitch;
+                const float* p1 = io.in32 + (long long)(v * NP + 1) * io.pitch;
+                ff2 ub;
+                ub.hi = f2(__ldg(p0 + pa), __ldg(p0 + pb));
+                ub.lo = COMP ? f2(__ldg(p1 + pa), __ldg(p1 + pb)) : f2(0.f);
+                sfor<1, K>([&](auto Ki) {
+                    constexpr int k = decltype(Ki)::value;
+                    const float* pk = io.in32 + (long long)(v * NP + k + 1) * io.pitch;
+                    c[v][k] = f2(__ldg(pk + pa), __ldg(pk + pb));
+                });
+                u0[v] = A::add(ub, -average_minus_centre<P>(c[v]));
+                c[v][0] = u0[v].hi;
+                if constexpr (kPark) {
+                    put(v, 0, ub.hi);
+                    if constexpr (COMP) put(v, 1, ub.lo);
+                } else {
+                    ub_r[v] = ub;
+                }
             });
-            u0[v] = A::add(ub[v], -average_minus_centre<P>(c[v]));
-            c[v][0] = u0[v].hi;
-        });
+            ff2 f0[NV];
+            flux_ff2<SYS, COMP>(u0, args, f0);
+            sfor<0, NV>([&](auto V) {
+                constexpr int v = decltype(V)::value;
+                const ff2 lf = A::mul(f0[v], lam2);
+                if constexpr (kPark) {
+                    put(v, 2, lf.hi);
+                    if constexpr (COMP) put(v, 3, lf.lo);
+                } else {
+                    lf_r[v] = lf;
+                }
+            });
+        }
         f2 X[NV][K][K], F0[NV][K];
         ck_table<SYS, P, f2>(c, lam2.hi, args, X, F0);
-        ff2 f0[NV];
-        flux_ff2<SYS, COMP>(u0, args, f0);
         // Record of the parent (Eqs. Cal1DFlux, SubEq:1DCellAVGR/L,
         // SubEq:Cal_1D_Derivatives_4): its cell average ubar and
         //   A   = ubar / 2 + g,  g = lam fbar + dodd / 2, the part of ubar that
@@ -367,31 +407,27 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
                 if constexpr (k & 1) dodd = fma(f2((float)(1.0 / ((k + 1.0) * cpow2(k)))), c[v][k], dodd);
             });
             const f2 h = fma(lam2.hi, fhigh, f2(0.5f) * dodd);
-            const ff2 Ac = A::add(ff2_scale(ub[v], 0.5f), A::add(A::mul(f0[v], lam2), h));
+            ff2 ub, lf;
+            if constexpr (kPark) {
+                ub = ff2{get(v, 0), COMP ? get(v, 1) : f2(0.f)};
+                lf = ff2{get(v, 2), COMP ? get(v, 3) : f2(0.f)};
+            } else {
+                ub = ub_r[v];
+                lf = lf_r[v];
+                put(v, 0, ub.hi);
+                if constexpr (COMP) put(v, 1, ub.lo);
+            }
+            const ff2 Ac = A::add(ff2_scale(ub, 0.5f), A::add(lf, h));
+            put(v, 2, Ac.hi);
+            if constexpr (COMP) put(v, 3, Ac.lo);
             f2 vt0(0.f);
             sfor<1, K>([&](auto Mi) { vt0 += X[v][0][decltype(Mi)::value]; });
-            float2* r = rec + v * RV * W;
-            f2 vals[RV];
-            vals[0] = ub[v].hi;
-            vals[1] = ub[v].lo;
-            vals[2] = Ac.hi;
-            vals[3] = Ac.lo;
-            vals[4] = vt0 - average_minus_centre<P>(c[v]);
+            put(v, 4, vt0 - average_minus_centre<P>(c[v]));
             sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
                 f2 s = X[v][k][0];
                 sfor<1, K - k>([&](auto Mi) { s += X[v][k][decltype(Mi)::value]; });
-                vals[4 + k] = s;
-            });
-            sfor<0, RV>([&](auto Ri) {
-                constexpr int row = decltype(Ri)::value;
-                if constexpr (COMP || (row != 1 && row != 3)) {
-                    r[row * W + t] = vals[row].v;
-                    // slot kThreadsMixed (lane y of thread 0) is also the right parent of
-                    // new cell kThreadsMixed - 1 (lane x of the last thread); its y lane
-                    // repeats the value so that the unused lane sees real data
-                    if (t == 0) r[row * W + kThreadsMixed] = make_float2(vals[row].y(), vals[row].y());
-                }
+                put(v, 4 + k, s);
             });
         });
     }
@@ -488,7 +524,7 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
 }
 
 template <int SYS, int P, bool COMP = true>
-__global__ void __launch_bounds__(kThreadsMixed, kMixedMinCtas) halfstep_mixed2(const StepArgs args) {
+__global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_mixed2(const StepArgs args) {
     __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
     const StepSize z = step_size(args);
     const TileIO io{args.in32, args.out32, args.pitch, args.n_old, args.n_new,
