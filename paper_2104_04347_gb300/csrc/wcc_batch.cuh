@@ -66,10 +66,11 @@ __global__ void __launch_bounds__(kThreadsMixed, (mixed_min_ctas<PA>() < mixed_m
         StepArgs ph = b.phys;  // per-instance boundary and mesh width
         ph.bc = I.bc;
         ph.dx = I.dx;
+        // both degrees share one register budget: both park (see mixed_tile2)
         if (g == 0)
-            mixed_tile2<SYS, PA, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
+            mixed_tile2<SYS, PA, true, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
         else
-            mixed_tile2<SYS, PB, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
+            mixed_tile2<SYS, PB, true, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
         reduce_and_finish<float, kThreadsMixed>(speed, err, z.dt, st, ntiles, b.hist + (long long)i * b.hist_cap, b.hist_cap,
                                  b.parity, 1, b.phys.cfl, I.dx);
     }

@@ -311,7 +311,7 @@ constexpr int mixed2_smem_float2() {
 // of shared memory.  Returns the larger of the thread's two cell speeds
 // (cells outside the stage count as 0) and error bits; the caller
 // synchronises the block before rec is written again.
-template <int SYS, int P, bool COMP>
+template <int SYS, int P, bool COMP, bool PARK = (P >= 3)>
 __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, const StepArgs& args, float2* rec,
                                             float& speed, unsigned& err) {
     using A = FF<COMP>;
@@ -339,10 +339,11 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
             if (t == 0) r[kThreadsMixed] = make_float2(x.y(), x.y());
         };
         auto get = [&](int v, int row) { return f2(rec[v * RV * W + row * W + t]); };
-        // For P >= 3, ubar and lam f(u_0) wait in their record rows (0-1 and
-        // 2-3) while the Cauchy-Kovalewski table holds the registers; for
-        // lower P they fit in registers, which is faster.
-        constexpr bool kPark = P >= 3;
+        // With PARK (the default for P >= 3), ubar and lam f(u_0) wait in
+        // their record rows (0-1 and 2-3) while the Cauchy-Kovalewski table
+        // holds the registers; for lower P alone they fit in registers, which
+        // is faster.
+        constexpr bool kPark = PARK;
         f2 c[NV][K];
         ff2 ub_r[NV], lf_r[NV];
         {
