@@ -90,36 +90,8 @@ __global__ void __launch_bounds__(kConvThreads) planes_to_aos_fp64(const double*
     }
 }
 
-// FP32-mixed / FP32: per (cell, var) the cell average (Eq. SubEq:1DCellAVG:
-// ubar = sum_{k even} u_kx / ((k+1)! 2^k)) as a float-float pair (plain FP32
-// keeps only its rounded hi part) and e_k = u_kx / k! in FP32 for k >= 1;
-// FP32 and integer arithmetic only (wcc_convert.cuh).
-template <int K>
-__global__ void __launch_bounds__(kConvThreads) aos_to_planes_mixed(const double* __restrict__ aos, long long n,
-                                                                    int nv, long long pitch,
-                                                                    float* __restrict__ planes, int keep_lo) {
-    __shared__ double sm[kConvMaxElems];
-    constexpr int NP = K + 1;
-    const int row = nv * K;
-    for (long long c0 = (long long)blockIdx.x * kConvCells; c0 < n; c0 += (long long)gridDim.x * kConvCells) {
-        const int m = (int)min((long long)kConvCells, n - c0);
-        tile_load(aos, c0, m, row, sm);
-        __syncthreads();
-        for (int i = threadIdx.x; i < kConvCells * nv; i += kConvThreads) {
-            const int c = i % kConvCells, v = i / kConvCells;
-            if (c >= m) continue;
-            float e[K];
-            const ff u = host_to_mixed<K>(sm + c * row + v * K, e);
-            float* pl = planes + (long long)(v * NP) * pitch + c0 + c;
-            pl[0] = u.hi;
-            pl[pitch] = keep_lo ? u.lo : 0.f;
-#pragma unroll
-            for (int k = 1; k < K; ++k) pl[(long long)(k + 1) * pitch] = e[k];
-        }
-        __syncthreads();
-    }
-}
-
+// FP32-mixed / FP32 host layout from the planes (the set-up direction is
+// load_stage_mixed, which also takes the stage's CFL bound).
 template <int K>
 __global__ void __launch_bounds__(kConvThreads) planes_to_aos_mixed(const float* __restrict__ planes, long long n,
                                                                     int nv, long long pitch,
@@ -144,19 +116,7 @@ __global__ void __launch_bounds__(kConvThreads) planes_to_aos_mixed(const float*
     }
 }
 
-// Launch helpers: K = P + 1 as a template argument.
-cudaError_t launch_aos_to_planes_mixed(int K, unsigned grid, cudaStream_t s, const double* aos, long long n, int nv,
-                                       long long pitch, float* planes, int keep_lo) {
-    switch (K) {
-        case 2: aos_to_planes_mixed<2><<<grid, kConvThreads, 0, s>>>(aos, n, nv, pitch, planes, keep_lo); break;
-        case 3: aos_to_planes_mixed<3><<<grid, kConvThreads, 0, s>>>(aos, n, nv, pitch, planes, keep_lo); break;
-        case 4: aos_to_planes_mixed<4><<<grid, kConvThreads, 0, s>>>(aos, n, nv, pitch, planes, keep_lo); break;
-        case 5: aos_to_planes_mixed<5><<<grid, kConvThreads, 0, s>>>(aos, n, nv, pitch, planes, keep_lo); break;
-        default: return cudaErrorInvalidValue;
-    }
-    return cudaGetLastError();
-}
-
+// Launch helper: K = P + 1 as a template argument.
 cudaError_t launch_planes_to_aos_mixed(int K, unsigned grid, cudaStream_t s, const float* planes, long long n, int nv,
                                        long long pitch, double* aos) {
     switch (K) {
@@ -493,33 +453,31 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     h->parity = 0;
     h->steps = 0;
     const bool mixed = h->opt.precision != WCC_FP64;
+    WCC_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
+    StepArgs a = make_args(h, 0, 0, 0.0, 0.0);
+    cudaError_t e;
     if (mixed) {
-        WCC_CHECK(h, launch_aos_to_planes_mixed(h->K, conv_grid(n), h->stream, src, n, h->nv, h->pitch, h->s32[0],
-                                                h->opt.precision == WCC_FP32_MIXED));
+        // conversion and the stage's CFL bound in one kernel
+        const int keep_lo = h->opt.precision == WCC_FP32_MIXED;
+        switch (h->system) {
+            case WCC_ADVECTION: e = launch_load_stage_mixed<ADVECTION>(h->P, src, n, h->pitch, h->s32[0], keep_lo, a, 0, h->stream); break;
+            case WCC_BURGERS: e = launch_load_stage_mixed<BURGERS>(h->P, src, n, h->pitch, h->s32[0], keep_lo, a, 0, h->stream); break;
+            default: e = launch_load_stage_mixed<EULER>(h->P, src, n, h->pitch, h->s32[0], keep_lo, a, 0, h->stream); break;
+        }
+        h->launches += 1;
     } else {
         aos_to_planes_fp64<<<conv_grid(n), kConvThreads, 0, h->stream>>>(src, n, h->nv, h->K, h->pitch,
                                                                               h->s64[0]);
         WCC_CHECK(h, cudaGetLastError());
-    }
-    WCC_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
-    StepArgs a = make_args(h, 0, 0, 0.0, 0.0);
-    cudaError_t e;
-    const long long var_stride = (long long)h->K * h->pitch;
-    if (mixed) {
-        switch (h->system) {
-            case WCC_ADVECTION: e = launch_stage_speed_mixed<ADVECTION>(h->P, h->s32[0], h->pitch, n, a, 0, h->stream); break;
-            case WCC_BURGERS: e = launch_stage_speed_mixed<BURGERS>(h->P, h->s32[0], h->pitch, n, a, 0, h->stream); break;
-            default: e = launch_stage_speed_mixed<EULER>(h->P, h->s32[0], h->pitch, n, a, 0, h->stream); break;
-        }
-    } else {
+        const long long var_stride = (long long)h->K * h->pitch;
         switch (h->system) {
             case WCC_ADVECTION: e = launch_stage_speed<ADVECTION>(h->s64[0], var_stride, n, a, 0, h->stream); break;
             case WCC_BURGERS: e = launch_stage_speed<BURGERS>(h->s64[0], var_stride, n, a, 0, h->stream); break;
             default: e = launch_stage_speed<EULER>(h->s64[0], var_stride, n, a, 0, h->stream); break;
         }
+        h->launches += 2;
     }
-    if (e != cudaSuccess) return cuda_fail(h, e, "stage speed launch");
-    h->launches += 2;
+    if (e != cudaSuccess) return cuda_fail(h, e, "stage set-up launch");
     h->initialised = true;
     DevState s;
     int rc = read_state(h, &s);

@@ -19,10 +19,13 @@ template <int SYS>
 cudaError_t launch_stage_speed(const double* u0planes, long long var_stride, long long n,
                                const StepArgs& args, int slot, cudaStream_t stream);
 
-// Same for an FP32-mixed stage (planes [v][ubar hi, ubar lo, e_1..e_P][cell]).
+// Set-up of an FP32-mixed stage (planes [v][ubar hi, ubar lo, e_1..e_P][cell],
+// plane pitch `pitch`) from n cells of host-layout DOFs already in device
+// memory (aos), and its largest characteristic speed into st->amax_bits[slot]
+// (zero beforehand), in one pass.  keep_lo = 0 stores the plain FP32 average.
 template <int SYS>
-cudaError_t launch_stage_speed_mixed(int P, const float* planes, long long pitch, long long n,
-                                     const StepArgs& args, int slot, cudaStream_t stream);
+cudaError_t launch_load_stage_mixed(int P, const double* aos, long long n, long long pitch, float* planes,
+                                    int keep_lo, const StepArgs& args, int slot, cudaStream_t stream);
 
 struct BatchArgs;
 enum { BATCH_STEP = 0, BATCH_SPEED = 1, BATCH_CONVERT = 2 };

@@ -29,6 +29,7 @@
 // each.
 #pragma once
 
+#include "wcc_convert.cuh"
 #include "wcc_f2.cuh"
 #include "wcc_ff.cuh"
 #include "wcc_halfstep.cuh"
@@ -536,31 +537,56 @@ __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_m
     finish_halfstep<float, kThreadsMixed>(speed, err, z.dt, args);
 }
 
-// Largest characteristic speed of a stored FP32-mixed stage.
+// Set-up of an FP32-mixed stage in one pass: the host-layout DOFs (already in
+// device memory) are converted tile by tile through shared memory with the
+// conversions of wcc_convert.cuh (plain FP32 keeps only the rounded
+// average), and the largest characteristic speed at the centre values of the
+// stored planes goes to st->amax_bits[slot] (zero beforehand).
+constexpr int kLoadCells = 128;  // cells per tile = threads per CTA
+
 template <int SYS, int P>
-__global__ void __launch_bounds__(256) stage_speed_mixed(const float* planes, long long pitch, long long n,
-                                                          StepArgs args, int slot) {
+__global__ void __launch_bounds__(kLoadCells) load_stage_mixed(const double* __restrict__ aos, long long n,
+                                                               long long pitch, float* __restrict__ planes,
+                                                               int keep_lo, StepArgs args, int slot) {
     constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
     constexpr int NP = P + 2;
-    float m = 0.f;  // the largest float speed, converted once (same value as a max over doubles)
+    constexpr int ROW = NV * K;
+    __shared__ double sm[kLoadCells * ROW];
+    float m = 0.f;  // the largest float speed, converted once at the end
     unsigned err = 0u;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x) {
-        float u0[NV];
+    for (long long c0 = (long long)blockIdx.x * kLoadCells; c0 < n; c0 += (long long)gridDim.x * kLoadCells) {
+        const int cnt = (int)min((long long)kLoadCells, n - c0);
+        const double* src = aos + c0 * ROW;
+        for (int i = threadIdx.x; i < cnt * ROW; i += kLoadCells) sm[i] = src[i];
+        __syncthreads();
+        const int c = threadIdx.x;
+        if (c < cnt) {
+            float u0[NV];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
-            float corr = 0.f;
+            for (int v = 0; v < NV; ++v) {
+                float e[K];
+                const ff u = host_to_mixed<K>(sm + c * ROW + v * K, e);
+                const float lo = keep_lo ? u.lo : 0.f;
+                float* pl = planes + (long long)(v * NP) * pitch + c0 + c;
+                pl[0] = u.hi;
+                pl[pitch] = lo;
 #pragma unroll
-            for (int k = 2; k <= P; k += 2)
-                corr += planes[(long long)(v * NP + k + 1) * pitch + i] / (float)((k + 1) * (1 << k));
-            u0[v] = (planes[(long long)(v * NP) * pitch + i] + planes[(long long)(v * NP + 1) * pitch + i]) - corr;
+                for (int k = 1; k < K; ++k) pl[(long long)(k + 1) * pitch] = e[k];
+                // centre value of the stored cell: average minus the even terms
+                float corr = 0.f;
+#pragma unroll
+                for (int k = 2; k <= P; k += 2) corr += e[k] / (float)((k + 1) * (1 << k));
+                u0[v] = (u.hi + lo) - corr;
+            }
+            float sp = wave_speed<SYS, float>(u0, args, err);
+            if (sp != sp) {
+                sp = INFINITY;
+                err |= ERR_NONFINITE;
+            }
+            m = fmaxf(m, sp);
         }
-        float s = wave_speed<SYS, float>(u0, args, err);
-        if (s != s) {
-            s = INFINITY;
-            err |= ERR_NONFINITE;
-        }
-        m = fmaxf(m, s);
+        __syncthreads();
     }
     m = warp_max<float>(m);
     if ((threadIdx.x & 31) == 0 && m > 0.f)
