@@ -43,15 +43,16 @@ constexpr int kConvCells = 128;                 // cells per tile
 constexpr int kConvThreads = 256;
 constexpr int kConvMaxElems = kConvCells * 3 * 5;  // nv <= 3, K <= 5
 
-// Copies cells [c0, c0 + m) of the host-layout array to / from smem.
-__device__ __forceinline__ void tile_load(const double* __restrict__ aos, long long c0, int m, int row,
-                                          double* sm) {
-    const double* src = aos + c0 * row;
+// Copies cells [c0, c0 + m) of the host-layout array to / from smem (as
+// doubles, or as their bit patterns for the FP32-mixed conversions).
+template <class T>
+__device__ __forceinline__ void tile_load(const T* __restrict__ aos, long long c0, int m, int row, T* sm) {
+    const T* src = aos + c0 * row;
     for (int i = threadIdx.x; i < m * row; i += kConvThreads) sm[i] = src[i];
 }
-__device__ __forceinline__ void tile_store(double* __restrict__ aos, long long c0, int m, int row,
-                                           const double* sm) {
-    double* dst = aos + c0 * row;
+template <class T>
+__device__ __forceinline__ void tile_store(T* __restrict__ aos, long long c0, int m, int row, const T* sm) {
+    T* dst = aos + c0 * row;
     for (int i = threadIdx.x; i < m * row; i += kConvThreads) dst[i] = sm[i];
 }
 
@@ -96,7 +97,7 @@ template <int K>
 __global__ void __launch_bounds__(kConvThreads) planes_to_aos_mixed(const float* __restrict__ planes, long long n,
                                                                     int nv, long long pitch,
                                                                     double* __restrict__ aos) {
-    __shared__ double sm[kConvMaxElems];
+    __shared__ unsigned long long sm[kConvMaxElems];  // DOFs as bit patterns
     constexpr int NP = K + 1;
     const int row = nv * K;
     for (long long c0 = (long long)blockIdx.x * kConvCells; c0 < n; c0 += (long long)gridDim.x * kConvCells) {
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(kConvThreads) planes_to_aos_mixed(const float*
             mixed_to_host<K>(ff{pl[0], pl[pitch]}, e, sm + c * row + v * K);
         }
         __syncthreads();
-        tile_store(aos, c0, m, row, sm);
+        tile_store(reinterpret_cast<unsigned long long*>(aos), c0, m, row, sm);
         __syncthreads();
     }
 }

@@ -128,7 +128,7 @@ __device__ __forceinline__ void convert_cell(double* q, float* pl, long long pit
         float* p = pl + (long long)(v * NP) * pitch + c;
         float e[K];
         if (to_planes) {
-            const ff u = host_to_mixed<K>(q + v * K, e);
+            const ff u = host_to_mixed<K>(reinterpret_cast<const unsigned long long*>(q) + v * K, e);
             p[0] = u.hi;
             p[pitch] = u.lo;
 #pragma unroll
@@ -136,7 +136,7 @@ __device__ __forceinline__ void convert_cell(double* q, float* pl, long long pit
         } else {
 #pragma unroll
             for (int k = 1; k < K; ++k) e[k] = p[(long long)(k + 1) * pitch];
-            mixed_to_host<K>(ff{p[0], p[pitch]}, e, q + v * K);
+            mixed_to_host<K>(ff{p[0], p[pitch]}, e, reinterpret_cast<unsigned long long*>(q) + v * K);
         }
     }
 }

@@ -15,7 +15,10 @@
 //     as float-float products, so the cell average keeps float-float accuracy
 //     (a few units of 2^-48).
 // Values outside the range where these are exact (zero aside: subnormal,
-// tiny, huge, inf, NaN) take the hardware conversion, which is rare.
+// tiny, huge, inf, NaN) take the hardware conversion, which is rare.  The
+// doubles travel as 64-bit integers (their bit patterns): held as `double`,
+// they kept the FP64 pipe two-thirds busy in the conversion kernels although
+// no FP64 arithmetic ran.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -61,15 +64,14 @@ __device__ __forceinline__ float uint29_to_float(unsigned n) {
     return fmaf(hi, 8388608.f, lo);
 }
 
-// d = hi + lo: hi = d truncated to 24 significant bits, lo = the remaining
-// bits rounded to FP32 (|lo| < ulp(hi)); integer operations only for
-// 2^-74 <= |d| < 2^128 and for zero.
-__device__ __forceinline__ ff split_double_bits(double d) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+// The double with bit pattern b as hi + lo: hi = b truncated to 24
+// significant bits, lo = the remaining bits rounded to FP32 (|lo| < ulp(hi));
+// integer operations only for 2^-74 <= |d| < 2^128 and for zero.
+__device__ __forceinline__ ff split_double_bits(unsigned long long b) {
     const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
     if ((b << 1) == 0ull) return ff{__uint_as_float(sign), 0.f};
     const int e = (int)((b >> 52) & 0x7ffull) - 1023;
-    if (e < -74 || e > 127) return split_double_hw(d);
+    if (e < -74 || e > 127) return split_double_hw(__longlong_as_double((long long)b));
     const unsigned long long mant = b & ((1ull << 52) - 1ull);
     const float hi = __uint_as_float(sign | ((unsigned)(e + 127) << 23) | (unsigned)(mant >> 29));
     // lo = +-rest * 2^(e - 52): rest (< 2^29) rounded to FP32, times a power of two
@@ -78,29 +80,30 @@ __device__ __forceinline__ ff split_double_bits(double d) {
     return ff{hi, uint29_to_float(rest) * scale};
 }
 
-// f * M exactly as a double, for an integer 1 <= M <= 24: the 24-bit
-// significand times M (< 2^29) renormalised with integer operations (its
-// leading bit is 23 + floor(log2 M) or one above).
+// The bit pattern of f * M exactly as a double, for an integer 1 <= M <= 24:
+// the 24-bit significand times M (< 2^29) renormalised with integer
+// operations (its leading bit is 23 + floor(log2 M) or one above).
 template <unsigned M>
-__device__ __forceinline__ double float_times_exact(float f) {
+__device__ __forceinline__ unsigned long long float_times_exact(float f) {
     constexpr int L0 = 23 + (M >= 16 ? 4 : M >= 8 ? 3 : M >= 4 ? 2 : M >= 2 ? 1 : 0);
     const unsigned u = __float_as_uint(f);
-    if ((u << 1) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));  // +-0
+    if ((u << 1) == 0u) return (unsigned long long)u << 32;  // +-0
     const unsigned ex = (u >> 23) & 0xffu;
-    if (ex == 0u || ex == 0xffu) return float_times_hw(f, (double)M);  // subnormal, inf, NaN
+    if (ex == 0u || ex == 0xffu)  // subnormal, inf, NaN
+        return (unsigned long long)__double_as_longlong(float_times_hw(f, (double)M));
     const unsigned long long n = (unsigned long long)((u & 0x7fffffu) | 0x800000u) * M;
     const int lead = L0 + (int)(n >> (L0 + 1));  // n < 2^(L0 + 2)
     const unsigned long long bits = ((unsigned long long)(u & 0x80000000u) << 32) |
                                     ((unsigned long long)(lead + (int)ex - 150 + 1023) << 52) |
                                     ((n << (52 - lead)) & ((1ull << 52) - 1ull));
-    return __longlong_as_double((long long)bits);
+    return bits;
 }
 
 // The host-layout DOFs q[0..K-1] of one (cell, variable) -> the device
 // values: the cell average ubar = sum over even k of q_k / ((k+1)! 2^k) as a
 // float-float (normalised), and e_k = q_k / k! rounded to FP32, k >= 1.
 template <int K>
-__device__ __forceinline__ ff host_to_mixed(const double* q, float (&e)[K]) {
+__device__ __forceinline__ ff host_to_mixed(const unsigned long long* q, float (&e)[K]) {
     ff u = split_double_bits(q[0]);
 #pragma unroll
     for (int k = 1; k < K; ++k) {
@@ -111,11 +114,11 @@ __device__ __forceinline__ ff host_to_mixed(const double* q, float (&e)[K]) {
     return fast_two_sum(u.hi, u.lo);
 }
 
-// The device values of one (cell, variable) -> host-layout DOFs: q_k = e_k k!
-// (exact), q_0 = ubar - sum over even k of e_k / ((k+1) 2^k) (float-float,
-// then one FP64 add to form the double).
+// The device values of one (cell, variable) -> host-layout DOFs (bit
+// patterns): q_k = e_k k! (exact), q_0 = ubar - sum over even k of
+// e_k / ((k+1) 2^k) (float-float, then one FP64 add to form the double).
 template <int K>
-__device__ __forceinline__ void mixed_to_host(ff ubar, const float (&e)[K], double* q) {
+__device__ __forceinline__ void mixed_to_host(ff ubar, const float (&e)[K], unsigned long long* q) {
     ff u = ubar;
 #pragma unroll
     for (int k = 1; k < K; ++k) {
@@ -123,7 +126,9 @@ __device__ __forceinline__ void mixed_to_host(ff ubar, const float (&e)[K], doub
                : k == 4 ? float_times_exact<24>(e[k]) : float_times_exact<1>(e[k]);
         if ((k & 1) == 0) u = ff_sub(u, ff_mul_c(ff{e[k], 0.f}, avg_from_e_c(k)));
     }
-    q[0] = float_times_exact<1>(u.hi) + float_times_exact<1>(u.lo);
+    q[0] = (unsigned long long)__double_as_longlong(
+        __longlong_as_double((long long)float_times_exact<1>(u.hi)) +
+        __longlong_as_double((long long)float_times_exact<1>(u.lo)));
 }
 
 }  // namespace wcc

@@ -552,12 +552,12 @@ __global__ void __launch_bounds__(kLoadCells) load_stage_mixed(const double* __r
     constexpr int K = P + 1;
     constexpr int NP = P + 2;
     constexpr int ROW = NV * K;
-    __shared__ double sm[kLoadCells * ROW];
+    __shared__ unsigned long long sm[kLoadCells * ROW];  // DOFs as bit patterns
     float m = 0.f;  // the largest float speed, converted once at the end
     unsigned err = 0u;
     for (long long c0 = (long long)blockIdx.x * kLoadCells; c0 < n; c0 += (long long)gridDim.x * kLoadCells) {
         const int cnt = (int)min((long long)kLoadCells, n - c0);
-        const double* src = aos + c0 * ROW;
+        const unsigned long long* src = reinterpret_cast<const unsigned long long*>(aos) + c0 * ROW;
         for (int i = threadIdx.x; i < cnt * ROW; i += kLoadCells) sm[i] = src[i];
         __syncthreads();
         const int c = threadIdx.x;
