@@ -432,8 +432,10 @@ def run_wcc(args, rank, world):
     clk = clocks.stop()
 
     # ---- end to end through the public API with host buffers (headline precision)
+    # up to 10 steps per in-flight problem, so that filling and draining the
+    # pipeline of problems is a small part of the timed region
     e2e = e2e_bench(wcc, pr, wcc.FP64 if args.precision == "fp64" else wcc.FP32_MIXED, cells_per_step,
-                    max(2, min(args.steps, 5)), dev, barrier)
+                    max(4, min(args.steps, 10)), dev, barrier)
 
     fp64_peak_meas = wcc.measure_fp_peak(wcc.FP64)
     fp32_peak_meas = wcc.measure_fp_peak(wcc.FP32_MIXED)
