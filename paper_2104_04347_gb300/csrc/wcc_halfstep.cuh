@@ -79,41 +79,46 @@ template <class T, int NT = kThreads>
 __device__ __forceinline__ void reduce_and_finish(T speed, unsigned err, double dt, DevState* st, long long ctas,
                                                   double* hist, long long hist_cap, int parity, int cfl_mode,
                                                   double cfl, double dx) {
+    // One block barrier: the warps' maxima and error bits meet in shared
+    // memory, thread 0 combines them, posts them and counts the CTA; the CTA
+    // that counts last finishes the launch's bookkeeping.  The barrier also
+    // guarantees that every warp is done with the tile's shared records.
     __shared__ T s_max[NT / 32];
-    __shared__ unsigned s_err;
-    __shared__ int s_last;
-    if (threadIdx.x == 0) s_err = 0u;
-    __syncthreads();
+    __shared__ unsigned s_err[NT / 32];
     // NaN must win the max: map it to +Inf and flag it
     if (speed != speed) {
         speed = (T)INFINITY;
         err |= ERR_NONFINITE;
     }
     speed = warp_max<T>(speed);
-    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = speed;
-    if (err) atomicOr(&s_err, err);
+    err = __reduce_or_sync(0xffffffffu, err);
+    if ((threadIdx.x & 31) == 0) {
+        s_max[threadIdx.x >> 5] = speed;
+        s_err[threadIdx.x >> 5] = err;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
         T m = s_max[0];
+        unsigned e = s_err[0];
 #pragma unroll
-        for (int w = 1; w < NT / 32; ++w) m = fmax(m, s_max[w]);
+        for (int w = 1; w < NT / 32; ++w) {
+            m = fmax(m, s_max[w]);
+            e |= s_err[w];
+        }
         if constexpr (sizeof(T) == 8) {
             if (m > 0.0) atomicMax(&st->amax_bits[parity ^ 1], (unsigned long long)__double_as_longlong(m));
         } else {
             if (m > 0.f) atomicMax(&st->amax_f32[parity ^ 1], __float_as_uint(m));
         }
-        if (s_err) atomicOr(&st->err, s_err);
+        if (e) atomicOr(&st->err, e);
         __threadfence();
         const unsigned done = atomicAdd(&st->blocks_done, 1u);
-        s_last = (done == (unsigned)(ctas - 1));
-    }
-    __syncthreads();
-    if (s_last && threadIdx.x == 0) {
-        __threadfence();
-        finalize_state(st, sizeof(T) == 4, dt, hist, hist_cap, parity, cfl_mode, cfl, dx);
+        if (done == (unsigned)(ctas - 1)) {
+            __threadfence();
+            finalize_state(st, sizeof(T) == 4, dt, hist, hist_cap, parity, cfl_mode, cfl, dx);
+        }
     }
 }
-
 template <class T, int NT = kThreads>
 __device__ __forceinline__ void finish_halfstep(T speed, unsigned err, double dt, const StepArgs& args) {
     reduce_and_finish<T, NT>(speed, err, dt, args.st, (long long)gridDim.x, args.hist, args.hist_cap, args.parity,
