@@ -140,10 +140,10 @@ FP64_FLOPS_PER_CELL_UPDATE = 885.04
 # (201425408 + 149216768 at N = 2^21), scaled by cells to N = 2^22.
 FP64_TRAFFIC_PER_CELL = (201425408 + 149216768) / 2097152.5
 # DRAM bytes (read + write) of one FP32-mixed launch per cell, from an ncu
-# capture of halfstep_mixed2<EULER, 3> at N = 2^21 (125889280 + 74695680; the
-# kernel compiled for 6 CTAs per SM with parked float-float terms), scaled by
-# cells to N = 2^22.
-MIXED_TRAFFIC_PER_CELL = (125889280 + 74695680) / 2097152.5
+# capture of halfstep_mixed2<EULER, 3> at N = 2^21 (125892096 + 73494272; the
+# current kernel: 6 CTAs per SM, parked float-float terms, one-barrier
+# reduction), scaled by cells to N = 2^22.
+MIXED_TRAFFIC_PER_CELL = (125892096 + 73494272) / 2097152.5
 # FP64 pipe peak of the GB300 (dense, nominal): 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 
