@@ -239,16 +239,50 @@ def cpu_oracle_rate(log2n, seconds):
 
 
 def run_reference(args, rank, world):
+    """The reference arm: the CPU oracle as it stands, on the host cores.  A
+    step is HALFSTEPS_PER_STEP half-steps of a bounded sample of the
+    workload (the 2^16-cell window of the N = 2^log2n grid around the jump);
+    W untimed steps, then K timed ones."""
     if rank != 0:
         return
-    rate, cores, sample = cpu_oracle_rate(args.log2n, max(1.0, args.cpu_seconds))
+    import oracle
+    from paper_2104_04347_gb300 import inputs
+
+    cores = os.cpu_count() or 1
+    oracle.set_threads(cores)
+    N = 1 << args.log2n
+    pr = inputs.euler_riemann_seeded(N, P)
+    win = 1 << 16
+    lo = N // 2 - win // 2
+    law = oracle.make_law(oracle.EULER, P, limiter=True, bc=oracle.TRANSMISSIVE)
+    s = oracle.Solver(law, pr.q0[lo:lo + win + 1].copy(), pr.dx)
+
+    def one_step():
+        cells = 0
+        for _ in range(HALFSTEPS_PER_STEP):
+            n = s.q.shape[0]
+            s.step_cfl(1, CFL)
+            cells += oracle.new_count(law, s.parity ^ 1, n)
+        return cells
+
+    for _ in range(args.warmup):
+        one_step()
+    cells = 0
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        cells += one_step()
+    dt = time.perf_counter() - t0
+    rate = cells / dt
+    sample = (f"{args.steps} steps of {HALFSTEPS_PER_STEP} half-steps (after {args.warmup} untimed) of a "
+              f"{win}-cell window of the N=2^{args.log2n} grid around the jump, {dt:.1f} s")
     line = {
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "cell-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.log2n), "N": 1 << args.log2n, "P": P,
-                   "precision": "fp64", "halfsteps_per_step": HALFSTEPS_PER_STEP},
+        "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": workload_name(args.log2n), "N": N, "P": P,
+                   "precision": "fp64", "halfsteps_per_step": HALFSTEPS_PER_STEP,
+                   "sample_cells": win + 1},
         "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
