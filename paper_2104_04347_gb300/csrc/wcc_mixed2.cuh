@@ -47,6 +47,14 @@ constexpr int kTileMixed = 2 * kThreadsMixed - 1;
 // budget 65536 / (kThreadsMixed * CTAs) per thread): the most that still
 // compiles without spills (measured on GB300, Euler): 7 for P <= 2, 6 for
 // P = 3, 5 for P = 4.  WCC_MIXED_MIN_CTAS overrides it for every P.
+// Consecutive tiles per CTA of the single-grid kernel: 2 for P <= 2 (one
+// CTA reduction for two tiles; measured faster), 1 for P >= 3 (measured
+// slower with 2).
+template <int P>
+constexpr int mixed_tiles_per_cta() {
+    return P <= 2 ? 2 : 1;
+}
+
 template <int P>
 constexpr int mixed_min_ctas() {
 #ifdef WCC_MIXED_MIN_CTAS
@@ -528,12 +536,27 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
 template <int SYS, int P, bool COMP = true>
 __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_mixed2(const StepArgs args) {
     __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
+    constexpr int TPC = mixed_tiles_per_cta<P>();
     const StepSize z = step_size(args);
-    const TileIO io{args.in32, args.out32, args.pitch, args.n_old, args.n_new,
-                    (long long)blockIdx.x * kTileMixed, args.parity, args.bc};
     float speed = 0.f;
     unsigned err = 0u;
-    mixed_tile2<SYS, P, COMP>(io, ff_make(z.lam_hi, z.lam_lo), args, rec, speed, err);
+    if constexpr (TPC == 1) {
+        const TileIO io{args.in32, args.out32, args.pitch, args.n_old, args.n_new,
+                        (long long)blockIdx.x * kTileMixed, args.parity, args.bc};
+        mixed_tile2<SYS, P, COMP>(io, ff_make(z.lam_hi, z.lam_lo), args, rec, speed, err);
+    } else {
+        const long long ntiles = (args.n_new + kTileMixed - 1) / kTileMixed;
+        for (int r = 0; r < TPC; ++r) {
+            const long long tile = (long long)blockIdx.x * TPC + r;
+            if (tile >= ntiles) break;
+            if (r) __syncthreads();  // the previous tile's records are read
+            const TileIO io{args.in32, args.out32, args.pitch, args.n_old, args.n_new,
+                            tile * kTileMixed, args.parity, args.bc};
+            float sp = 0.f;
+            mixed_tile2<SYS, P, COMP>(io, ff_make(z.lam_hi, z.lam_lo), args, rec, sp, err);
+            speed = fmaxf(speed, sp);
+        }
+    }
     finish_halfstep<float, kThreadsMixed>(speed, err, z.dt, args);
 }
 
