@@ -222,7 +222,7 @@ def cpu_oracle_rate(log2n, seconds):
     oracle.set_threads(threads)
     N = 1 << log2n
     pr = inputs.euler_riemann_seeded(N, P)
-    win = 1 << 16
+    win = min(1 << 16, N)
     lo = N // 2 - win // 2
     q = pr.q0[lo:lo + win + 1].copy()
     law = oracle.make_law(oracle.EULER, P, limiter=True, bc=oracle.TRANSMISSIVE)
@@ -252,7 +252,7 @@ def run_reference(args, rank, world):
     oracle.set_threads(cores)
     N = 1 << args.log2n
     pr = inputs.euler_riemann_seeded(N, P)
-    win = 1 << 16
+    win = min(1 << 16, N)
     lo = N // 2 - win // 2
     law = oracle.make_law(oracle.EULER, P, limiter=True, bc=oracle.TRANSMISSIVE)
     s = oracle.Solver(law, pr.q0[lo:lo + win + 1].copy(), pr.dx)
