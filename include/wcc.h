@@ -114,6 +114,20 @@ int wcc_step(wcc_handle h, int64_t nsteps, double cfl);
  * nsteps doubles, each > 0).  Asynchronous; dts is read before return. */
 int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts);
 
+/* Advance from the current time to t_end, ending on an integer stage
+ * (the reading of the paper's Table 2 runs, which do not say how t_end is
+ * hit): CFL half-steps (as wcc_step) in pairs while a pair fits, then the
+ * remaining time split into two equal half-steps.  Each half-step's CFL size
+ * is the one the kernels will take (read from the device between steps), so
+ * the decision is exact; near t_end this synchronises after every
+ * half-step.  A rest below 1e-9 of a half-step counts as the rounding of the
+ * summed time and is not stepped.  If the second CFL step of a pair would pass t_end, the rest of
+ * the time is taken in one step.  Must start on an integer stage
+ * (WCC_E_STATE otherwise); t_end before the current time is WCC_E_INVAL.
+ * *nsteps_taken (may be NULL) receives the number of half-steps taken.
+ * Synchronous; reports device-side errors. */
+int wcc_step_until(wcc_handle h, double t_end, double cfl, int64_t* nsteps_taken);
+
 /* Copy the current stage to host FP64 DOFs [cell][var][k] (count =
  * cells*nv*(P+1) of the current stage).  Synchronises the stream and
  * reports any device-side error raised since the last check. */

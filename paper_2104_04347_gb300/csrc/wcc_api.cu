@@ -2,6 +2,8 @@
 // layout conversion, time marching with device-side dt and CUDA graphs.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -552,6 +554,65 @@ int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
                                  h->stream));
     DevState s;
     return read_state(h, &s);
+}
+
+int wcc_step_until(wcc_handle h, double t_end, double cfl, int64_t* nsteps_taken) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    if (nsteps_taken) *nsteps_taken = 0;
+    if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
+    if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
+    if (!(std::fabs(t_end) < 1e300)) return fail(h, WCC_E_INVAL, "t_end must be finite");
+    if (h->parity != 0) return fail(h, WCC_E_STATE, "wcc_step_until starts on an integer stage");
+    DevState s;
+    int rc = read_state(h, &s);
+    if (rc != WCC_OK) return rc;
+    if (t_end < s.t) return fail(h, WCC_E_INVAL, "t_end is before the current time");
+    const unsigned long long cfl_bits = (unsigned long long)__double_as_longlong_host(cfl);
+    // the size the next CFL half-step will take: the kernels' own rule
+    auto next_dt = [&](const DevState& st) {
+        if ((unsigned long long)__double_as_longlong_host(st.next_cfl) == cfl_bits) return st.next_dt;
+        double amax;
+        std::memcpy(&amax, &st.amax_bits[h->parity], sizeof amax);
+        return cfl * h->dx / amax;
+    };
+    int64_t taken = 0;
+    auto finish = [&](int code) {
+        if (nsteps_taken) *nsteps_taken = taken;
+        return code;
+    };
+    const int chunk = h->opt.graph_chunk >= 2 ? h->opt.graph_chunk : 2;
+    for (;;) {
+        const double dt = next_dt(s);
+        if (!(dt > 0.0) || !(dt < 1e300)) return finish(fail(h, WCC_E_NONFINITE, "the CFL half-step size is not positive"));
+        const double left = t_end - s.t;
+        // a rest below 1e-9 of a half-step is the rounding of the summed time
+        const double tiny = std::max(1e-14 * std::max(1.0, std::fabs(t_end)), 1e-9 * dt);
+        if (left >= 4.0 * chunk * dt) {  // far from t_end: a whole graph (dt may grow a little)
+            if ((rc = wcc_step(h, chunk, cfl)) != WCC_OK) return finish(rc);
+            taken += chunk;
+        } else if (left >= 2.0 * dt * (1.0 - 1e-12)) {  // a pair of CFL half-steps fits
+            if ((rc = wcc_step(h, 1, cfl)) != WCC_OK) return finish(rc);
+            ++taken;
+            if ((rc = read_state(h, &s)) != WCC_OK) return finish(rc);
+            const double left2 = t_end - s.t;
+            if (left2 >= next_dt(s) * (1.0 - 1e-12)) {
+                if ((rc = wcc_step(h, 1, cfl)) != WCC_OK) return finish(rc);
+            } else {  // the second CFL step would pass t_end
+                if ((rc = wcc_step_dt(h, 1, &left2)) != WCC_OK) return finish(rc);
+            }
+            ++taken;
+        } else {  // the rest, in two equal half-steps
+            if (left > tiny) {
+                const double dts[2] = {0.5 * left, 0.5 * left};
+                if ((rc = wcc_step_dt(h, 2, dts)) != WCC_OK) return finish(rc);
+                taken += 2;
+            }
+            break;
+        }
+        if ((rc = read_state(h, &s)) != WCC_OK) return finish(rc);
+        if (s.t >= t_end - 1e-14 * std::max(1.0, std::fabs(t_end))) break;
+    }
+    return finish(read_state(h, &s));
 }
 
 int wcc_get_state(wcc_handle h, double* t, int64_t* half_steps, int* parity) {

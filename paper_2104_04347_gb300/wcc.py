@@ -60,6 +60,8 @@ _SIGS = {
     "wcc_set_initial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "wcc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
     "wcc_step_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp]),
+    "wcc_step_until": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
+                                      ctypes.POINTER(ctypes.c_int64)]),
     "wcc_get_dofs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "wcc_get_state": (ctypes.c_int, [ctypes.c_void_p, _dp, _i64p, ctypes.POINTER(ctypes.c_int)]),
     "wcc_get_dt_history": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int64, _i64p]),
@@ -207,6 +209,12 @@ class Solver:
     def step_dt(self, dts) -> None:
         d = np.ascontiguousarray(dts, dtype=np.float64)
         self._check(self.lib.wcc_step_dt(self.h, d.size, d.ctypes.data_as(_dp)))
+
+    def step_until(self, t_end: float, cfl: float) -> int:
+        """Advance to exactly t_end on an integer stage; returns the half-steps taken."""
+        n = ctypes.c_int64(0)
+        self._check(self.lib.wcc_step_until(self.h, float(t_end), float(cfl), ctypes.byref(n)))
+        return int(n.value)
 
     def get_dofs(self) -> np.ndarray:
         n = self.num_cells()

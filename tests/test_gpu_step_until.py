@@ -1,0 +1,83 @@
+"""wcc_step_until: reaching a given time exactly, on an integer stage.
+
+The paper's Table 2 runs end at a fixed time; it does not say how the last
+half-steps are sized.  The reading used here (and by the oracle's
+constant_speed_dts) takes CFL half-steps in pairs while a pair fits, then
+splits the remaining time into two equal half-steps.  For a constant wave
+speed the GPU must therefore take exactly the oracle's list of half-step
+sizes; for varying speeds the run must end at t_end on an integer stage, and
+its state must match the oracle replaying the same sizes.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_04347_gb300 import inputs, wcc
+from tests.gpu_common import TOL64, gpu_solver, oracle_run, scaled_error, trajectory_check
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("t_end", [2.0, 1.0013, 0.0061])
+def test_constant_speed_matches_the_reading(t_end):
+    # advection of sin(pi x) on periodic [0, 2], N = 200, P = 2, nu = 0.25
+    pr = inputs.advection_sine(200, 2, 0.0, 2.0)
+    cfl = 0.25
+    expected = oracle.constant_speed_dts(t_end, cfl * pr.dx / 1.0)
+    with gpu_solver(pr, limiter=False) as s:
+        s.set_initial(pr.q0)
+        taken = s.step_until(t_end, cfl)
+        t, steps, parity = s.state()
+        dts = s.dt_history()
+        q = s.get_dofs()
+    assert taken == steps == len(expected) and taken % 2 == 0 and parity == 0
+    assert abs(t - t_end) <= 1e-12 * max(1.0, t_end)
+    # the CFL steps are identical; the two that split the rest differ by the
+    # rounding of the summed time (the oracle forms the rest as t_end - n dt)
+    assert np.array_equal(dts[:-2], expected[:-2])
+    assert np.allclose(dts[-2:], expected[-2:], rtol=0.0, atol=1e-12)
+    ref, _, _ = oracle_run(pr, dts, limiter=False)
+    assert scaled_error(q, ref) <= TOL64
+
+
+@pytest.mark.parametrize("precision", [wcc.FP64, wcc.FP32_MIXED])
+def test_varying_speed_ends_on_t_end(precision):
+    pr = inputs.euler_riemann_seeded(2048, 3)
+    t_end = 0.031
+    with gpu_solver(pr, precision=precision) as s:
+        s.set_initial(pr.q0)
+        taken = s.step_until(t_end, 0.2)
+        t, steps, parity = s.state()
+        dts = s.dt_history()
+        q = s.get_dofs()
+    assert taken == steps and taken % 2 == 0 and parity == 0 and taken > 64
+    assert abs(t - t_end) <= 1e-12
+    assert np.all(dts > 0.0) and abs(float(np.sum(dts)) - t_end) <= 1e-12
+    # every half-step but the last two is a CFL step of the stage it advanced
+    # (the oracle's CFL rule on the same states reproduces it)
+    if precision == wcc.FP64:
+        law = oracle.make_law(oracle.EULER, 3, limiter=True, bc=oracle.TRANSMISSIVE)
+        sol = oracle.Solver(law, pr.q0, pr.dx)
+        for dt in dts[:-2]:
+            assert abs(dt - 0.2 * pr.dx / oracle.max_speed(law, sol.q)) <= 1e-8 * dt
+            sol.step_dt([dt])
+        viol, _ = trajectory_check(pr, q, dts)
+        assert viol <= 1.0
+
+
+def test_continues_from_a_later_time_and_rejects_bad_calls():
+    pr = inputs.burgers_fourier(512, 2)
+    with gpu_solver(pr) as s:
+        s.set_initial(pr.q0)
+        n1 = s.step_until(0.05, 0.3)
+        n2 = s.step_until(0.1, 0.3)
+        t, steps, parity = s.state()
+        assert n1 + n2 == steps and parity == 0 and abs(t - 0.1) <= 1e-12
+        assert s.step_until(0.1, 0.3) == 0  # already there
+        with pytest.raises(wcc.WCCError) as ei:
+            s.step_until(0.05, 0.3)  # behind the current time
+        assert ei.value.code == -1
+        s.step(1, 0.3)  # now on a half stage
+        with pytest.raises(wcc.WCCError) as ei:
+            s.step_until(0.2, 0.3)
+        assert ei.value.code == -2
