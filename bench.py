@@ -144,6 +144,14 @@ FP64_TRAFFIC_PER_CELL = (201425408 + 149216768) / 2097152.5
 # current kernel: 6 CTAs per SM, parked float-float terms, one-barrier
 # reduction), scaled by cells to N = 2^22.
 MIXED_TRAFFIC_PER_CELL = (125892096 + 73494272) / 2097152.5
+# FP32 flops per cell-update of the same kernel, from the same capture's
+# executed paired instructions (sm__sass_thread_inst_executed_op_f{add2,ffma2,
+# fmul2}): 158.1 FADD2, 144.6 FFMA2 and 81.8 FMUL2 thread instructions per
+# cell-update.  A thread carries two cells and a paired instruction does one
+# operation for each, so per cell-update that is 2 x 158.1 adds, 2 x 144.6
+# FMAs (2 flops each) and 2 x 81.8 multiplies.  Lane-wise min/max and compares
+# are not counted.
+MIXED_FP32_FLOPS_PER_CELL = 316.2 + 2 * 289.2 + 163.6
 # FP64 pipe peak of the GB300 (dense, nominal): 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 
@@ -477,6 +485,12 @@ def run_wcc(args, rank, world):
     roof = dict(head["roofline"])
     roof["fp64_fma_peak_measured_tflops"] = fp64_peak_meas
     roof["fp32_fma_peak_measured_tflops"] = fp32_peak_meas
+    if args.precision == "mixed" and fp32_peak_meas > 0:
+        # the other side of the roofline: FP32 flops over the measured FP32 peak
+        fl = MIXED_FP32_FLOPS_PER_CELL * cells_per_launch / (roof["kernel_ms"] * 1e-3) / 1e12
+        roof["fp32_flops_per_cell_update"] = MIXED_FP32_FLOPS_PER_CELL
+        roof["fp32_tflops"] = fl
+        roof["fp32_frac"] = fl / fp32_peak_meas
     line = {
         "metric": METRIC, "value": head["value"], "unit": "cell-updates/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
