@@ -57,37 +57,10 @@ __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.hi, -a.lo}; }
 
 __device__ __forceinline__ ff ff_sub(ff a, ff b) { return ff_add(a, ff_neg(b)); }
 
-// exact scaling by a power of two
-__device__ __forceinline__ ff ff_scale(ff a, float pow2) { return ff{a.hi * pow2, a.lo * pow2}; }
-
 __device__ __forceinline__ ff ff_mul(ff a, ff b) {
     ff p = two_prod(a.hi, b.hi);
     const float e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo));
     return fast_two_sum(p.hi, e);
-}
-
-__device__ __forceinline__ ff ff_mul(ff a, float b) {
-    ff p = two_prod(a.hi, b);
-    const float e = fmaf(a.lo, b, p.lo);
-    return fast_two_sum(p.hi, e);
-}
-
-// a / b: an approximate float quotient q1, its remainder a - q1 b in
-// float-float, and one correction q2 = remainder / b.hi; the remainder is
-// formed exactly enough that the result keeps ~44 bits even though both
-// quotients use the fast (2 ulp) division.
-__device__ __forceinline__ ff ff_div(ff a, ff b) {
-    const float q1 = __fdividef(a.hi, b.hi);
-    const ff r = ff_sub(a, ff_mul(b, q1));
-    const float q2 = __fdividef(r.hi, b.hi);
-    return fast_two_sum(q1, q2);
-}
-
-// (a - b) rounded to float, for a, b close to each other: the hi parts
-// subtract exactly when they are within a factor of two (Sterbenz), so the
-// difference keeps full FP32 accuracy relative to itself.
-__device__ __forceinline__ float ff_diff(ff a, ff b) {
-    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
 }
 
 // Split a double into a float-float (host or device).
