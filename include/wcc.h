@@ -32,7 +32,10 @@
  *
  * Ownership: the handle owns all device memory it allocates (cudaMalloc in
  * wcc_create); caller buffers are borrowed for the duration of a call only.
- * Calls on one handle are not thread-safe.  wcc_step only enqueues work on
+ * Calls on one handle are not thread-safe, but a handle (single-grid or
+ * batch) may be used from any host thread, one at a time: each call makes
+ * the device the handle was created on current for its duration and then
+ * restores the calling thread's device.  wcc_step only enqueues work on
  * the handle's stream; device-side errors (non-finite values, non-positive
  * density or pressure) are reported by the next call that synchronises
  * (wcc_synchronize, wcc_get_*).

@@ -444,6 +444,7 @@ int wcc_num_cells(wcc_handle h, int64_t* ncells) {
 
 int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
     if (!dofs) return fail(h, WCC_E_INVAL, "dofs is NULL");
     const long long n = stage_cells(h, 0);
     if (count != n * h->nv * h->K) return fail(h, WCC_E_INVAL, "count does not match cells*nv*(P+1) of an integer stage");
@@ -493,6 +494,7 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
 
 int wcc_step(wcc_handle h, int64_t nsteps, double cfl) {
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     if (nsteps < 0) return fail(h, WCC_E_INVAL, "nsteps < 0");
     if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
@@ -522,6 +524,7 @@ int wcc_step(wcc_handle h, int64_t nsteps, double cfl) {
 
 int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts) {
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     if (nsteps < 0 || (nsteps > 0 && !dts)) return fail(h, WCC_E_INVAL, "bad nsteps / dts");
     for (int64_t s = 0; s < nsteps; ++s)
@@ -537,6 +540,7 @@ int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts) {
 
 int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
     if (!dofs) return fail(h, WCC_E_INVAL, "dofs is NULL");
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     const long long n = stage_cells(h, h->parity);
@@ -558,6 +562,7 @@ int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
 
 int wcc_step_until(wcc_handle h, double t_end, double cfl, int64_t* nsteps_taken) {
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
     if (nsteps_taken) *nsteps_taken = 0;
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
@@ -617,6 +622,7 @@ int wcc_step_until(wcc_handle h, double t_end, double cfl, int64_t* nsteps_taken
 
 int wcc_get_state(wcc_handle h, double* t, int64_t* half_steps, int* parity) {
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
     DevState s;
     int rc = read_state(h, &s);
     if (t) *t = s.t;
@@ -627,6 +633,7 @@ int wcc_get_state(wcc_handle h, double* t, int64_t* half_steps, int* parity) {
 
 int wcc_get_dt_history(wcc_handle h, double* dts, int64_t cap, int64_t* n) {
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
     if (cap < 0 || (cap > 0 && !dts)) return fail(h, WCC_E_INVAL, "bad dts / cap");
     DevState s;
     int rc = read_state(h, &s);
@@ -640,6 +647,7 @@ int wcc_get_dt_history(wcc_handle h, double* dts, int64_t cap, int64_t* n) {
 
 int wcc_synchronize(wcc_handle h) {
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
     DevState s;
     return read_state(h, &s);
 }
@@ -660,6 +668,7 @@ const char* wcc_last_error(wcc_handle h) { return h ? h->err.c_str() : g_create_
 
 void wcc_destroy(wcc_handle h) {
     if (!h) return;
+    DeviceScope ds_(h->device);
     cudaStreamSynchronize(h->stream);
     release(h);
     delete h;

@@ -25,6 +25,7 @@ struct wcc_batch_ctx {
     cudaStream_t stream = nullptr;
     bool own_stream = false;
     int PA = 0, PB = 0;  // degrees of group 0 / 1 (equal when the batch has one degree)
+    int device = 0;      // the device the batch lives on
 
     std::vector<long long> N;
     std::vector<int> P, bc;
@@ -360,6 +361,7 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
     }
     int dev = 0;
     cudaGetDevice(&dev);
+    b->device = dev;
     cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
 
     bool ok = true;
@@ -441,6 +443,7 @@ int wcc_batch_dof_count(wcc_batch b, int64_t* count) {
 
 int wcc_batch_set_initial(wcc_batch b, const double* dofs, int64_t count) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
     if (!dofs) return bfail(b, WCC_E_INVAL, "dofs is NULL");
     if (count != b->aos_total[0]) return bfail(b, WCC_E_INVAL, "count does not match the integer stages of the batch");
     WCC_BCHECK(b, cudaMemcpyAsync(b->staging, dofs, (size_t)count * sizeof(double), cudaMemcpyHostToDevice, b->stream));
@@ -464,6 +467,7 @@ int wcc_batch_set_initial(wcc_batch b, const double* dofs, int64_t count) {
 
 int wcc_batch_step(wcc_batch b, int64_t nsteps, double cfl) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
     if (!b->initialised) return bfail(b, WCC_E_STATE, "wcc_batch_set_initial has not been called");
     if (nsteps < 0 || !(cfl > 0.0) || !(cfl < 1e6)) return bfail(b, WCC_E_INVAL, "need nsteps >= 0 and cfl > 0");
     return do_step(b, nsteps, cfl);
@@ -471,6 +475,7 @@ int wcc_batch_step(wcc_batch b, int64_t nsteps, double cfl) {
 
 int wcc_batch_get_dofs(wcc_batch b, double* dofs, int64_t count) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
     if (!dofs) return bfail(b, WCC_E_INVAL, "dofs is NULL");
     if (!b->initialised) return bfail(b, WCC_E_STATE, "wcc_batch_set_initial has not been called");
     if (count != b->aos_total[b->parity]) return bfail(b, WCC_E_INVAL, "count does not match the current stages");
@@ -485,6 +490,7 @@ int wcc_batch_get_dofs(wcc_batch b, double* dofs, int64_t count) {
 
 int wcc_batch_get_times(wcc_batch b, double* t, int64_t count) {
     if (!b || !t || count != b->count) return bfail(b, WCC_E_INVAL, "need t[count] with count = instances");
+    DeviceScope ds_(b->device);
     std::vector<DevState> st;
     int rc = read_states(b, st);
     for (size_t k = 0; k < b->order.size(); ++k) t[b->order[k]] = st[k].t;
@@ -493,6 +499,7 @@ int wcc_batch_get_times(wcc_batch b, double* t, int64_t count) {
 
 int wcc_batch_get_state(wcc_batch b, int64_t* half_steps, int* parity) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
     std::vector<DevState> st;
     int rc = read_states(b, st);
     if (half_steps) *half_steps = b->steps;
@@ -502,6 +509,7 @@ int wcc_batch_get_state(wcc_batch b, int64_t* half_steps, int* parity) {
 
 int wcc_batch_get_dt_history(wcc_batch b, int64_t instance, double* dts, int64_t cap, int64_t* n) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
     if (instance < 0 || instance >= b->count || cap < 0 || (cap > 0 && !dts))
         return bfail(b, WCC_E_INVAL, "bad instance / dts / cap");
     std::vector<DevState> st;
@@ -517,6 +525,7 @@ int wcc_batch_get_dt_history(wcc_batch b, int64_t instance, double* dts, int64_t
 
 int wcc_batch_set_grid(wcc_batch b, int ctas) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
     if (ctas < 0) return bfail(b, WCC_E_INVAL, "ctas must be >= 0");
     b->grid = ctas == 0 ? (unsigned)(b->max_ctas_per_sm * b->sms) : (unsigned)ctas;
     return WCC_OK;
@@ -524,6 +533,7 @@ int wcc_batch_set_grid(wcc_batch b, int ctas) {
 
 int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
     if (!b->initialised) return bfail(b, WCC_E_STATE, "wcc_batch_set_initial has not been called");
     if (!(cfl > 0.0)) return bfail(b, WCC_E_INVAL, "cfl must be positive");
     // Candidates: persistent grids of 1..max resident CTAs per SM, and one
@@ -602,6 +612,7 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
 
 int wcc_batch_synchronize(wcc_batch b) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
     std::vector<DevState> st;
     return read_states(b, st);
 }
@@ -622,6 +633,7 @@ const char* wcc_batch_last_error(wcc_batch b) { return b ? b->err.c_str() : g_ba
 
 void wcc_batch_destroy(wcc_batch b) {
     if (!b) return;
+    DeviceScope ds_(b->device);
     cudaStreamSynchronize(b->stream);
     release(b);
     delete b;

@@ -41,6 +41,23 @@ cudaError_t launch_batch(int PA, int PB, int kind, const BatchArgs& b, double* a
 template <int SYS>
 int batch_blocks_per_sm(int PA, int PB);
 
+// Makes `device` current for the calling host thread for the scope of one
+// library call and restores the thread's previous device afterwards: a
+// handle may be used from any host thread, and the CUDA runtime's current
+// device is per thread.
+struct DeviceScope {
+    int prev = -1;
+    explicit DeviceScope(int device) {
+        int cur = -1;
+        if (cudaGetDevice(&cur) == cudaSuccess && cur != device && cudaSetDevice(device) == cudaSuccess) prev = cur;
+    }
+    ~DeviceScope() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+    DeviceScope(const DeviceScope&) = delete;
+    DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
 inline unsigned halfstep_grid(long long n_new) { return (unsigned)((n_new + kTile - 1) / kTile); }
 
 }  // namespace wcc
