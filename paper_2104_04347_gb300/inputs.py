@@ -208,6 +208,113 @@ def euler_density_wave(N: int, P: int, amp: float = 0.2, gamma: float = GAMMA) -
     return Problem(EULER, N, P, x_l, x_r, PERIODIC, q, "euler-density-wave")
 
 
+# ------------------------------------------------ piecewise-smooth initial data
+
+
+def projected_dofs(func, N: int, P: int, x_l: float, x_r: float, bc: int, breaks=(), nodes: int = 24) -> np.ndarray:
+    """DOFs of piecewise-smooth data: in every cell of the integer stage the
+    L2 projection of func (x -> [points, nv] values) onto polynomials of
+    degree P, written as the paper's scaled derivatives at the centre.  With
+    xi = (x - x_i) / dx on [-1/2, 1/2] the projection is sum_n c_n L_n(2 xi),
+    L_n the Legendre polynomials (orthogonal there, int L_n(2 xi)^2 dxi =
+    1 / (2n + 1)), so c_n = (2n + 1) int u L_n(2 xi) dxi; expanding L_n(2 xi)
+    in powers of xi gives the Taylor coefficients e_k and u_kx = k! e_k.
+    Each cell is integrated piece by piece between the break points (jumps
+    and kinks of the data) with Gauss-Legendre nodes mapped by
+    x = a0 + (a1 - a0)(1 - cos t)/2, t in [0, pi]: the nodes cluster at both
+    ends, which keeps square-root endpoints (the half ellipses) accurate.
+    Result [cells, nv, P+1]."""
+    x = centres(N, x_l, x_r, bc)
+    dx = (x_r - x_l) / N
+    g, gw = np.polynomial.legendre.leggauss(nodes)
+    brk = np.sort(np.asarray(breaks, dtype=np.float64))
+    # A[n, k]: coefficient of xi^k in L_n(2 xi)
+    A = np.zeros((P + 1, P + 1))
+    for n in range(P + 1):
+        c = np.polynomial.legendre.leg2poly(np.eye(P + 1)[n])
+        A[n, :c.size] = c * 2.0 ** np.arange(c.size)
+    fact = np.array([math.factorial(k) for k in range(P + 1)], dtype=np.float64)
+    out = None
+    th = 0.5 * math.pi * (g + 1.0)
+    for i, xc in enumerate(x):
+        # pieces in the cell's own coordinate xi, so that their lengths sum to
+        # exactly 1 whatever the rounding of the cell's position
+        lo, hi = xc - 0.5 * dx, xc + 0.5 * dx
+        inner = brk[(brk > lo) & (brk < hi)]
+        cuts = np.concatenate(([-0.5], np.clip((inner - xc) / dx, -0.5, 0.5), [0.5]))
+        mom = None
+        for a0, a1 in zip(cuts[:-1], cuts[1:]):
+            xi = a0 + (a1 - a0) * 0.5 * (1.0 - np.cos(th))
+            ws = gw * (a1 - a0) * 0.25 * math.pi * np.sin(th)
+            xs = xc + dx * xi
+            vals = np.atleast_2d(func(xs))  # [points, nv]
+            if vals.shape[0] != xs.size:
+                vals = vals.T
+            leg = np.polynomial.legendre.legvander(2.0 * xi, P)  # [points, P+1]
+            part = np.einsum("p,pv,pn->vn", ws, vals, leg)
+            mom = part if mom is None else mom + part
+        cn = mom * (2.0 * np.arange(P + 1) + 1.0)  # [nv, P+1]
+        e = cn @ A  # Taylor coefficients
+        if out is None:
+            out = np.zeros((x.size, e.shape[0], P + 1))
+        out[i] = e * fact
+    return out
+
+
+def composite_wave_data(x):
+    """Jiang-Shu composite profile on [-1, 1] (Sec. 5.1, second case): three
+    Gaussians, a square wave, a triangle and three half ellipses, with a =
+    0.5, z = -0.7, delta = 0.005, alpha = 10, beta = log 2 / (36 delta^2)."""
+    a, z, d, al = 0.5, -0.7, 0.005, 10.0
+    be = math.log(2.0) / (36.0 * d * d)
+    x = np.asarray(x, dtype=np.float64)
+
+    def G(zz):
+        return np.exp(-be * (x - zz) ** 2)
+
+    def F(aa):
+        return np.sqrt(np.maximum(1.0 - al * al * (x - aa) ** 2, 0.0))
+
+    u = np.zeros_like(x)
+    m = (x >= -0.8) & (x <= -0.6)
+    u[m] = ((G(z - d) + 4.0 * G(z) + G(z + d)) / 6.0)[m]
+    u[(x >= -0.4) & (x <= -0.2)] = 1.0
+    m = (x >= 0.0) & (x <= 0.2)
+    u[m] = (1.0 - 10.0 * np.abs(x - 0.1))[m]
+    m = (x >= 0.4) & (x <= 0.6)
+    u[m] = ((F(a - d) + 4.0 * F(a) + F(a + d)) / 6.0)[m]
+    return u[:, None]
+
+
+# jumps and kinks of the composite profile (piece ends, the triangle's apex,
+# the ellipses' edges a +- delta +- 1/alpha inside [0.4, 0.6])
+COMPOSITE_BREAKS = (-0.8, -0.6, -0.4, -0.2, 0.0, 0.1, 0.2, 0.4, 0.405, 0.5, 0.595, 0.6)
+
+
+def advection_composite(N: int, P: int) -> Problem:
+    """The composite wave advected on periodic [-1, 1] (a = 1)."""
+    q = projected_dofs(composite_wave_data, N, P, -1.0, 1.0, PERIODIC, COMPOSITE_BREAKS)
+    return Problem(ADVECTION, N, P, -1.0, 1.0, PERIODIC, q, "advection-composite")
+
+
+def shu_osher_data(x, gamma: float = GAMMA):
+    """Modified Shu-Osher problem (Sec. 5.2, second case): a Mach 1.1 shock at
+    x = -4.5, (rho, u, p) = (1.515695, 0.523346, 1.805) behind it, and
+    (1 + 0.1 sin(20 pi x), 0, 1) ahead.  Conserved variables [points, 3]."""
+    x = np.asarray(x, dtype=np.float64)
+    left = x < -4.5
+    rho = np.where(left, 1.515695, 1.0 + 0.1 * np.sin(20.0 * math.pi * x))
+    u = np.where(left, 0.523346, 0.0)
+    p = np.where(left, 1.805, 1.0)
+    return primitive_to_conserved(rho, u, p, gamma)
+
+
+def shu_osher(N: int, P: int) -> Problem:
+    """The modified Shu-Osher problem on [-5, 5], transmissive boundaries."""
+    q = projected_dofs(shu_osher_data, N, P, -5.0, 5.0, TRANSMISSIVE, (-4.5,))
+    return Problem(EULER, N, P, -5.0, 5.0, TRANSMISSIVE, q, "shu-osher")
+
+
 def random_smooth_dofs(ncells: int, nv: int, P: int, seed: int, scale: float = 1.0) -> np.ndarray:
     """Uniform random DOFs in [-scale, scale] (for unit-level checks)."""
     rng = np.random.default_rng(seed)

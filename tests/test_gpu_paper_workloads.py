@@ -1,0 +1,180 @@
+"""The paper's piecewise-smooth 1D workloads (Sec. 5) as GPU regression runs.
+
+* Jiang-Shu composite wave (Gaussians, square, triangle, half ellipse) under
+  linear advection, periodic [-1, 1], 400 cells, t = 12 (six periods).
+* Sod shock tube, [0, 2], dx = 1/100, t = 0.4, transmissive boundaries.
+* Modified Shu-Osher problem, [-5, 5], dx = 1/200, t = 5, transmissive.
+
+Each runs at P = 1, 2, 3 with the CFL numbers of Sec. 5 and reaches t_end
+through wcc_step_until.  Checks:
+  * FP64: at every half-step (every 16th on the 7000-step Shu-Osher run) the
+    GPU's half-step from its own previous state matches the oracle's half-step
+    from the same state within the conditioning-aware bound of
+    tests/gpu_common.py, and the whole trajectory stays within 50 x the
+    oracle's own L1 spread (at least 1e-6);
+  * FP32-mixed: the trajectory's L1 distance from the oracle replaying the
+    same half-step sizes is within max(1e-6, 50 x the oracle's L1 spread under
+    1e-7 input noise);
+  * accuracy by degree, as Sec. 5 observes it: P = 2, 3 beat P = 1 against
+    the exact solution (composite wave, Sod), and P = 1 damps the entropy
+    wave behind the Shu-Osher shock while P = 3 keeps most of it.
+The paper's own results here are figures, so these are behaviour checks,
+not printed numbers."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import exact
+from paper_2104_04347_gb300 import inputs, wcc
+from tests.gpu_common import PERTURB, SCATTER_FACTOR, gpu_solver, law_of, oracle_l1_spread, oracle_spread, \
+    parity_violation, scales
+
+pytestmark = pytest.mark.gpu
+
+CFL = {1: 0.4, 2: 0.3, 3: 0.25}
+SOD_LEFT, SOD_RIGHT = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+
+
+def _avg(q):
+    """Cell averages (Eq. SubEq:1DCellAVG) of DOFs [cells, nv, P+1]."""
+    P = q.shape[-1] - 1
+    w = np.array([1.0 / (math.factorial(k + 1) * 2.0 ** k) if k % 2 == 0 else 0.0 for k in range(P + 1)])
+    return q @ w
+
+
+def _l1(q, ref):
+    sc = scales(ref)
+    return float(np.max(np.mean(np.abs(q[:, :, 0] - ref[:, :, 0]), axis=0) / sc))
+
+
+def _until(pr, t_end, precision):
+    with gpu_solver(pr, precision=precision) as s:
+        s.set_initial(pr.q0)
+        taken = s.step_until(t_end, CFL[pr.P])
+        t, steps, parity = s.state()
+        q = s.get_dofs()
+        dts = s.dt_history()
+    assert taken == steps and parity == 0 and abs(t - t_end) <= 1e-12 * max(1.0, t_end)
+    return q, dts
+
+
+def _teacher_forced(pr, dts, every):
+    """Replay dts on the GPU; on every `every`-th half-step compare the GPU's
+    half-step with the oracle's from the same state."""
+    law = law_of(pr)
+    worst = 0.0
+    with gpu_solver(pr) as s:
+        s.set_initial(pr.q0)
+        for n in range(0, len(dts), every):
+            if n and every > 1:
+                s.step_dt(dts[n - every + 1:n])
+            dt = float(dts[n])
+            prev = s.get_dofs()
+            parity = s.state()[2]
+            s.step_dt([dt])
+            cur = s.get_dofs()
+            lam = dt / pr.dx
+
+            def run(qq):
+                return oracle.halfstep(law, parity, qq, lam)
+
+            ref = run(prev)
+            worst = max(worst, parity_violation(cur, ref, oracle_spread(run, prev, ref, seed=n)))
+    return worst
+
+
+def _parity(pr, t_end, every=1):
+    q64, dts = _until(pr, t_end, wcc.FP64)
+    worst = _teacher_forced(pr, dts, every)
+    assert worst <= 1.0, worst
+    ref, spread64 = oracle_l1_spread(pr, dts, PERTURB)
+    assert _l1(q64, ref) <= max(1e-6, SCATTER_FACTOR * spread64)
+    qm, dtm = _until(pr, t_end, wcc.FP32_MIXED)
+    ref, spread32 = oracle_l1_spread(pr, dtm, 1e-7)
+    assert _l1(qm, ref) <= max(1e-6, SCATTER_FACTOR * spread32)
+    return q64, qm
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_composite_wave_t12(P):
+    pr = inputs.advection_composite(400, P)
+    q64, qm = _parity(pr, 12.0)
+    # six periods: the exact solution is the initial data again
+    exact_avg = _avg(pr.q0)[:, 0]
+    for q in (q64, qm):
+        err = np.mean(np.abs(_avg(q)[:, 0] - exact_avg))
+        assert err < {1: 0.04, 2: 0.015, 3: 0.012}[P], err
+
+
+def test_composite_wave_accuracy_by_degree():
+    # Sec. 5.1: the third- and fourth-order schemes do much better than the
+    # second-order one on every part of the wave
+    errs = {}
+    for P in (1, 2, 3):
+        pr = inputs.advection_composite(400, P)
+        for prec in (wcc.FP64, wcc.FP32_MIXED):
+            q, _ = _until(pr, 12.0, prec)
+            errs[P, prec] = np.mean(np.abs(_avg(q)[:, 0] - _avg(pr.q0)[:, 0]))
+    for prec in (wcc.FP64, wcc.FP32_MIXED):
+        assert errs[2, prec] < 0.6 * errs[1, prec] and errs[3, prec] < 0.6 * errs[1, prec], errs
+
+
+def _sod_exact_avg(pr, t):
+    x = inputs.centres(pr.N, pr.x_l, pr.x_r, pr.bc)
+    m = 64
+    pts = x[:, None] + pr.dx * ((np.arange(m) + 0.5) / m - 0.5)[None, :]
+    rho, _, _ = exact.riemann_sample(SOD_LEFT, SOD_RIGHT, (pts - 1.0) / t)
+    return rho.mean(axis=1)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_sod_t04(P):
+    pr = inputs.sod(200, P)
+    q64, qm = _parity(pr, 0.4)
+    ex = _sod_exact_avg(pr, 0.4)
+    for q in (q64, qm):
+        # L1 over [0, 2] of the density averages against the exact solution
+        err = 2.0 * np.mean(np.abs(_avg(q)[:, 0] - ex))
+        assert err < 0.006, err
+
+
+def test_sod_accuracy_by_degree():
+    # Sec. 5.2: WCCS-3 and WCCS-4 resolve the tube better than WCCS-2,
+    # most visibly at the contact
+    errs = {}
+    for P in (1, 2, 3):
+        pr = inputs.sod(200, P)
+        ex = _sod_exact_avg(pr, 0.4)
+        for prec in (wcc.FP64, wcc.FP32_MIXED):
+            q, _ = _until(pr, 0.4, prec)
+            errs[P, prec] = np.mean(np.abs(_avg(q)[:, 0] - ex))
+    for prec in (wcc.FP64, wcc.FP32_MIXED):
+        assert errs[2, prec] < 0.85 * errs[1, prec] and errs[3, prec] < 0.85 * errs[1, prec], errs
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_shu_osher_t5(P):
+    pr = inputs.shu_osher(2000, P)
+    q64, _ = _parity(pr, 5.0, every=16)
+    # the shock (speed 1.538 from x = -4.5 for the paper's left state) is
+    # near x = 3.19 at t = 5
+    x = inputs.centres(pr.N, pr.x_l, pr.x_r, pr.bc)
+    rho = q64[:, 0, 0]
+    assert abs(x[int(np.argmax(np.abs(np.diff(rho))))] - 3.19) < 0.05
+
+
+def test_shu_osher_entropy_wave_by_degree():
+    # Sec. 5.2: the second-order scheme damps the high-frequency entropy wave
+    # behind the shock (it is first order at extrema); WCCS-4 keeps most of it
+    amp = {}
+    for P in (1, 2, 3):
+        pr = inputs.shu_osher(2000, P)
+        x = inputs.centres(pr.N, pr.x_l, pr.x_r, pr.bc)
+        band = (x > 0.5) & (x < 2.3)
+        for prec in (wcc.FP64, wcc.FP32_MIXED):
+            q, _ = _until(pr, 5.0, prec)
+            amp[P, prec] = float(np.std(_avg(q)[band, 0]))
+    for prec in (wcc.FP64, wcc.FP32_MIXED):
+        assert amp[1, prec] < 0.1 * amp[3, prec] and amp[2, prec] < amp[3, prec], amp
