@@ -16,6 +16,8 @@ Metric: cell-updates/s = cells of the stage x half-steps / time.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl wcc|reference]
                     [--precision fp64|mixed] [--log2n 22]
+    python bench.py --sweep        # precision / convergence sweep (density wave)
+    python bench.py --workloads    # the paper's 1D workloads of Sec. 5
 
 Under torchrun each rank runs an independent replica (the path has no
 exchange step here); value = cell-updates of all ranks / max time.
@@ -56,6 +58,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=1, help="also time the 4096-instance batch (1/0)")
     ap.add_argument("--sweep", action="store_true", help="precision / convergence sweep (density wave) instead")
     ap.add_argument("--sweep-max-log2n", type=int, default=16)
+    ap.add_argument("--workloads", action="store_true",
+                    help="the paper's 1D workloads (composite wave, Sod, Shu-Osher) instead")
     return ap.parse_args()
 
 
@@ -574,10 +578,94 @@ def precision_sweep(max_log2n=16):
         print(f"| {r['P']} | {r['N']} | {r['precision']} | {r['l1_exact']:.3e} | {o} | {r['l1_vs_fp64']:.2e} | {lo} |")
 
 
+def paper_workloads():
+    """The 1D workloads of Sec. 5 at the paper's sizes, P = 1..3 with the
+    Sec. 5 CFL numbers, run to t_end through wcc_step_until in every
+    precision:
+      * composite wave, periodic [-1, 1], 400 cells, t = 12 (six periods; the
+        exact solution is the initial data);
+      * Sod, [0, 2], 200 cells, t = 0.4 (exact Riemann solution);
+      * modified Shu-Osher, [-5, 5], 2000 cells, t = 5 (no exact solution:
+        the standard deviation of the density behind the shock, x in
+        [0.5, 2.3], shows how much of the entropy wave survives).
+    Per case: half-steps, time to solution (second pass on the same handle,
+    host wall clock around the call, which returns synchronised), L1 of the
+    density cell averages against the exact solution, and L1 against the
+    oracle replaying the same half-step sizes (FP64 and FP32-mixed).  One JSON
+    line per case and a markdown table."""
+    import math
+
+    import oracle
+    from oracle import exact
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    oracle.set_threads(os.cpu_count() or 1)
+    nu = {1: 0.4, 2: 0.3, 3: 0.25}
+    names = {wcc.FP64: "fp64", wcc.FP32_MIXED: "fp32-mixed", wcc.FP32: "fp32"}
+
+    def avg(q):
+        k = np.arange(q.shape[-1])
+        w = np.where(k % 2 == 0, 1.0 / (np.array([math.factorial(i + 1) for i in k]) * 2.0 ** k), 0.0)
+        return q @ w
+
+    def sod_exact(pr, t):
+        x = inputs.centres(pr.N, pr.x_l, pr.x_r, pr.bc)
+        pts = x[:, None] + pr.dx * ((np.arange(64) + 0.5) / 64 - 0.5)[None, :]
+        rho, _, _ = exact.riemann_sample((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), (pts - 1.0) / t)
+        return rho.mean(axis=1)
+
+    cases = (("composite-wave", lambda P: inputs.advection_composite(400, P), 12.0),
+             ("sod", lambda P: inputs.sod(200, P), 0.4),
+             ("shu-osher", lambda P: inputs.shu_osher(2000, P), 5.0))
+    rows = []
+    for name, make, t_end in cases:
+        for P in (1, 2, 3):
+            pr = make(P)
+            length = pr.x_r - pr.x_l
+            ref_exact = avg(pr.q0)[:, 0] if name == "composite-wave" else (
+                sod_exact(pr, t_end) if name == "sod" else None)
+            x = inputs.centres(pr.N, pr.x_l, pr.x_r, pr.bc)
+            band = (x > 0.5) & (x < 2.3)
+            for prec in (wcc.FP64, wcc.FP32_MIXED, wcc.FP32):
+                with wcc.Solver(pr.system, pr.N, P, (pr.x_l, pr.x_r), pr.bc, precision=prec) as s:
+                    s.set_initial(pr.q0)
+                    s.step_until(t_end, nu[P])  # first pass: graph capture, history growth
+                    s.set_initial(pr.q0)
+                    t0 = time.perf_counter()
+                    n = s.step_until(t_end, nu[P])
+                    secs = time.perf_counter() - t0
+                    q = s.get_dofs()
+                    dts = s.dt_history()
+                rho = avg(q)[:, 0]
+                row = {"workload": name, "P": P, "N": pr.N, "precision": names[prec], "t_end": t_end,
+                       "halfsteps": n, "seconds": secs, "us_per_halfstep": 1e6 * secs / n,
+                       "l1_exact": None if ref_exact is None else float(length * np.mean(np.abs(rho - ref_exact))),
+                       "wave_std": float(np.std(rho[band])) if name == "shu-osher" else None,
+                       "l1_vs_oracle": None}
+                if prec != wcc.FP32:
+                    sol = oracle.Solver(oracle.make_law(pr.system, P, limiter=True, bc=pr.bc), pr.q0, pr.dx)
+                    sol.step_dt(dts)
+                    row["l1_vs_oracle"] = float(length * np.mean(np.abs(rho - avg(sol.q)[:, 0])))
+                rows.append(row)
+                print(json.dumps(row), flush=True)
+    print("| workload | P | precision | half-steps | time to t_end | µs / half-step | L1 vs exact | "
+          "entropy-wave std | L1 vs oracle |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    for r in rows:
+        le = "" if r["l1_exact"] is None else f"{r['l1_exact']:.3e}"
+        ws = "" if r["wave_std"] is None else f"{r['wave_std']:.4f}"
+        lo = "" if r["l1_vs_oracle"] is None else f"{r['l1_vs_oracle']:.1e}"
+        print(f"| {r['workload']} | {r['P']} | {r['precision']} | {r['halfsteps']} | {1e3 * r['seconds']:.1f} ms | "
+              f"{r['us_per_halfstep']:.2f} | {le} | {ws} | {lo} |")
+
+
 def main():
     args = parse()
     if args.sweep:
         precision_sweep(args.sweep_max_log2n)
+        return
+    if args.workloads:
+        paper_workloads()
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
