@@ -342,3 +342,204 @@ def batch_workload(count: int = 4096, n_min: int = 256, n_max: int = 65536, degr
             pr.name = f"density-wave-{i}"
         out.append(pr)
     return out
+
+
+# ------------------------------------------------------------------- 2D data
+#
+# 2D DOFs are the scaled derivatives u_{kx,ly} = dx^k dy^l d^k_x d^l_y u0 at
+# every cell centre of the integer stage (Eq. 2DPolynomial_Space), k + l <= P,
+# stored float64 [ny, nx, nv, nq] with nq = (P+1)(P+2)/2 and u_{kx,ly} at
+# position (k+l)(k+l+1)/2 + l (by total degree, then by l).
+
+
+def nq2d(P: int) -> int:
+    return (P + 1) * (P + 2) // 2
+
+
+def idx2d(k: int, l: int) -> int:
+    d = k + l
+    return d * (d + 1) // 2 + l
+
+
+class Taylor2:
+    """Truncated Taylor series in two variables (X, Y), one per point:
+    ``c[..., k, l]`` is the coefficient of X^k Y^l, kept for k + l <= P.
+    Enough arithmetic (+, -, *, exp, real powers) to evaluate initial data
+    and read off every mixed derivative at once: d^k_x d^l_y u = k! l! c_kl."""
+
+    def __init__(self, c: np.ndarray, P: int):
+        self.c = c
+        self.P = P
+
+    @staticmethod
+    def variable(x0, which: int, P: int) -> "Taylor2":
+        x0 = np.asarray(x0, dtype=np.float64)
+        c = np.zeros(x0.shape + (P + 1, P + 1))
+        c[..., 0, 0] = x0
+        if P >= 1:
+            c[..., (1, 0)[which], (0, 1)[which]] = 1.0
+        return Taylor2(c, P)
+
+    def _lift(self, o) -> "Taylor2":
+        if isinstance(o, Taylor2):
+            return o
+        c = np.zeros_like(self.c)
+        c[..., 0, 0] = o
+        return Taylor2(c, self.P)
+
+    def __add__(self, o):
+        return Taylor2(self.c + self._lift(o).c, self.P)
+
+    __radd__ = __add__
+
+    def __neg__(self):
+        return Taylor2(-self.c, self.P)
+
+    def __sub__(self, o):
+        return self + (-self._lift(o))
+
+    def __rsub__(self, o):
+        return self._lift(o) - self
+
+    def __mul__(self, o):
+        if not isinstance(o, Taylor2):
+            return Taylor2(self.c * np.asarray(o)[..., None, None], self.P)
+        P = self.P
+        out = np.zeros(np.broadcast_shapes(self.c.shape, o.c.shape))
+        for k in range(P + 1):
+            for l in range(P + 1 - k):
+                for i in range(k + 1):
+                    for j in range(l + 1):
+                        out[..., k, l] += self.c[..., i, j] * o.c[..., k - i, l - j]
+        return Taylor2(out, P)
+
+    __rmul__ = __mul__
+
+    def _series(self, coef) -> "Taylor2":
+        """sum_n coef[n] h^n with h = self - self(0), which vanishes to order
+        P + 1 after P factors."""
+        h = self - self.c[..., 0, 0]
+        term = self._lift(1.0)
+        acc = term * coef[0]
+        for n in range(1, self.P + 1):
+            term = term * h
+            acc = acc + term * coef[n]
+        return acc
+
+    def exp(self) -> "Taylor2":
+        a0 = self.c[..., 0, 0]
+        return self._series([1.0 / math.factorial(n) for n in range(self.P + 1)]) * np.exp(a0)
+
+    def pow(self, s: float) -> "Taylor2":
+        a0 = self.c[..., 0, 0]
+        coef = []
+        b = 1.0
+        for n in range(self.P + 1):
+            coef.append(b)
+            b *= (s - n) / (n + 1)
+        h = self * (1.0 / a0)  # (a0 + h)^s = a0^s (1 + h/a0)^s
+        return h._series(coef) * a0 ** s
+
+    def scaled_dofs(self, dx: float, dy: float) -> np.ndarray:
+        """[..., nq] scaled derivatives dx^k dy^l d^k_x d^l_y."""
+        P = self.P
+        out = np.zeros(self.c.shape[:-2] + (nq2d(P),))
+        for k in range(P + 1):
+            for l in range(P + 1 - k):
+                out[..., idx2d(k, l)] = (self.c[..., k, l] * math.factorial(k) * math.factorial(l)
+                                         * dx ** k * dy ** l)
+        return out
+
+
+@dataclass
+class Problem2D:
+    """A 2D workload: the law, mesh, boundary and integer-stage DOFs."""
+
+    system: int
+    nx: int
+    ny: int
+    P: int
+    x_l: float
+    x_r: float
+    y_l: float
+    y_r: float
+    bc: int
+    q0: np.ndarray  # [ny', nx', nv, nq]
+    name: str = ""
+    ax: float = 1.0
+    ay: float = 1.0
+
+    @property
+    def dx(self) -> float:
+        return (self.x_r - self.x_l) / self.nx
+
+    @property
+    def dy(self) -> float:
+        return (self.y_r - self.y_l) / self.ny
+
+    @property
+    def nv(self) -> int:
+        return 4 if self.system == EULER else 1
+
+
+def _grid2d(nx, ny, x_l, x_r, y_l, y_r, bc, parity=0):
+    x = centres(nx, x_l, x_r, bc, parity)
+    y = centres(ny, y_l, y_r, bc, parity)
+    return np.meshgrid(x, y)  # [ny, nx] each
+
+
+VORTEX_STRENGTH = 5.0
+
+
+def vortex_conserved(X, Y, gamma: float = GAMMA, psi: float = VORTEX_STRENGTH):
+    """Isentropic vortex of Sec. 5.3 centred at the origin: rho = 1, p = 1,
+    (u, v) = (1, 1) plus (du, dv) = psi/(2 pi) e^{(1 - r^2)/2} (-y, x),
+    dT = -(gamma - 1) psi^2 / (8 gamma pi^2) e^{1 - r^2}, dS = 0 with
+    T = p/rho, S = p/rho^gamma; so rho = T^{1/(gamma-1)}, p = rho T.
+    X, Y may be arrays or Taylor2 series; returns (rho, rho u, rho v, E)."""
+    r2 = X * X + Y * Y
+    f = (0.5 - 0.5 * r2).exp() if isinstance(r2, Taylor2) else np.exp(0.5 * (1.0 - r2))
+    k = psi / (2.0 * math.pi)
+    u = 1.0 - k * (Y * f)
+    v = 1.0 + k * (X * f)
+    T = 1.0 - ((gamma - 1.0) * psi ** 2 / (8.0 * gamma * math.pi ** 2)) * (f * f)
+    if isinstance(T, Taylor2):
+        rho = T.pow(1.0 / (gamma - 1.0))
+    else:
+        rho = T ** (1.0 / (gamma - 1.0))
+    p = rho * T
+    m, n = rho * u, rho * v
+    E = p * (1.0 / (gamma - 1.0)) + 0.5 * (m * u + n * v)
+    return rho, m, n, E
+
+
+def _wrap(z, lo, hi):
+    return np.mod(z - lo, hi - lo) + lo
+
+
+def vortex_exact(x, y, t, gamma: float = GAMMA):
+    """Conserved variables of the exact solution at time t on periodic
+    [-5, 5]^2: the vortex carried by the mean flow (1, 1)."""
+    return vortex_conserved(_wrap(x - t, -5.0, 5.0), _wrap(y - t, -5.0, 5.0), gamma)
+
+
+def isentropic_vortex(n: int, P: int, gamma: float = GAMMA) -> Problem2D:
+    """Sec. 5.3: periodic [-5, 5]^2, n x n cells (mesh size 10/n)."""
+    X, Y = _grid2d(n, n, -5.0, 5.0, -5.0, 5.0, PERIODIC)
+    dx = 10.0 / n
+    U = vortex_conserved(Taylor2.variable(X, 0, P), Taylor2.variable(Y, 1, P), gamma)
+    q = np.stack([u.scaled_dofs(dx, dx) for u in U], axis=2)  # [ny, nx, 4, nq]
+    return Problem2D(EULER, n, n, P, -5.0, 5.0, -5.0, 5.0, PERIODIC, q, "isentropic-vortex")
+
+
+def advection2d_sine(nx: int, ny: int, P: int, ax: float = 1.0, ay: float = 1.0,
+                     kx: float = math.pi, ky: float = math.pi, phase: float = 0.0) -> Problem2D:
+    """u0 = sin(kx x + ky y + phase) on periodic [-1, 1]^2; f = ax u, g = ay u."""
+    X, Y = _grid2d(nx, ny, -1.0, 1.0, -1.0, 1.0, PERIODIC)
+    dx, dy = 2.0 / nx, 2.0 / ny
+    q = np.zeros((ny, nx, 1, nq2d(P)))
+    for k in range(P + 1):
+        for l in range(P + 1 - k):
+            q[:, :, 0, idx2d(k, l)] = (kx ** k * ky ** l * np.sin(kx * X + ky * Y + phase + (k + l) * math.pi / 2)
+                                       * dx ** k * dy ** l)
+    return Problem2D(ADVECTION, nx, ny, P, -1.0, 1.0, -1.0, 1.0, PERIODIC, q, "advection2d-sine", ax, ay)
