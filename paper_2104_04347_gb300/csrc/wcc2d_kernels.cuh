@@ -1,0 +1,365 @@
+// wcc2d_kernels.cuh -- kernels of the 2D WCC path: the fused half-step, the
+// CFL rate of a loaded stage, and the conversions between the host layout
+// [row][col][var][q] (FP64) and the device planes.
+//
+// Device layout: plane (v, q) holds u_{kx,ly} of variable v (q = position of
+// (k, l)) for every cell, row-major with `pitch` elements per row; planes are
+// `plane` elements apart.  T is double (FP64 path) or float (FP32 path).
+//
+// The half-step kernel runs one CTA of TW threads per strip of TW - 1 new
+// columns and `rows_per_cta` new rows.  It marches up the strip: each step
+// computes the Cauchy-Kovalewski expansion and Appendix-B terms of one row of
+// TW parents (thread t: parent column t of the strip) into a two-row ring
+// in shared memory; the new cells between the previous parent row and this
+// one then read their four parents from the ring (thread t: new cell between
+// parent columns t and t + 1).  Every parent is expanded once per strip; the
+// first parent row of a strip is also expanded by the strip below.
+#pragma once
+
+#include <algorithm>
+
+#include "wcc2d_scheme.cuh"
+
+namespace wcc2d {
+
+struct DevState2D {
+    // rate_bits[s]: max over the stage of parity s of s_x/dx + s_y/dy at
+    // the cell centres, as the bit pattern of a non-negative double
+    unsigned long long rate_bits[2];
+    double t;
+    long long step;
+    unsigned int blocks_done;
+    unsigned int err;  // ERR_* bits, sticky
+};
+
+struct Step2D {
+    const void* in;
+    void* out;
+    long long pitch, plane;
+    long long rows_alloc;  // rows of a plane
+    int nx_old, ny_old, nx_new, ny_new;
+    int parity, bc, rows_per_cta;
+    double dx, dy;
+    double dt_given;  // > 0: the half-step size; otherwise cfl / rate of the old stage
+    double cfl;
+    Law2D law;
+    DevState2D* st;
+    double* hist;
+    long long hist_cap;
+};
+
+__device__ __forceinline__ int parent_index(int j, int n_old, int bc) {
+    if (bc == PERIODIC) {
+        j %= n_old;
+        return j < 0 ? j + n_old : j;
+    }
+    return j < 0 ? 0 : (j > n_old - 1 ? n_old - 1 : j);
+}
+
+// Reads parent records from the ring: vertex r = 0..3 is parent column t
+// (r = 0, 3) or t + 1 (r = 1, 2) of the lower (r = 0, 1) or upper row.
+template <class T, int TW, int NV, int NQ1>
+struct RingReader {
+    const T* lo;
+    const T* hi;
+    int t;
+    __device__ __forceinline__ T get(int r, int f) const {
+        return r == 0 ? lo[f * TW + t] : r == 1 ? lo[f * TW + t + 1] : r == 2 ? hi[f * TW + t + 1] : hi[f * TW + t];
+    }
+    __device__ __forceinline__ T qa(int r, int v, int s) const { return get(r, v * 4 + s); }
+    __device__ __forceinline__ T fl(int r, int v, int s) const { return get(r, NV * 4 + v * 4 + s); }
+    __device__ __forceinline__ T V(int r, int v, int q) const { return get(r, NV * 8 + v * NQ1 + q); }
+};
+
+template <int SYS, int P>
+__host__ __device__ constexpr int record_fields() {
+    return nvars(SYS) * (8 + nq(P - 1));
+}
+
+template <class T, int TW>
+__host__ __device__ constexpr size_t ring_bytes(int fields) {
+    return 2 * (size_t)fields * TW * sizeof(T);
+}
+
+// Block-wide max of the rate and OR of the error bits, one atomic each per
+// CTA; the CTA that finishes last does the half-step's bookkeeping.
+template <class T, int NT>
+__device__ __forceinline__ void finish2d(T rate, unsigned err, double dt, const Step2D& a) {
+    __shared__ double s_max[NT / 32];
+    __shared__ unsigned s_err[NT / 32];
+    double r = (double)rate;
+    if (r != r) {
+        r = INFINITY;
+        err |= ERR_NONFINITE;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    err = __reduce_or_sync(0xffffffffu, err);
+    if ((threadIdx.x & 31) == 0) {
+        s_max[threadIdx.x >> 5] = r;
+        s_err[threadIdx.x >> 5] = err;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = s_max[0];
+        unsigned e = s_err[0];
+#pragma unroll
+        for (int w = 1; w < NT / 32; ++w) {
+            m = fmax(m, s_max[w]);
+            e |= s_err[w];
+        }
+        DevState2D* st = a.st;
+        atomicMax(&st->rate_bits[a.parity ^ 1], (unsigned long long)__double_as_longlong(m));
+        if (e) atomicOr(&st->err, e);
+        __threadfence();
+        const unsigned total = gridDim.x * gridDim.y;
+        const unsigned done = atomicAdd(&st->blocks_done, 1u);
+        if (done == total - 1) {
+            __threadfence();
+            // every CTA has read rate_bits[parity]; clear it for the launch after next
+            st->rate_bits[a.parity] = 0ull;
+            const long long k = st->step;
+            if (k < a.hist_cap) a.hist[k] = dt;
+            st->step = k + 1;
+            st->t = st->t + dt;
+            st->blocks_done = 0u;
+            if (!(dt > 0.0) || dt == INFINITY) st->err |= ERR_NONFINITE;
+            __threadfence();
+        }
+    }
+}
+
+template <int SYS, int P, class T, int TW>
+__global__ void __launch_bounds__(TW) halfstep2d(const Step2D a) {
+    constexpr int NV = nvars(SYS), NQ = nq(P), NQ1 = nq(P - 1);
+    constexpr int NF = record_fields<SYS, P>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* ring = reinterpret_cast<T*>(smem_raw);  // [2][NF][TW]
+
+    const int t = threadIdx.x;
+    const int off = a.parity ? -1 : 0;
+    const int i0 = blockIdx.x * (TW - 1);
+    const int j0 = blockIdx.y * a.rows_per_cta;
+    const int rows = min(a.rows_per_cta, a.ny_new - j0);
+
+    double dt = a.dt_given;
+    if (!(dt > 0.0)) dt = a.cfl / __longlong_as_double((long long)a.st->rate_bits[a.parity]);
+    const T lamx = (T)(dt / a.dx), lamy = (T)(dt / a.dy);
+    const T idx = (T)(1.0 / a.dx), idy = (T)(1.0 / a.dy);
+
+    const T* in = static_cast<const T*>(a.in);
+    T* out = static_cast<T*>(a.out);
+    const int pc = parent_index(i0 + t + off, a.nx_old, a.bc);
+    T rate_max = 0;
+    unsigned err = 0;
+
+    for (int s = 0; s <= rows; ++s) {
+        {
+            const int pr = parent_index(j0 + off + s, a.ny_old, a.bc);
+            long long cell = (long long)pr * a.pitch + pc;
+#ifdef WCC2D_BOUNDS_CHECK
+            // opt-in checked build: an out-of-range parent is recorded and cell 0 read instead
+            if (pr < 0 || pr >= a.rows_alloc || pc < 0 || pc >= a.pitch) {
+                atomicOr(&a.st->err, ERR_BOUNDS);
+                cell = 0;
+            }
+#endif
+            T q[NV][NQ];
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int qq = 0; qq < NQ; ++qq) q[v][qq] = in[(long long)(v * NQ + qq) * a.plane + cell];
+            Parent<SYS, P, T> par;
+            parent_terms<SYS, P, T>(q, lamx, lamy, a.law, par);
+            T* r = ring + (s & 1) * NF * TW;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    r[(v * 4 + k) * TW + t] = par.qa[v][k];
+                    r[(NV * 4 + v * 4 + k) * TW + t] = par.fl[v][k];
+                }
+#pragma unroll
+                for (int qq = 0; qq < NQ1; ++qq) r[(NV * 8 + v * NQ1 + qq) * TW + t] = par.V[v][qq];
+            }
+        }
+        __syncthreads();
+        if (s >= 1 && t < TW - 1 && i0 + t < a.nx_new) {
+            const RingReader<T, TW, NV, NQ1> rd{ring + ((s - 1) & 1) * NF * TW, ring + (s & 1) * NF * TW, t};
+            T D[NV][NQ], ub[NV];
+            linear_cell<SYS, P, T>(rd, lamx, lamy, D, ub);
+            if (a.law.limiter) {
+                if constexpr (SYS == EULER) {
+                    T vv[4][4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) vv[v][r] = rd.V(r, v, 0);
+                    if (!limit_euler<P, T>(D, ub, vv, lamx, lamy, a.law)) err |= ERR_POSITIVITY;
+                } else {
+                    T vv[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) vv[r] = rd.V(r, 0, 0);
+                    limit_scalar<P, T>(D[0], ub[0], vv, a.law);
+                }
+            }
+            const long long cell = (long long)(j0 + s - 1) * a.pitch + (i0 + t);
+            bool store = true;
+#ifdef WCC2D_BOUNDS_CHECK
+            if (j0 + s - 1 >= a.rows_alloc || i0 + t >= a.pitch) {  // recorded, not written
+                atomicOr(&a.st->err, ERR_BOUNDS);
+                store = false;
+            }
+#endif
+            if (store) {
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+#pragma unroll
+                    for (int qq = 0; qq < NQ; ++qq) out[(long long)(v * NQ + qq) * a.plane + cell] = D[v][qq];
+            }
+            T centre[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) centre[v] = D[v][0];
+            const T rate = cfl_rate<SYS, T>(centre, a.law, idx, idy);
+            if (rate != rate) {
+                err |= (SYS == EULER && ub[0] == ub[0]) ? ERR_POSITIVITY : ERR_NONFINITE;
+                rate_max = (T)INFINITY;
+            } else {
+                rate_max = rate > rate_max ? rate : rate_max;
+            }
+        }
+        __syncthreads();
+    }
+    finish2d<T, TW>(rate_max, err, dt, a);
+}
+
+// CFL rate of a loaded stage into rate_bits[0] (and the error bits).
+template <int SYS, class T>
+__global__ void __launch_bounds__(256) stage_rate2d(const T* planes, long long pitch, long long plane, int nx, int ny,
+                                                    int nq_, Law2D law, double dx, double dy, DevState2D* st) {
+    constexpr int NV = nvars(SYS);
+    T m = 0;
+    unsigned err = 0;
+    const long long n = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const long long cell = (c / nx) * pitch + (c % nx);
+        T centre[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) centre[v] = planes[(long long)(v * nq_) * plane + cell];
+        const T r = cfl_rate<SYS, T>(centre, law, (T)(1.0 / dx), (T)(1.0 / dy));
+        if (r != r) {
+            err |= SYS == EULER ? ERR_POSITIVITY : ERR_NONFINITE;
+            m = (T)INFINITY;
+        } else if (r > m) {
+            m = r;
+        }
+    }
+    double r = (double)m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    err = __reduce_or_sync(0xffffffffu, err);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&st->rate_bits[0], (unsigned long long)__double_as_longlong(r));
+        if (err) atomicOr(&st->err, err);
+    }
+}
+
+// host [row][col][v][q] FP64 (staging) -> planes of T, and back; one thread
+// per (cell, value), consecutive threads on consecutive cells of a plane
+template <class T>
+__global__ void aos_to_planes2d(const double* aos, T* planes, int nx, int ny, int nd, long long pitch,
+                                long long plane) {
+    const long long n = (long long)nx * ny;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n * nd;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long f = g / n, c = g % n;
+        planes[f * plane + (c / nx) * pitch + (c % nx)] = (T)aos[c * nd + f];
+    }
+}
+
+template <class T>
+__global__ void planes_to_aos2d(const T* planes, double* aos, int nx, int ny, int nd, long long pitch,
+                                long long plane) {
+    const long long n = (long long)nx * ny;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < n * nd;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long f = g / n, c = g % n;
+        aos[c * nd + f] = (double)planes[f * plane + (c / nx) * pitch + (c % nx)];
+    }
+}
+
+// CTA width of the half-step: 64 threads for FP64, 128 for FP32, narrowed
+// in steps of one warp until the shared ring fits in the 48 KB a kernel gets
+// without the opt-in attribute (Euler at P = 3: 32 for FP64, 96 for FP32).
+template <int SYS, int P, class T>
+constexpr int strip_width() {
+    int tw = sizeof(T) == 8 ? 64 : 128;
+    while (tw > 32 && ring_bytes<T, 1>(record_fields<SYS, P>()) * tw > 48 * 1024) tw -= 32;
+    return tw;
+}
+
+// Launch one half-step of system SYS at degree P in type T.
+template <int SYS, int P, class T>
+cudaError_t launch_halfstep2d_t(const Step2D& a, cudaStream_t stream) {
+    constexpr int TW = strip_width<SYS, P, T>();
+    constexpr size_t smem = ring_bytes<T, TW>(record_fields<SYS, P>());
+    static_assert(smem <= 48 * 1024, "the shared ring must fit without the opt-in attribute");
+    const dim3 grid((a.nx_new + TW - 2) / (TW - 1), (a.ny_new + a.rows_per_cta - 1) / a.rows_per_cta);
+    halfstep2d<SYS, P, T, TW><<<grid, TW, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+// Per-thread local memory (spill stack) of the half-step kernel.
+template <int SYS, int P, class T>
+cudaError_t halfstep2d_local_bytes_t(size_t* bytes) {
+    cudaFuncAttributes attr;
+    cudaError_t e = cudaFuncGetAttributes(&attr, halfstep2d<SYS, P, T, strip_width<SYS, P, T>()>);
+    if (e == cudaSuccess) *bytes = attr.localSizeBytes;
+    return e;
+}
+
+template <int SYS, class T>
+cudaError_t halfstep2d_local_bytes_sys(int P, size_t* bytes) {
+    switch (P) {
+        case 1: return halfstep2d_local_bytes_t<SYS, 1, T>(bytes);
+        case 2: return halfstep2d_local_bytes_t<SYS, 2, T>(bytes);
+        case 3: return halfstep2d_local_bytes_t<SYS, 3, T>(bytes);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int SYS, class T>
+cudaError_t launch_halfstep2d_sys(int P, const Step2D& a, cudaStream_t stream) {
+    switch (P) {
+        case 1: return launch_halfstep2d_t<SYS, 1, T>(a, stream);
+        case 2: return launch_halfstep2d_t<SYS, 2, T>(a, stream);
+        case 3: return launch_halfstep2d_t<SYS, 3, T>(a, stream);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int SYS>
+cudaError_t launch_stage_rate2d_sys(bool fp32, const void* planes, long long pitch, long long plane, int nx, int ny,
+                                    int nq_, const Law2D& law, double dx, double dy, DevState2D* st,
+                                    cudaStream_t stream) {
+    const long long n = (long long)nx * ny;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 152 * 8);
+    if (fp32)
+        stage_rate2d<SYS, float><<<grid, 256, 0, stream>>>(static_cast<const float*>(planes), pitch, plane, nx, ny,
+                                                           nq_, law, dx, dy, st);
+    else
+        stage_rate2d<SYS, double><<<grid, 256, 0, stream>>>(static_cast<const double*>(planes), pitch, plane, nx,
+                                                            ny, nq_, law, dx, dy, st);
+    return cudaGetLastError();
+}
+
+}  // namespace wcc2d
+
+namespace wcc2d {
+// Instantiated in wcc2d_scalar.cu, wcc2d_euler_f64.cu, wcc2d_euler_f32.cu.
+cudaError_t launch_halfstep2d(int system, int P, bool fp32, const Step2D& a, cudaStream_t stream);
+cudaError_t halfstep2d_local_bytes(int system, int P, bool fp32, size_t* bytes);
+cudaError_t launch_stage_rate2d(int system, bool fp32, const void* planes, long long pitch, long long plane, int nx,
+                                int ny, int nq_, const Law2D& law, double dx, double dy, DevState2D* st,
+                                cudaStream_t stream);
+}  // namespace wcc2d

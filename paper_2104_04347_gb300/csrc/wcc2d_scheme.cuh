@@ -1,0 +1,531 @@
+// wcc2d_scheme.cuh -- device arithmetic of the 2D WCC half-step (Sec. 3.1,
+// Sec. 3.2, Sec. 4 and Appendix B of arXiv 2104.04347), in the compute type
+// T (double or float).
+//
+// DOFs are the paper's scaled derivatives u_{kx,ly} = dx^k dy^l d^k_x d^l_y u
+// at the cell centre (Eq. 2DPolynomial_Space), k + l <= P, at position
+// q = (k+l)(k+l+1)/2 + l of a variable's block.  Space-time series are kept
+// as cubes X[k][l][m] (dx^k dy^l dt^m d^k_x d^l_y d^m_t), of which only the
+// entries with k + l + m <= P are ever touched; every loop is unrolled so that
+// each entry is a register and each coefficient a compile-time constant.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+namespace wcc2d {
+
+enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
+enum { PERIODIC = 0, TRANSMISSIVE = 1 };
+enum : unsigned { ERR_NONFINITE = 1u, ERR_POSITIVITY = 2u, ERR_BOUNDS = 4u /* checked build only */ };
+
+__host__ __device__ constexpr int nvars(int sys) { return sys == EULER ? 4 : 1; }
+__host__ __device__ constexpr int nq(int P) { return (P + 1) * (P + 2) / 2; }
+__host__ __device__ constexpr int qidx(int k, int l) { return (k + l) * (k + l + 1) / 2 + l; }
+__host__ __device__ constexpr double factd(int n) { return n <= 1 ? 1.0 : n * factd(n - 1); }
+__host__ __device__ constexpr double binomd(int n, int k) { return factd(n) / (factd(k) * factd(n - k)); }
+__host__ __device__ constexpr double pow2m(int n) { return n <= 0 ? 1.0 : 0.5 * pow2m(n - 1); }  // 2^-n
+__host__ __device__ constexpr double sgnd(int k) { return (k & 1) ? -1.0 : 1.0; }              // (-1)^k
+__host__ __device__ constexpr double ipow(double x, int n) { return n <= 0 ? 1.0 : x * ipow(x, n - 1); }
+
+// mean of xi^e over [-1/2, 1/2]
+__host__ __device__ constexpr double moment(int e) { return (e & 1) ? 0.0 : pow2m(e) / (e + 1); }
+
+// Coefficient of c_q c_q2 in the smoothness indicator of Eq.
+// 2DSmoothIndicator (scaled form: the mean over the cell of the squared
+// xi/eta-derivatives of every order 1..P), for q = (a, b), q2 = (a2, b2).
+__host__ __device__ constexpr double beta_coef(int P, int a, int b, int a2, int b2) {
+    double s = 0.0;
+    for (int k = 0; k <= P; ++k)
+        for (int l = 0; k + l <= P; ++l) {
+            if (k + l == 0 || a < k || b < l || a2 < k || b2 < l) continue;
+            s += moment(a - k + a2 - k) * moment(b - l + b2 - l) /
+                 (factd(a - k) * factd(b - l) * factd(a2 - k) * factd(b2 - l));
+        }
+    return s;
+}
+
+// Value at a vertex (sx/2, sy/2) of the monomial with scaled derivative
+// u_{ax,by}: (sx/2)^a (sy/2)^b / (a! b!).
+__host__ __device__ constexpr double vertex_coef(int a, int b, int sx, int sy) {
+    return ipow(0.5 * sx, a) * ipow(0.5 * sy, b) / (factd(a) * factd(b));
+}
+
+// Physical constants and options a kernel needs.
+struct Law2D {
+    double ax, ay;     // advection velocity
+    double gamma;      // Euler
+    double alpha, eps; // limiter weights
+    int limiter;
+};
+
+template <class T>
+__device__ __forceinline__ T weight_pow(T x, T alpha) {
+    return alpha == (T)2 ? x * x : (T)pow((double)x, (double)alpha);
+}
+
+// ------------------------------------------------------------------ parent
+
+// What an old cell contributes to the new cells it touches (Appendix B,
+// Eq. SubEq:2DUij), per variable v:
+//   qa[v][0..3]: quarter averages RU, RD, LU, LD at t^n;
+//   fl[v][0..3]: time-averaged edge fluxes f_U, f_D (line x = x_i) and
+//                g_R, g_L (line y = y_j) over [t^n, t^{n+1/2}];
+//   V[v][q]:     scaled derivatives at the centre at t^{n+1/2}, k + l <= P - 1
+//                (the entries Eqs. SubEq:2DUx, SubEq:2DUy read; q = 0 is the
+//                vertex value of the limiter).
+template <int SYS, int P, class T>
+struct Parent {
+    static constexpr int NV = nvars(SYS);
+    static constexpr int NQ1 = nq(P - 1);
+    T qa[NV][4];
+    T fl[NV][4];
+    T V[NV][NQ1];
+};
+
+// Cauchy-Kovalewski procedure in 2D (Sec. 3.1; Sec. 4 for systems) in
+// scaled form, U_{k,l,m+1} = -lamx F_{k+1,l,m} - lamy G_{k,l+1,m}, with the
+// Leibniz rule for products and quotients (Dyson / Dumbser-Munz).  Each flux
+// entry is used as soon as it is formed: for the next time level of U and
+// for the edge-flux integrals of Appendix B.
+template <int SYS, int P, class T>
+__device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T lamx, T lamy, const Law2D& law,
+                                             Parent<SYS, P, T>& out) {
+    constexpr int NV = nvars(SYS);
+    // quarter averages: mean of xi^k over [0, 1/2] is 1/((k+1) 2^k), (-1)^k that over [-1/2, 0]
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        T ru = 0, rd = 0, lu = 0, ld = 0;
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int l = 0; l <= P - k; ++l) {
+                const T d = q[v][qidx(k, l)];
+                const T c = (T)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1));
+                const T cd = c * d;
+                ru += cd;
+                rd += (T)sgnd(l) * cd;
+                lu += (T)sgnd(k) * cd;
+                ld += (T)(sgnd(k) * sgnd(l)) * cd;
+            }
+        out.qa[v][0] = ru;
+        out.qa[v][1] = rd;
+        out.qa[v][2] = lu;
+        out.qa[v][3] = ld;
+#pragma unroll
+        for (int s = 0; s < 4; ++s) out.fl[v][s] = 0;
+    }
+
+    T U[NV][P + 1][P + 1][P + 1];
+    T w1[P + 1][P + 1][P + 1], w2[P + 1][P + 1][P + 1], Ep[P + 1][P + 1][P + 1];
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 0; k <= P; ++k)
+#pragma unroll
+            for (int l = 0; l <= P - k; ++l) U[v][k][l][0] = q[v][qidx(k, l)];
+
+#pragma unroll
+    for (int m = 0; m <= P; ++m) {
+        if (m < P) {
+#pragma unroll
+            for (int v = 0; v < NV; ++v)
+#pragma unroll
+                for (int k = 0; k <= P - m - 1; ++k)
+#pragma unroll
+                    for (int l = 0; l <= P - m - 1 - k; ++l) U[v][k][l][m + 1] = 0;
+        }
+#pragma unroll
+        for (int k = 0; k <= P - m; ++k)
+#pragma unroll
+            for (int l = 0; l <= P - m - k; ++l) {
+                T F[NV], G[NV];
+                if constexpr (SYS == ADVECTION) {
+                    F[0] = (T)law.ax * U[0][k][l][m];
+                    G[0] = (T)law.ay * U[0][k][l][m];
+                } else if constexpr (SYS == BURGERS) {
+                    T s = 0;
+#pragma unroll
+                    for (int i = 0; i <= k; ++i)
+#pragma unroll
+                        for (int j = 0; j <= l; ++j)
+#pragma unroll
+                            for (int n = 0; n <= m; ++n)
+                                s += (T)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * U[0][i][j][n] *
+                                     U[0][k - i][l - j][m - n];
+                    F[0] = (T)0.5 * s;
+                    G[0] = F[0];
+                } else {
+                    // velocities from rho w = momentum, solved entry by entry
+                    T s1 = U[1][k][l][m], s2 = U[2][k][l][m];
+#pragma unroll
+                    for (int i = 0; i <= k; ++i)
+#pragma unroll
+                        for (int j = 0; j <= l; ++j)
+#pragma unroll
+                            for (int n = 0; n <= m; ++n) {
+                                if (i + j + n == 0) continue;
+                                const T c = (T)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * U[0][i][j][n];
+                                s1 -= c * w1[k - i][l - j][m - n];
+                                s2 -= c * w2[k - i][l - j][m - n];
+                            }
+                    const T inv_rho = (T)1 / U[0][0][0][0];
+                    w1[k][l][m] = s1 * inv_rho;
+                    w2[k][l][m] = s2 * inv_rho;
+                    T qxx = 0, qxy = 0, qyy = 0;
+#pragma unroll
+                    for (int i = 0; i <= k; ++i)
+#pragma unroll
+                        for (int j = 0; j <= l; ++j)
+#pragma unroll
+                            for (int n = 0; n <= m; ++n) {
+                                const T c = (T)(binomd(k, i) * binomd(l, j) * binomd(m, n));
+                                const T a1 = c * U[1][i][j][n], a2 = c * U[2][i][j][n];
+                                qxx += a1 * w1[k - i][l - j][m - n];
+                                qxy += a1 * w2[k - i][l - j][m - n];
+                                qyy += a2 * w2[k - i][l - j][m - n];
+                            }
+                    const T p = (T)(law.gamma - 1.0) * (U[3][k][l][m] - (T)0.5 * (qxx + qyy));
+                    Ep[k][l][m] = U[3][k][l][m] + p;
+                    T e1 = 0, e2 = 0;
+#pragma unroll
+                    for (int i = 0; i <= k; ++i)
+#pragma unroll
+                        for (int j = 0; j <= l; ++j)
+#pragma unroll
+                            for (int n = 0; n <= m; ++n) {
+                                const T c = (T)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * Ep[i][j][n];
+                                e1 += c * w1[k - i][l - j][m - n];
+                                e2 += c * w2[k - i][l - j][m - n];
+                            }
+                    F[0] = U[1][k][l][m];
+                    F[1] = qxx + p;
+                    F[2] = qxy;
+                    F[3] = e1;
+                    G[0] = U[2][k][l][m];
+                    G[1] = qxy;
+                    G[2] = qyy + p;
+                    G[3] = e2;
+                }
+#pragma unroll
+                for (int v = 0; v < NV; ++v) {
+                    // (k + l >= 1 implies m + 1 <= P; the clamps only keep the
+                    // indices of the branches not taken in range)
+                    if (k >= 1) U[v][k >= 1 ? k - 1 : 0][l][m < P ? m + 1 : P] -= lamx * F[v];
+                    if (l >= 1) U[v][k][l >= 1 ? l - 1 : 0][m < P ? m + 1 : P] -= lamy * G[v];
+                    // Eqs. SubEq:2DFluxFU ... GL: one space direction along the edge, and time
+                    const T ct = (T)(1.0 / factd(m + 1));
+                    if (k == 0) {
+                        const T cs = (T)(pow2m(l) / factd(l + 1)) * ct * F[v];
+                        out.fl[v][0] += cs;
+                        out.fl[v][1] += (T)sgnd(l) * cs;
+                    }
+                    if (l == 0) {
+                        const T cs = (T)(pow2m(k) / factd(k + 1)) * ct * G[v];
+                        out.fl[v][2] += cs;
+                        out.fl[v][3] += (T)sgnd(k) * cs;
+                    }
+                }
+            }
+    }
+    // Eq. SubEq:2DUij
+#pragma unroll
+    for (int v = 0; v < NV; ++v)
+#pragma unroll
+        for (int k = 0; k <= P - 1; ++k)
+#pragma unroll
+            for (int l = 0; l <= P - 1 - k; ++l) {
+                T s = 0;
+#pragma unroll
+                for (int m = 0; m <= P - k - l; ++m) s += (T)(1.0 / factd(m)) * U[v][k][l][m];
+                out.V[v][qidx(k, l)] = s;
+            }
+}
+
+// ---------------------------------------------------------------- new cell
+
+// The linear part of a new cell (Sec. 3.1) from its four parents in the
+// vertex order of Eq. 2DTaylorSeries (1 lower left, 2 lower right, 3 upper
+// right, 4 upper left): the cell average (Eq. 2DIntegral), the derivatives
+// from the highest degree down (Eqs. SubEq:2DUx, SubEq:2DUy, mixed ones as
+// the mean of both), the point value (Eq. SubEq:2DCellAVG).  get(r, field)
+// reads field of parent r.
+template <int SYS, int P, class T, class Rd>
+__device__ __forceinline__ void linear_cell(const Rd& rd, T lamx, T lamy, T (&D)[nvars(SYS)][nq(P)],
+                                            T (&ubar)[nvars(SYS)]) {
+    constexpr int NV = nvars(SYS);
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+        const T quarters = rd.qa(0, v, 0) + rd.qa(3, v, 1) + rd.qa(1, v, 2) + rd.qa(2, v, 3);
+        const T fx = (rd.fl(0, v, 0) + rd.fl(3, v, 1)) - (rd.fl(1, v, 0) + rd.fl(2, v, 1));
+        const T gy = (rd.fl(0, v, 2) + rd.fl(1, v, 3)) - (rd.fl(3, v, 2) + rd.fl(2, v, 3));
+        ubar[v] = (T)0.25 * quarters + (T)0.5 * lamx * fx + (T)0.5 * lamy * gy;
+#pragma unroll
+        for (int d = P; d >= 1; --d)
+#pragma unroll
+            for (int b = 0; b <= d; ++b) {
+                const int a = d - b;
+                T sum = 0;
+                if (a >= 1) {
+                    const int k = a - 1, l = b, r = P - k - l;
+                    T s = (T)0.5 * ((rd.V(1, v, qidx(k, l)) + rd.V(2, v, qidx(k, l))) -
+                                    (rd.V(0, v, qidx(k, l)) + rd.V(3, v, qidx(k, l))));
+#pragma unroll
+                    for (int s3 = 3; s3 <= r; ++s3)
+                        s -= (T)((pow2m(s3) - ipow(-0.5, s3)) / factd(s3)) * D[v][qidx(k + s3, l)];
+#pragma unroll
+                    for (int t = 2; t <= r; ++t)
+#pragma unroll
+                        for (int s1 = 1; s1 <= r - t; ++s1)
+                            if (s1 & 1)
+                                s -= (T)(2.0 * pow2m(s1 + t) / (factd(s1) * factd(t)) * ((t & 1) ? 0.0 : 1.0)) *
+                                     D[v][qidx(k + s1, l + t)];
+                    sum += s;
+                }
+                if (b >= 1) {
+                    const int k = a, l = b - 1, r = P - k - l;
+                    T s = (T)0.5 * ((rd.V(3, v, qidx(k, l)) + rd.V(2, v, qidx(k, l))) -
+                                    (rd.V(0, v, qidx(k, l)) + rd.V(1, v, qidx(k, l))));
+#pragma unroll
+                    for (int t3 = 3; t3 <= r; ++t3)
+                        s -= (T)((pow2m(t3) - ipow(-0.5, t3)) / factd(t3)) * D[v][qidx(k, l + t3)];
+#pragma unroll
+                    for (int t = 1; t <= r; ++t)
+#pragma unroll
+                        for (int s2 = 2; s2 <= r - t; ++s2)
+                            if ((t & 1) && !(s2 & 1))
+                                s -= (T)(2.0 * pow2m(s2 + t) / (factd(s2) * factd(t))) * D[v][qidx(k + s2, l + t)];
+                    sum += s;
+                }
+                D[v][qidx(a, b)] = (a >= 1 && b >= 1) ? (T)0.5 * sum : sum;
+            }
+        T s = ubar[v];
+#pragma unroll
+        for (int k = 0; k <= P; k += 2)
+#pragma unroll
+            for (int l = 0; l <= P - k; l += 2) {
+                if (k + l == 0) continue;
+                s -= (T)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1)) * D[v][qidx(k, l)];
+            }
+        D[v][0] = s;
+    }
+}
+
+// ----------------------------------------------------------------- limiter
+
+// Limiter of Sec. 3.2 for one scalar component: d (the DOFs of u_0, replaced
+// by those of u_*), its cell average ub and the vertex values vv[0..3] at
+// vertices 1..4.  FP64 follows the printed weights; in FP32 the same weights
+// are formed from ratios (every term divided by the largest) so that the
+// tiny epsilon cannot overflow them.
+template <int P, class T>
+__device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[4], const Law2D& law) {
+    constexpr int NQ = nq(P);
+    T sx[5], sy[5];
+    sx[1] = (T)2 * ub - (vv[0] + vv[3]);
+    sy[1] = vv[3] - vv[0];
+    sx[2] = vv[1] - vv[0];
+    sy[2] = (T)2 * ub - (vv[0] + vv[1]);
+    sx[3] = (vv[1] + vv[2]) - (T)2 * ub;
+    sy[3] = vv[2] - vv[1];
+    sx[4] = vv[2] - vv[3];
+    sy[4] = (vv[3] + vv[2]) - (T)2 * ub;
+    T beta[5];
+    {
+        T b = 0;
+#pragma unroll
+        for (int a = 0; a <= P; ++a)
+#pragma unroll
+            for (int bb = 0; bb <= P - a; ++bb)
+#pragma unroll
+                for (int a2 = 0; a2 <= P; ++a2)
+#pragma unroll
+                    for (int b2 = 0; b2 <= P - a2; ++b2) {
+                        if (qidx(a2, b2) < qidx(a, bb)) continue;
+                        const double c = beta_coef(P, a, bb, a2, b2) * (qidx(a2, b2) == qidx(a, bb) ? 1.0 : 2.0);
+                        if (c != 0.0) b += (T)c * d[qidx(a, bb)] * d[qidx(a2, b2)];
+                    }
+        beta[0] = b;
+    }
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) beta[m] = sx[m] * sx[m] + sy[m] * sy[m];
+    const T alpha = (T)law.alpha, eps = (T)law.eps;
+    T w[5];
+    if constexpr (P == 1) {
+        // Eq. 2D2ndOrderWeights
+        if constexpr (sizeof(T) == 8) {
+            T s = 0;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                w[m] = weight_pow<T>((T)1 / (beta[m] + eps), alpha);
+                s += w[m];
+            }
+#pragma unroll
+            for (int m = 0; m < 5; ++m) w[m] = w[m] / s;
+        } else {
+            T bmin = beta[0] + eps;
+#pragma unroll
+            for (int m = 1; m < 5; ++m) bmin = fminf(bmin, beta[m] + eps);
+            T s = 0;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                w[m] = weight_pow<T>(bmin / (beta[m] + eps), alpha);
+                s += w[m];
+            }
+#pragma unroll
+            for (int m = 0; m < 5; ++m) w[m] = w[m] / s;
+        }
+    } else {
+        // Eq. 1DHighOrderWeights in the 2D form of Sec. 3.2: sigma from the
+        // four vertex residuals, tau from the degree-P derivatives
+        T sigma = 0;
+        const int vsx[4] = {-1, 1, 1, -1}, vsy[4] = {-1, -1, 1, 1};
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            T val = 0;
+#pragma unroll
+            for (int a = 0; a <= P; ++a)
+#pragma unroll
+                for (int b = 0; b <= P - a; ++b) val += (T)vertex_coef(a, b, vsx[r], vsy[r]) * d[qidx(a, b)];
+            const T res = val - vv[r];
+            sigma += res * res;
+        }
+        T tau = 0;
+#pragma unroll
+        for (int k = 0; k <= P; ++k) tau += d[qidx(k, P - k)] * d[qidx(k, P - k)];
+        const T st = sigma * tau;
+        if constexpr (sizeof(T) == 8) {
+            T s = 0;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                w[m] = weight_pow<T>(st / (beta[m] * beta[m] + eps), alpha);
+                if (m == 0) w[m] += (T)1;
+                s += w[m];
+            }
+#pragma unroll
+            for (int m = 0; m < 5; ++m) w[m] = w[m] / s;
+        } else {
+            // divide every weight by (st / dmin)^alpha, dmin the smallest denominator
+            T den[5];
+            T dmin = (T)INFINITY;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) {
+                den[m] = beta[m] * beta[m] + eps;
+                dmin = fminf(dmin, den[m]);
+            }
+            const T lead = weight_pow<T>(dmin / st, alpha);  // the "1 +" of w_0, rescaled
+            if (!(st > (T)0) || isinf(lead)) {
+                w[0] = 1;
+                w[1] = w[2] = w[3] = w[4] = 0;
+            } else {
+                T s = 0;
+#pragma unroll
+                for (int m = 0; m < 5; ++m) {
+                    w[m] = weight_pow<T>(dmin / den[m], alpha);
+                    if (m == 0) w[m] += lead;
+                    s += w[m];
+                }
+#pragma unroll
+                for (int m = 0; m < 5; ++m) w[m] = w[m] / s;
+            }
+        }
+    }
+    // Eq. 2DLimitedPolynomial
+    T l0 = w[0] * d[0], l1 = w[0] * d[1], l2 = w[0] * d[2];
+#pragma unroll
+    for (int m = 1; m <= 4; ++m) {
+        l0 += w[m] * ub;
+        l1 += w[m] * sx[m];
+        l2 += w[m] * sy[m];
+    }
+    d[0] = l0;
+    d[1] = l1;
+    d[2] = l2;
+#pragma unroll
+    for (int i = 3; i < NQ; ++i) d[i] = w[0] * d[i];
+}
+
+// Rotated characteristic limiting for the 2D Euler equations (Sec. 4):
+// direction n from the central-difference gradient of rho e (Eq.
+// RotatedNormal), eigenvectors of cos(theta) dF/dU + sin(theta) dG/dU at the
+// cell average in closed form, the scalar limiter on each characteristic
+// component, and back.  Returns false if the average has non-positive
+// density or pressure.
+template <int P, class T>
+__device__ __forceinline__ bool limit_euler(T (&D)[4][nq(P)], const T (&ub)[4], const T (&vv)[4][4], T lamx,
+                                            T lamy, const Law2D& law) {
+    constexpr int NQ = nq(P);
+    T gx = (T)0.5 * ((vv[3][1] + vv[3][2]) - (vv[3][0] + vv[3][3])) * lamx;
+    T gy = (T)0.5 * ((vv[3][3] + vv[3][2]) - (vv[3][0] + vv[3][1])) * lamy;
+    const T norm = sqrt(gx * gx + gy * gy);
+    T nx = 1, ny = 0;
+    if (norm > (T)0) {
+        nx = gx / norm;
+        ny = gy / norm;
+    }
+    const T gm1 = (T)(law.gamma - 1.0);
+    const T rho = ub[0], u = ub[1] / rho, v = ub[2] / rho;
+    const T q2 = u * u + v * v;
+    const T p = gm1 * (ub[3] - (T)0.5 * rho * q2);
+    if (!(rho > (T)0) || !(p > (T)0)) return false;
+    const T c = sqrt((T)law.gamma * p / rho);
+    const T H = (ub[3] + p) / rho;
+    const T un = u * nx + v * ny, ut = -u * ny + v * nx;
+    const T b1 = gm1 / (c * c), b2 = (T)0.5 * b1 * q2, ic = (T)1 / c;
+    const T R[4][4] = {{1, 1, 0, 1},
+                       {u - c * nx, u, -ny, u + c * nx},
+                       {v - c * ny, v, nx, v + c * ny},
+                       {H - c * un, (T)0.5 * q2, ut, H + c * un}};
+    const T L[4][4] = {{(T)0.5 * (b2 + un * ic), (T)-0.5 * (b1 * u + nx * ic), (T)-0.5 * (b1 * v + ny * ic), (T)0.5 * b1},
+                       {(T)1 - b2, b1 * u, b1 * v, -b1},
+                       {-ut, -ny, nx, 0},
+                       {(T)0.5 * (b2 - un * ic), (T)-0.5 * (b1 * u - nx * ic), (T)-0.5 * (b1 * v - ny * ic), (T)0.5 * b1}};
+    T cd[4][NQ], cub[4], cvv[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        cub[i] = 0;
+#pragma unroll
+        for (int r = 0; r < 4; ++r) cvv[i][r] = 0;
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) cd[i][qq] = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            cub[i] += L[i][j] * ub[j];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) cvv[i][r] += L[i][j] * vv[j][r];
+#pragma unroll
+            for (int qq = 0; qq < NQ; ++qq) cd[i][qq] += L[i][j] * D[j][qq];
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) limit_scalar<P, T>(cd[i], cub[i], cvv[i], law);
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int qq = 0; qq < NQ; ++qq) {
+            T s = 0;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) s += R[j][i] * cd[i][qq];
+            D[j][qq] = s;
+        }
+    return true;
+}
+
+// s_x/dx + s_y/dy at a cell's centre point values (the 2D CFL rate; the
+// half step is dt = nu / max of it).  NaN for non-physical Euler states.
+template <int SYS, class T>
+__device__ __forceinline__ T cfl_rate(const T* centre, const Law2D& law, T idx, T idy) {
+    if constexpr (SYS == ADVECTION) {
+        return fabs((T)law.ax) * idx + fabs((T)law.ay) * idy;
+    } else if constexpr (SYS == BURGERS) {
+        return fabs(centre[0]) * (idx + idy);
+    } else {
+        const T rho = centre[0], u = centre[1] / rho, v = centre[2] / rho;
+        const T p = (T)(law.gamma - 1.0) * (centre[3] - (T)0.5 * rho * (u * u + v * v));
+        if (!(rho > (T)0) || !(p > (T)0)) return (T)NAN;
+        const T c = sqrt((T)law.gamma * p / rho);
+        return (fabs(u) + c) * idx + (fabs(v) + c) * idy;
+    }
+}
+
+}  // namespace wcc2d

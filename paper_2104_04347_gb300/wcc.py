@@ -47,6 +47,23 @@ class Options(ctypes.Structure):
     ]
 
 
+class Options2D(ctypes.Structure):
+    """Mirror of wcc2d_options (include/wcc2d.h)."""
+
+    _fields_ = [
+        ("precision", ctypes.c_int),
+        ("limiter", ctypes.c_int),
+        ("alpha", ctypes.c_double),
+        ("eps", ctypes.c_double),
+        ("gamma", ctypes.c_double),
+        ("ax", ctypes.c_double),
+        ("ay", ctypes.c_double),
+        ("rows_per_cta", ctypes.c_int),
+        ("reserved", ctypes.c_int),
+        ("cuda_stream", ctypes.c_void_p),
+    ]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -91,6 +108,22 @@ _SIGS = {
     "wcc_batch_destroy": (None, [ctypes.c_void_p]),
     "wcc_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
     "wcc_destroy": (None, [ctypes.c_void_p]),
+    "wcc2d_default_options": (None, [ctypes.POINTER(Options2D)]),
+    "wcc2d_create": (ctypes.c_int, [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+                                    ctypes.c_int, _dp, ctypes.c_int, ctypes.POINTER(Options2D)]),
+    "wcc2d_stage_dims": (ctypes.c_int, [ctypes.c_void_p, _i64p, _i64p]),
+    "wcc2d_set_initial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "wcc2d_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
+    "wcc2d_step_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp]),
+    "wcc2d_step_until": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double, _i64p]),
+    "wcc2d_get_dofs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
+    "wcc2d_get_state": (ctypes.c_int, [ctypes.c_void_p, _dp, _i64p, ctypes.POINTER(ctypes.c_int)]),
+    "wcc2d_get_dt_history": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int64, _i64p]),
+    "wcc2d_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
+    "wcc2d_launch_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc2d_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
+    "wcc2d_last_error": (ctypes.c_char_p, [ctypes.c_void_p]),
+    "wcc2d_destroy": (ctypes.c_int, [ctypes.c_void_p]),
 }
 
 
@@ -98,7 +131,7 @@ def header_functions(path: str = HEADER) -> list[str]:
     """Names of the functions declared in a public header."""
     text = open(path).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(wcc_\w+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(wcc(?:2d)?_\w+)\s*\(", text)))
 
 
 def load(path: str = LIB_PATH):
@@ -376,4 +409,106 @@ class Batch:
     def device_bytes(self) -> int:
         b = ctypes.c_int64()
         self._check(self.lib.wcc_batch_device_bytes(self.h, ctypes.byref(b)))
+        return b.value
+
+
+class Solver2D:
+    """One 2D WCC problem on the GPU (wraps a wcc2d_handle, include/wcc2d.h).
+
+    ``dofs`` arrays are float64 [rows, cols, nv, nq] of the scaled
+    derivatives u_{kx,ly}, nq = (P+1)(P+2)/2, position (k+l)(k+l+1)/2 + l.
+    ``domain`` is (x_S, x_E, y_S, y_E).  precision is FP64 or FP32."""
+
+    def __init__(self, system: int, nx: int, ny: int, P: int, domain, bc: int, *, precision: int = FP64,
+                 limiter: bool = True, alpha: float = 2.0, eps: float = 1e-40, gamma: float = 1.4,
+                 ax: float = 1.0, ay: float = 1.0, rows_per_cta: int = 32, stream: int | None = None):
+        self.lib = load()
+        o = Options2D()
+        self.lib.wcc2d_default_options(ctypes.byref(o))
+        o.precision = precision
+        o.limiter = 1 if limiter else 0
+        o.alpha, o.eps, o.gamma, o.ax, o.ay = alpha, eps, gamma, ax, ay
+        o.rows_per_cta = rows_per_cta
+        o.cuda_stream = stream
+        h = ctypes.c_void_p()
+        dom = (ctypes.c_double * 4)(*[float(d) for d in domain])
+        rc = self.lib.wcc2d_create(ctypes.byref(h), system, int(nx), int(ny), int(P), dom, bc, ctypes.byref(o))
+        if rc != 0:
+            raise WCCError(rc, self.lib.wcc2d_last_error(None).decode())
+        self.h = h
+        self.system, self.nx, self.ny, self.P, self.bc = system, int(nx), int(ny), int(P), bc
+        self.nv = 4 if system == EULER else 1
+        self.nq = (P + 1) * (P + 2) // 2
+
+    def _check(self, rc: int) -> None:
+        if rc != 0:
+            raise WCCError(rc, self.lib.wcc2d_last_error(self.h).decode())
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            self.lib.wcc2d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def stage_dims(self):
+        nx, ny = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.wcc2d_stage_dims(self.h, ctypes.byref(nx), ctypes.byref(ny)))
+        return nx.value, ny.value
+
+    def set_initial(self, dofs: np.ndarray) -> None:
+        a = np.ascontiguousarray(dofs, dtype=np.float64)
+        self._check(self.lib.wcc2d_set_initial(self.h, _ptr(a), a.size))
+
+    def step(self, nsteps: int, cfl: float) -> None:
+        self._check(self.lib.wcc2d_step(self.h, int(nsteps), float(cfl)))
+
+    def step_dt(self, dts) -> None:
+        d = np.ascontiguousarray(dts, dtype=np.float64)
+        self._check(self.lib.wcc2d_step_dt(self.h, d.size, d.ctypes.data_as(_dp)))
+
+    def step_until(self, t_end: float, cfl: float) -> int:
+        n = ctypes.c_int64(0)
+        self._check(self.lib.wcc2d_step_until(self.h, float(t_end), float(cfl), ctypes.byref(n)))
+        return int(n.value)
+
+    def get_dofs(self) -> np.ndarray:
+        nx, ny = self.stage_dims()
+        out = np.empty((ny, nx, self.nv, self.nq))
+        self._check(self.lib.wcc2d_get_dofs(self.h, _ptr(out), out.size))
+        return out
+
+    def state(self):
+        t, s, p = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int()
+        self._check(self.lib.wcc2d_get_state(self.h, ctypes.byref(t), ctypes.byref(s), ctypes.byref(p)))
+        return t.value, s.value, p.value
+
+    def dt_history(self) -> np.ndarray:
+        n = ctypes.c_int64()
+        self._check(self.lib.wcc2d_get_dt_history(self.h, None, 0, ctypes.byref(n)))
+        out = np.empty(n.value)
+        self._check(self.lib.wcc2d_get_dt_history(self.h, out.ctypes.data_as(_dp), out.size, ctypes.byref(n)))
+        return out
+
+    def synchronize(self) -> None:
+        self._check(self.lib.wcc2d_synchronize(self.h))
+
+    def launch_count(self) -> int:
+        b = ctypes.c_int64()
+        self._check(self.lib.wcc2d_launch_count(self.h, ctypes.byref(b)))
+        return b.value
+
+    def device_bytes(self) -> int:
+        b = ctypes.c_int64()
+        self._check(self.lib.wcc2d_device_bytes(self.h, ctypes.byref(b)))
         return b.value

@@ -1,0 +1,200 @@
+"""GPU parity of the 2D path (include/wcc2d.h) against the 2D oracle.
+
+* One half-step from the same state, both parities, every system, P = 1..3,
+  limiter on and off, periodic and transmissive, on meshes whose strips and
+  rows end in ragged tails (FP64 strips are 63 new columns wide, FP32 strips
+  127; 32 new rows per CTA): FP64 within 1e-11 of each variable's scale.
+* Trajectories through wcc2d_step_until, the oracle replaying the same
+  half-step sizes: FP64 within 1e-10 on smooth data; FP32 in L1.
+* Table 3 (Sec. 5.3) on the GPU at mesh 1/10: the same errors as the oracle.
+* Errors: non-physical data, out-of-order calls.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2104_04347_gb300 import inputs, wcc
+
+pytestmark = pytest.mark.gpu
+
+CFL = {1: 0.4, 2: 0.3, 3: 0.25}
+EULER, ADV, BURG = inputs.EULER, inputs.ADVECTION, inputs.BURGERS
+
+
+def _scaled_error(a, b):
+    sc = np.maximum(np.max(np.abs(b[:, :, :, 0]), axis=(0, 1)), 1e-300)
+    return float(np.max(np.abs(a - b) / sc[None, None, :, None]))
+
+
+def _solver(pr, precision=wcc.FP64, limiter=True, rows_per_cta=32):
+    return wcc.Solver2D(pr.system, pr.nx, pr.ny, pr.P, (pr.x_l, pr.x_r, pr.y_l, pr.y_r), pr.bc,
+                        precision=precision, limiter=limiter, ax=pr.ax, ay=pr.ay, rows_per_cta=rows_per_cta)
+
+
+def _law(pr, limiter=True):
+    return oracle.make_law2d(pr.system, pr.P, limiter=limiter, bc=pr.bc, ax=pr.ax, ay=pr.ay)
+
+
+def _problem(system, nx, ny, P, bc):
+    """Smooth data of each system on a mesh of nx x ny cells."""
+    if system == EULER:
+        if bc == inputs.PERIODIC and nx == ny:
+            pr = inputs.isentropic_vortex(nx, P)
+            # off-centre, so that x and y and the strips differ
+            pr.q0 = np.roll(pr.q0, (nx // 7, -nx // 5), axis=(0, 1))
+            return pr
+        X, Y = inputs._grid2d(nx, ny, -5.0, 5.0, -4.0, 4.0, bc)
+        dx, dy = 10.0 / nx, 8.0 / ny
+        U = inputs.vortex_conserved(inputs.Taylor2.variable(X - 0.7, 0, P), inputs.Taylor2.variable(Y + 0.4, 1, P))
+        q = np.stack([u.scaled_dofs(dx, dy) for u in U], axis=2)
+        return inputs.Problem2D(EULER, nx, ny, P, -5.0, 5.0, -4.0, 4.0, bc, q, "vortex-rect")
+    pr = inputs.advection2d_sine(nx, ny, P, ax=0.8, ay=-0.55, kx=math.pi, ky=2 * math.pi, phase=0.3)
+    if bc == inputs.TRANSMISSIVE:
+        X, Y = inputs._grid2d(nx, ny, -1.0, 1.0, -1.0, 1.0, bc)
+        dx, dy = 2.0 / nx, 2.0 / ny
+        q = np.zeros((Y.shape[0], X.shape[1], 1, inputs.nq2d(P)))
+        for k in range(P + 1):
+            for l in range(P + 1 - k):
+                q[:, :, 0, inputs.idx2d(k, l)] = (math.pi ** k * (2 * math.pi) ** l * dx ** k * dy ** l *
+                                                  np.sin(math.pi * X + 2 * math.pi * Y + 0.3 + (k + l) * math.pi / 2))
+        pr = inputs.Problem2D(ADV, nx, ny, P, -1.0, 1.0, -1.0, 1.0, bc, q, "sine-rect", 0.8, -0.55)
+    if system == BURG:
+        pr.system = BURG
+        pr.q0 = pr.q0 * 0.5
+        pr.q0[:, :, 0, 0] += 1.0
+    return pr
+
+
+@pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
+@pytest.mark.parametrize("P", [1, 2, 3])
+@pytest.mark.parametrize("system", [ADV, BURG, EULER])
+def test_one_halfstep_each_parity_fp64(system, P, bc):
+    nx, ny = (70, 70) if (system == EULER and bc == inputs.PERIODIC) else (70, 45)
+    pr = _problem(system, nx, ny, P, bc)
+    for limiter in (False, True):
+        law = _law(pr, limiter)
+        with _solver(pr, limiter=limiter) as s:
+            s.set_initial(pr.q0)
+            q = pr.q0
+            for parity in (0, 1):
+                dt = 0.6 * oracle.cfl_dt2d(law, q, pr.dx, pr.dy, 1.0) * CFL[P]
+                s.step_dt([dt])
+                got = s.get_dofs()
+                want = oracle.halfstep2d(law, parity, q, dt / pr.dx, dt / pr.dy)
+                assert got.shape == want.shape
+                err = _scaled_error(got, want)
+                assert err <= 1e-11, (system, P, bc, limiter, parity, err)
+                q = want
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_strip_and_row_tails(P):
+    # meshes of one strip and a bit, rows per CTA that do not divide ny
+    for nx, ny, rows in ((64, 9, 4), (127, 33, 32), (5, 130, 7)):
+        pr = _problem(ADV, nx, ny, P, inputs.TRANSMISSIVE)
+        law = _law(pr)
+        with _solver(pr, rows_per_cta=rows) as s:
+            s.set_initial(pr.q0)
+            s.step_dt([0.01, 0.012, 0.011])
+            got = s.get_dofs()
+        q = pr.q0
+        for parity, dt in enumerate((0.01, 0.012, 0.011)):
+            q = oracle.halfstep2d(law, parity % 2, q, dt / pr.dx, dt / pr.dy)
+        assert _scaled_error(got, q) <= 1e-11, (nx, ny, rows)
+
+
+@pytest.mark.parametrize("limiter", [False, True])
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_vortex_trajectory_fp64(P, limiter):
+    # Without the limiter the trajectory stays within 1e-10.  With it, the
+    # weights in the vortex's near-uniform far field are ratios of
+    # rounding-level quantities (beta, sigma, tau ~ 1e-20), so two correct
+    # FP64 runs that round differently drift apart; the bound is then per
+    # entry max(1e-10 x scale, 50 x the oracle's own spread when its inputs
+    # get 4e-16 relative noise), as in 1D.
+    pr = _problem(EULER, 40, 40, P, inputs.PERIODIC)
+    with _solver(pr, limiter=limiter) as s:
+        s.set_initial(pr.q0)
+        n = s.step_until(0.6, CFL[P])
+        t, steps, parity = s.state()
+        got = s.get_dofs()
+        dts = s.dt_history()
+    assert parity == 0 and n == steps == len(dts) and abs(t - 0.6) <= 1e-12
+    law = _law(pr, limiter)
+    ref = oracle.Solver2D(law, pr.q0, pr.dx, pr.dy)
+    # every CFL step is the oracle's CFL step of the state it advanced
+    for dt in dts[:-2]:
+        assert abs(dt - ref.cfl_dt(CFL[P])) <= 1e-12 * dt
+        ref.step_dt([dt])
+    ref.step_dt(dts[-2:])
+    sc = np.maximum(np.max(np.abs(ref.q[:, :, :, 0]), axis=(0, 1)), 1e-300)[None, None, :, None]
+    bound = 1e-10 * sc
+    if limiter:
+        rng = np.random.default_rng(P)
+        spread = np.zeros_like(ref.q)
+        for _ in range(3):
+            r2 = oracle.Solver2D(law, pr.q0 * (1.0 + 4e-16 * rng.standard_normal(pr.q0.shape)), pr.dx, pr.dy)
+            r2.step_dt(dts)
+            spread = np.maximum(spread, np.abs(r2.q - ref.q))
+        bound = np.maximum(bound, 50.0 * spread)
+    assert float(np.max(np.abs(got - ref.q) / bound)) <= 1.0
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_fp32_follows_the_oracle(P):
+    pr = _problem(EULER, 64, 64, P, inputs.PERIODIC)
+    with _solver(pr, precision=wcc.FP32) as s:
+        s.set_initial(pr.q0)
+        s.step_until(0.5, CFL[P])
+        got = s.get_dofs()
+        dts = s.dt_history()
+    ref = oracle.Solver2D(_law(pr), pr.q0, pr.dx, pr.dy)
+    ref.step_dt(dts)
+    sc = np.max(np.abs(ref.q[:, :, :, 0]), axis=(0, 1))
+    l1 = np.max(np.mean(np.abs(got[:, :, :, 0] - ref.q[:, :, :, 0]), axis=(0, 1)) / sc)
+    assert l1 <= 2e-6, l1
+
+
+def test_table3_mesh_1_10_on_gpu(golden_dir):
+    rows = []
+    with open(f"{golden_dir}/table3_vortex.txt") as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                sch, P, inv, l1, linf = line.split()
+                if int(inv) == 10:
+                    rows.append((sch, int(P), float(l1), float(linf)))
+    for sch, P, l1, linf in rows:
+        pr = inputs.isentropic_vortex(100, P)
+        with _solver(pr, limiter=sch == "WCCS") as s:
+            s.set_initial(pr.q0)
+            s.step_until(2.0, CFL[P])
+            q = s.get_dofs()
+            t = s.state()[0]
+        X, Y = inputs._grid2d(100, 100, -5.0, 5.0, -5.0, 5.0, inputs.PERIODIC)
+        e = np.abs(q[:, :, 0, 0] - inputs.vortex_exact(X, Y, t)[0])
+        assert abs(e.mean() / l1 - 1) < 0.05 and abs(e.max() / linf - 1) < 0.05, (sch, P, e.mean(), e.max())
+
+
+def test_errors_are_reported():
+    pr = _problem(EULER, 16, 16, 2, inputs.PERIODIC)
+    bad = pr.q0.copy()
+    bad[3, 4, 0, 0] = -1.0  # negative density
+    with _solver(pr) as s:
+        with pytest.raises(wcc.WCCError) as ei:
+            s.step(1, 0.3)  # before set_initial
+        assert ei.value.code == -2
+        with pytest.raises(wcc.WCCError) as ei:
+            s.set_initial(bad)
+        assert ei.value.code == -6
+        s.set_initial(pr.q0)
+        s.step(1, 0.3)
+        with pytest.raises(wcc.WCCError) as ei:
+            s.step_until(1.0, 0.3)  # on a half stage
+        assert ei.value.code == -2
+        s.step(1, 0.3)
+        t = s.state()[0]
+        with pytest.raises(wcc.WCCError) as ei:
+            s.step_until(t - 0.1, 0.3)
+        assert ei.value.code == -1
