@@ -13,6 +13,9 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+#include <utility>
+
 namespace wcc2d {
 
 enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
@@ -22,6 +25,14 @@ enum : unsigned { ERR_NONFINITE = 1u, ERR_POSITIVITY = 2u, ERR_BOUNDS = 4u /* ch
 __host__ __device__ constexpr int nvars(int sys) { return sys == EULER ? 4 : 1; }
 __host__ __device__ constexpr int nq(int P) { return (P + 1) * (P + 2) / 2; }
 __host__ __device__ constexpr int qidx(int k, int l) { return (k + l) * (k + l + 1) / 2 + l; }
+// total degree d and the pair (k, l) stored at position q
+__host__ __device__ constexpr int qdeg(int q) {
+    int d = 0;
+    while ((d + 1) * (d + 2) / 2 <= q) ++d;
+    return d;
+}
+__host__ __device__ constexpr int ql_of(int q) { return q - qdeg(q) * (qdeg(q) + 1) / 2; }
+__host__ __device__ constexpr int qk_of(int q) { return qdeg(q) - ql_of(q); }
 __host__ __device__ constexpr double factd(int n) { return n <= 1 ? 1.0 : n * factd(n - 1); }
 __host__ __device__ constexpr double binomd(int n, int k) { return factd(n) / (factd(k) * factd(n - k)); }
 __host__ __device__ constexpr double pow2m(int n) { return n <= 0 ? 1.0 : 0.5 * pow2m(n - 1); }  // 2^-n
@@ -83,6 +94,19 @@ struct Parent {
     T V[NV][NQ1];
 };
 
+// Compile-time loop: f(std::integral_constant<int, I>{}) for I = 0 .. N-1, so
+// that every index the body forms is a constant (loops whose bounds depend on
+// an outer index are not reliably unrolled by #pragma unroll, and a run-time
+// index into a register array sends it to local memory).
+template <class F, int... I>
+__device__ __forceinline__ void unroll_seq(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+template <int N, class F>
+__device__ __forceinline__ void unroll(F&& f) {
+    unroll_seq(f, std::make_integer_sequence<int, (N > 0 ? N : 0)>{});
+}
+
 // Cauchy-Kovalewski procedure in 2D (Sec. 3.1; Sec. 4 for systems) in
 // scaled form, U_{k,l,m+1} = -lamx F_{k+1,l,m} - lamy G_{k,l+1,m}, with the
 // Leibniz rule for products and quotients (Dyson / Dumbser-Munz).  Each flux
@@ -93,111 +117,103 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
                                              Parent<SYS, P, T>& out) {
     constexpr int NV = nvars(SYS);
     // quarter averages: mean of xi^k over [0, 1/2] is 1/((k+1) 2^k), (-1)^k that over [-1/2, 0]
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
+    unroll<NV>([&](auto vc) {
+        constexpr int v = vc;
         T ru = 0, rd = 0, lu = 0, ld = 0;
-#pragma unroll
-        for (int k = 0; k <= P; ++k)
-#pragma unroll
-            for (int l = 0; l <= P - k; ++l) {
-                const T d = q[v][qidx(k, l)];
-                const T c = (T)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1));
-                const T cd = c * d;
+        unroll<P + 1>([&](auto kc) {
+            constexpr int k = kc;
+            unroll<P + 1 - k>([&](auto lc) {
+                constexpr int l = lc;
+                const T cd = (T)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1)) * q[v][qidx(k, l)];
                 ru += cd;
                 rd += (T)sgnd(l) * cd;
                 lu += (T)sgnd(k) * cd;
                 ld += (T)(sgnd(k) * sgnd(l)) * cd;
-            }
+            });
+        });
         out.qa[v][0] = ru;
         out.qa[v][1] = rd;
         out.qa[v][2] = lu;
         out.qa[v][3] = ld;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) out.fl[v][s] = 0;
-    }
+        out.fl[v][0] = out.fl[v][1] = out.fl[v][2] = out.fl[v][3] = 0;
+    });
 
     T U[NV][P + 1][P + 1][P + 1];
     T w1[P + 1][P + 1][P + 1], w2[P + 1][P + 1][P + 1], Ep[P + 1][P + 1][P + 1];
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int k = 0; k <= P; ++k)
-#pragma unroll
-            for (int l = 0; l <= P - k; ++l) U[v][k][l][0] = q[v][qidx(k, l)];
+    unroll<NV>([&](auto vc) {
+        unroll<P + 1>([&](auto kc) {
+            unroll<P + 1 - kc>([&](auto lc) { U[vc][kc][lc][0] = q[vc][qidx(kc, lc)]; });
+        });
+    });
 
-#pragma unroll
-    for (int m = 0; m <= P; ++m) {
-        if (m < P) {
-#pragma unroll
-            for (int v = 0; v < NV; ++v)
-#pragma unroll
-                for (int k = 0; k <= P - m - 1; ++k)
-#pragma unroll
-                    for (int l = 0; l <= P - m - 1 - k; ++l) U[v][k][l][m + 1] = 0;
-        }
-#pragma unroll
-        for (int k = 0; k <= P - m; ++k)
-#pragma unroll
-            for (int l = 0; l <= P - m - k; ++l) {
+    unroll<P + 1>([&](auto mc) {
+        constexpr int m = mc;
+        unroll<NV>([&](auto vc) {
+            unroll<P - m>([&](auto kc) {
+                unroll<P - m - kc>([&](auto lc) { U[vc][kc][lc][m + 1] = 0; });
+            });
+        });
+        unroll<P + 1 - m>([&](auto kc) {
+            constexpr int k = kc;
+            unroll<P + 1 - m - k>([&](auto lc) {
+                constexpr int l = lc;
                 T F[NV], G[NV];
                 if constexpr (SYS == ADVECTION) {
                     F[0] = (T)law.ax * U[0][k][l][m];
                     G[0] = (T)law.ay * U[0][k][l][m];
                 } else if constexpr (SYS == BURGERS) {
                     T s = 0;
-#pragma unroll
-                    for (int i = 0; i <= k; ++i)
-#pragma unroll
-                        for (int j = 0; j <= l; ++j)
-#pragma unroll
-                            for (int n = 0; n <= m; ++n)
+                    unroll<k + 1>([&](auto i) {
+                        unroll<l + 1>([&](auto j) {
+                            unroll<m + 1>([&](auto n) {
                                 s += (T)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * U[0][i][j][n] *
                                      U[0][k - i][l - j][m - n];
+                            });
+                        });
+                    });
                     F[0] = (T)0.5 * s;
                     G[0] = F[0];
                 } else {
                     // velocities from rho w = momentum, solved entry by entry
                     T s1 = U[1][k][l][m], s2 = U[2][k][l][m];
-#pragma unroll
-                    for (int i = 0; i <= k; ++i)
-#pragma unroll
-                        for (int j = 0; j <= l; ++j)
-#pragma unroll
-                            for (int n = 0; n <= m; ++n) {
-                                if (i + j + n == 0) continue;
-                                const T c = (T)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * U[0][i][j][n];
-                                s1 -= c * w1[k - i][l - j][m - n];
-                                s2 -= c * w2[k - i][l - j][m - n];
-                            }
+                    unroll<k + 1>([&](auto i) {
+                        unroll<l + 1>([&](auto j) {
+                            unroll<m + 1>([&](auto n) {
+                                if constexpr (i + j + n != 0) {
+                                    const T c = (T)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * U[0][i][j][n];
+                                    s1 -= c * w1[k - i][l - j][m - n];
+                                    s2 -= c * w2[k - i][l - j][m - n];
+                                }
+                            });
+                        });
+                    });
                     const T inv_rho = (T)1 / U[0][0][0][0];
                     w1[k][l][m] = s1 * inv_rho;
                     w2[k][l][m] = s2 * inv_rho;
                     T qxx = 0, qxy = 0, qyy = 0;
-#pragma unroll
-                    for (int i = 0; i <= k; ++i)
-#pragma unroll
-                        for (int j = 0; j <= l; ++j)
-#pragma unroll
-                            for (int n = 0; n <= m; ++n) {
+                    unroll<k + 1>([&](auto i) {
+                        unroll<l + 1>([&](auto j) {
+                            unroll<m + 1>([&](auto n) {
                                 const T c = (T)(binomd(k, i) * binomd(l, j) * binomd(m, n));
                                 const T a1 = c * U[1][i][j][n], a2 = c * U[2][i][j][n];
                                 qxx += a1 * w1[k - i][l - j][m - n];
                                 qxy += a1 * w2[k - i][l - j][m - n];
                                 qyy += a2 * w2[k - i][l - j][m - n];
-                            }
+                            });
+                        });
+                    });
                     const T p = (T)(law.gamma - 1.0) * (U[3][k][l][m] - (T)0.5 * (qxx + qyy));
                     Ep[k][l][m] = U[3][k][l][m] + p;
                     T e1 = 0, e2 = 0;
-#pragma unroll
-                    for (int i = 0; i <= k; ++i)
-#pragma unroll
-                        for (int j = 0; j <= l; ++j)
-#pragma unroll
-                            for (int n = 0; n <= m; ++n) {
+                    unroll<k + 1>([&](auto i) {
+                        unroll<l + 1>([&](auto j) {
+                            unroll<m + 1>([&](auto n) {
                                 const T c = (T)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * Ep[i][j][n];
                                 e1 += c * w1[k - i][l - j][m - n];
                                 e2 += c * w2[k - i][l - j][m - n];
-                            }
+                            });
+                        });
+                    });
                     F[0] = U[1][k][l][m];
                     F[1] = qxx + p;
                     F[2] = qxy;
@@ -207,39 +223,37 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
                     G[2] = qyy + p;
                     G[3] = e2;
                 }
-#pragma unroll
-                for (int v = 0; v < NV; ++v) {
-                    // (k + l >= 1 implies m + 1 <= P; the clamps only keep the
-                    // indices of the branches not taken in range)
-                    if (k >= 1) U[v][k >= 1 ? k - 1 : 0][l][m < P ? m + 1 : P] -= lamx * F[v];
-                    if (l >= 1) U[v][k][l >= 1 ? l - 1 : 0][m < P ? m + 1 : P] -= lamy * G[v];
+                unroll<NV>([&](auto vc) {
+                    constexpr int v = vc;
+                    // (k + l >= 1 implies m + 1 <= P)
+                    if constexpr (k >= 1) U[v][k - 1][l][m + 1] -= lamx * F[v];
+                    if constexpr (l >= 1) U[v][k][l - 1][m + 1] -= lamy * G[v];
                     // Eqs. SubEq:2DFluxFU ... GL: one space direction along the edge, and time
-                    const T ct = (T)(1.0 / factd(m + 1));
-                    if (k == 0) {
-                        const T cs = (T)(pow2m(l) / factd(l + 1)) * ct * F[v];
+                    if constexpr (k == 0) {
+                        const T cs = (T)(pow2m(l) / factd(l + 1) / factd(m + 1)) * F[v];
                         out.fl[v][0] += cs;
                         out.fl[v][1] += (T)sgnd(l) * cs;
                     }
-                    if (l == 0) {
-                        const T cs = (T)(pow2m(k) / factd(k + 1)) * ct * G[v];
+                    if constexpr (l == 0) {
+                        const T cs = (T)(pow2m(k) / factd(k + 1) / factd(m + 1)) * G[v];
                         out.fl[v][2] += cs;
                         out.fl[v][3] += (T)sgnd(k) * cs;
                     }
-                }
-            }
-    }
+                });
+            });
+        });
+    });
     // Eq. SubEq:2DUij
-#pragma unroll
-    for (int v = 0; v < NV; ++v)
-#pragma unroll
-        for (int k = 0; k <= P - 1; ++k)
-#pragma unroll
-            for (int l = 0; l <= P - 1 - k; ++l) {
+    unroll<NV>([&](auto vc) {
+        unroll<P>([&](auto kc) {
+            unroll<P - kc>([&](auto lc) {
+                constexpr int k = kc, l = lc;
                 T s = 0;
-#pragma unroll
-                for (int m = 0; m <= P - k - l; ++m) s += (T)(1.0 / factd(m)) * U[v][k][l][m];
-                out.V[v][qidx(k, l)] = s;
-            }
+                unroll<P + 1 - k - l>([&](auto mc) { s += (T)(1.0 / factd(mc)) * U[vc][k][l][mc]; });
+                out.V[vc][qidx(k, l)] = s;
+            });
+        });
+    });
 }
 
 // ---------------------------------------------------------------- new cell
@@ -248,67 +262,73 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
 // vertex order of Eq. 2DTaylorSeries (1 lower left, 2 lower right, 3 upper
 // right, 4 upper left): the cell average (Eq. 2DIntegral), the derivatives
 // from the highest degree down (Eqs. SubEq:2DUx, SubEq:2DUy, mixed ones as
-// the mean of both), the point value (Eq. SubEq:2DCellAVG).  get(r, field)
-// reads field of parent r.
+// the mean of both), the point value (Eq. SubEq:2DCellAVG).  rd.qa(r, v, s),
+// rd.fl(r, v, s) and rd.V(r, v, q) read the terms of parent r.
 template <int SYS, int P, class T, class Rd>
 __device__ __forceinline__ void linear_cell(const Rd& rd, T lamx, T lamy, T (&D)[nvars(SYS)][nq(P)],
                                             T (&ubar)[nvars(SYS)]) {
     constexpr int NV = nvars(SYS);
-#pragma unroll
-    for (int v = 0; v < NV; ++v) {
+    unroll<NV>([&](auto vc) {
+        constexpr int v = vc;
         const T quarters = rd.qa(0, v, 0) + rd.qa(3, v, 1) + rd.qa(1, v, 2) + rd.qa(2, v, 3);
         const T fx = (rd.fl(0, v, 0) + rd.fl(3, v, 1)) - (rd.fl(1, v, 0) + rd.fl(2, v, 1));
         const T gy = (rd.fl(0, v, 2) + rd.fl(1, v, 3)) - (rd.fl(3, v, 2) + rd.fl(2, v, 3));
         ubar[v] = (T)0.25 * quarters + (T)0.5 * lamx * fx + (T)0.5 * lamy * gy;
-#pragma unroll
-        for (int d = P; d >= 1; --d)
-#pragma unroll
-            for (int b = 0; b <= d; ++b) {
-                const int a = d - b;
+        // degree d = P down to 1; within a degree b = d - a runs 0..d
+        unroll<P>([&](auto dd) {
+            constexpr int d = P - dd;
+            unroll<d + 1>([&](auto bc) {
+                constexpr int b = bc, a = d - b;
                 T sum = 0;
-                if (a >= 1) {
-                    const int k = a - 1, l = b, r = P - k - l;
-                    T s = (T)0.5 * ((rd.V(1, v, qidx(k, l)) + rd.V(2, v, qidx(k, l))) -
-                                    (rd.V(0, v, qidx(k, l)) + rd.V(3, v, qidx(k, l))));
-#pragma unroll
-                    for (int s3 = 3; s3 <= r; ++s3)
+                if constexpr (a >= 1) {  // Eq. SubEq:2DUx with (k, l) = (a - 1, b)
+                    constexpr int k = a - 1, l = b, r = P - k - l;
+                    constexpr int q0 = qidx(k, l);
+                    T s = (T)0.5 * ((rd.V(1, v, q0) + rd.V(2, v, q0)) - (rd.V(0, v, q0) + rd.V(3, v, q0)));
+                    unroll<r - 2>([&](auto s3c) {
+                        constexpr int s3 = s3c + 3;
                         s -= (T)((pow2m(s3) - ipow(-0.5, s3)) / factd(s3)) * D[v][qidx(k + s3, l)];
-#pragma unroll
-                    for (int t = 2; t <= r; ++t)
-#pragma unroll
-                        for (int s1 = 1; s1 <= r - t; ++s1)
-                            if (s1 & 1)
-                                s -= (T)(2.0 * pow2m(s1 + t) / (factd(s1) * factd(t)) * ((t & 1) ? 0.0 : 1.0)) *
-                                     D[v][qidx(k + s1, l + t)];
+                    });
+                    unroll<r - 1>([&](auto tc) {
+                        constexpr int t = tc + 2;
+                        unroll<r - t>([&](auto sc) {
+                            constexpr int s1 = sc + 1;
+                            if constexpr ((s1 & 1) && !(t & 1))
+                                s -= (T)(2.0 * pow2m(s1 + t) / (factd(s1) * factd(t))) * D[v][qidx(k + s1, l + t)];
+                        });
+                    });
                     sum += s;
                 }
-                if (b >= 1) {
-                    const int k = a, l = b - 1, r = P - k - l;
-                    T s = (T)0.5 * ((rd.V(3, v, qidx(k, l)) + rd.V(2, v, qidx(k, l))) -
-                                    (rd.V(0, v, qidx(k, l)) + rd.V(1, v, qidx(k, l))));
-#pragma unroll
-                    for (int t3 = 3; t3 <= r; ++t3)
+                if constexpr (b >= 1) {  // Eq. SubEq:2DUy with (k, l) = (a, b - 1)
+                    constexpr int k = a, l = b - 1, r = P - k - l;
+                    constexpr int q0 = qidx(k, l);
+                    T s = (T)0.5 * ((rd.V(3, v, q0) + rd.V(2, v, q0)) - (rd.V(0, v, q0) + rd.V(1, v, q0)));
+                    unroll<r - 2>([&](auto t3c) {
+                        constexpr int t3 = t3c + 3;
                         s -= (T)((pow2m(t3) - ipow(-0.5, t3)) / factd(t3)) * D[v][qidx(k, l + t3)];
-#pragma unroll
-                    for (int t = 1; t <= r; ++t)
-#pragma unroll
-                        for (int s2 = 2; s2 <= r - t; ++s2)
-                            if ((t & 1) && !(s2 & 1))
+                    });
+                    unroll<r>([&](auto tc) {
+                        constexpr int t = tc + 1;
+                        unroll<r - t - 1>([&](auto sc) {
+                            constexpr int s2 = sc + 2;
+                            if constexpr ((t & 1) && !(s2 & 1))
                                 s -= (T)(2.0 * pow2m(s2 + t) / (factd(s2) * factd(t))) * D[v][qidx(k + s2, l + t)];
+                        });
+                    });
                     sum += s;
                 }
                 D[v][qidx(a, b)] = (a >= 1 && b >= 1) ? (T)0.5 * sum : sum;
-            }
+            });
+        });
         T s = ubar[v];
-#pragma unroll
-        for (int k = 0; k <= P; k += 2)
-#pragma unroll
-            for (int l = 0; l <= P - k; l += 2) {
-                if (k + l == 0) continue;
-                s -= (T)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1)) * D[v][qidx(k, l)];
-            }
+        unroll<P + 1>([&](auto kc) {
+            unroll<P + 1 - kc>([&](auto lc) {
+                constexpr int k = kc, l = lc;
+                if constexpr (k + l > 0 && !(k & 1) && !(l & 1))
+                    s -= (T)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1)) * D[v][qidx(k, l)];
+            });
+        });
         D[v][0] = s;
-    }
+    });
 }
 
 // ----------------------------------------------------------------- limiter
@@ -332,19 +352,16 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
     sy[4] = (vv[3] + vv[2]) - (T)2 * ub;
     T beta[5];
     {
+        // the quadratic form of Eq. 2DSmoothIndicator over pairs q1 <= q2
         T b = 0;
-#pragma unroll
-        for (int a = 0; a <= P; ++a)
-#pragma unroll
-            for (int bb = 0; bb <= P - a; ++bb)
-#pragma unroll
-                for (int a2 = 0; a2 <= P; ++a2)
-#pragma unroll
-                    for (int b2 = 0; b2 <= P - a2; ++b2) {
-                        if (qidx(a2, b2) < qidx(a, bb)) continue;
-                        const double c = beta_coef(P, a, bb, a2, b2) * (qidx(a2, b2) == qidx(a, bb) ? 1.0 : 2.0);
-                        if (c != 0.0) b += (T)c * d[qidx(a, bb)] * d[qidx(a2, b2)];
-                    }
+        unroll<NQ>([&](auto q1) {
+            unroll<NQ>([&](auto q2) {
+                if constexpr (q2 >= q1) {
+                    constexpr double c = beta_coef(P, qk_of(q1), ql_of(q1), qk_of(q2), ql_of(q2)) * (q1 == q2 ? 1.0 : 2.0);
+                    if constexpr (c != 0.0) b += (T)c * d[q1] * d[q2];
+                }
+            });
+        });
         beta[0] = b;
     }
 #pragma unroll
@@ -379,17 +396,16 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
         // Eq. 1DHighOrderWeights in the 2D form of Sec. 3.2: sigma from the
         // four vertex residuals, tau from the degree-P derivatives
         T sigma = 0;
-        const int vsx[4] = {-1, 1, 1, -1}, vsy[4] = {-1, -1, 1, 1};
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
+        unroll<4>([&](auto r) {
+            constexpr int vsx = (r == 1 || r == 2) ? 1 : -1, vsy = (r >= 2) ? 1 : -1;
             T val = 0;
-#pragma unroll
-            for (int a = 0; a <= P; ++a)
-#pragma unroll
-                for (int b = 0; b <= P - a; ++b) val += (T)vertex_coef(a, b, vsx[r], vsy[r]) * d[qidx(a, b)];
+            unroll<NQ>([&](auto qq) {
+                constexpr double c = vertex_coef(qk_of(qq), ql_of(qq), vsx, vsy);
+                val += (T)c * d[qq];
+            });
             const T res = val - vv[r];
             sigma += res * res;
-        }
+        });
         T tau = 0;
 #pragma unroll
         for (int k = 0; k <= P; ++k) tau += d[qidx(k, P - k)] * d[qidx(k, P - k)];
