@@ -60,6 +60,9 @@ def parse():
     ap.add_argument("--sweep-max-log2n", type=int, default=16)
     ap.add_argument("--workloads", action="store_true",
                     help="the paper's 1D workloads (composite wave, Sod, Shu-Osher) instead")
+    ap.add_argument("--two-d", action="store_true",
+                    help="the 2D Euler half-step (isentropic vortex, P = 3) instead")
+    ap.add_argument("--n2d", type=int, default=2048, help="cells per axis of the 2D workload")
     return ap.parse_args()
 
 
@@ -659,8 +662,111 @@ def paper_workloads():
               f"{r['us_per_halfstep']:.2f} | {le} | {ws} | {lo} |")
 
 
+# 2D path (Sec. 3, Sec. 4): the isentropic vortex of Sec. 5.3 on n x n cells,
+# P = 3 (WCCS-4), limiter on, CFL 0.25 (Sec. 5), one bench step = 8 half-steps.
+HALFSTEPS_2D = 8
+CFL_2D = 0.25
+# Algorithmic DRAM bytes per cell-update: the 4 x 10 DOFs read and written
+# once (FP32: 4 B each, FP64: 8 B).
+BYTES_2D_PER_CELL = {"fp32": 2 * 40 * 4, "fp64": 2 * 40 * 8}
+# Arithmetic per cell-update of halfstep2d<EULER, 3>, from ncu's executed
+# FADD/FMUL/FFMA (FP32 kernel) and DADD/DMUL/DFMA (FP64 kernel) thread
+# instructions of one launch at n = 1024 divided by the 1024^2 cells (FMA = 2
+# flops; min/max, compares and conversions not counted; the FP32 kernel's few
+# FP64 instructions, 5 per cell, are left out).
+FLOPS_2D_PER_CELL = {"fp32": (481089204 + 2 * 2261558038 + 276111604) / 1048576.0,
+                     "fp64": (437243905 + 2 * 2366963976 + 336018465) / 1048576.0}
+# DRAM bytes (read + write) of one launch per cell, same captures.  The
+# writes undercount the stored DOFs: part of the output is still in L2 when
+# the kernel ends.
+TRAFFIC_2D_PER_CELL = {"fp32": (178842112 + 120581888) / 1048576.0, "fp64": (359289344 + 295520768) / 1048576.0}
+
+
+def two_d_bench(args):
+    """FP32 and FP64 2D Euler half-steps on the isentropic vortex: cell-updates/s
+    with inputs resident in HBM, the kernel's share of the HBM and arithmetic
+    rooflines, and the CPU oracle on a small sample of the same workload."""
+    import torch
+
+    import oracle
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    n, P = args.n2d, 3
+    pr = inputs.isentropic_vortex(n, P)
+    stream = torch.cuda.Stream()
+    pk, pk_src = peaks()
+    fp32_peak = wcc.measure_fp_peak(wcc.FP32_MIXED)  # the FP32 FMA probe
+    clocks = ClockSampler()
+    clocks.start()
+    results = {}
+    for prec, name, steps in ((wcc.FP32, "fp32", args.steps), (wcc.FP64, "fp64", max(2, min(args.steps, 3)))):
+        with wcc.Solver2D(pr.system, n, n, P, (pr.x_l, pr.x_r, pr.y_l, pr.y_r), pr.bc, precision=prec,
+                          rows_per_cta=16, stream=stream.cuda_stream) as s:
+            s.set_initial(pr.q0)
+            for _ in range(args.warmup):
+                s.step(HALFSTEPS_2D, CFL_2D)
+            s.synchronize()
+            l0 = s.launch_count()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+            with torch.cuda.stream(stream):
+                ev[0].record(stream)
+                for k in range(steps):
+                    s.step(HALFSTEPS_2D, CFL_2D)
+                    ev[k + 1].record(stream)
+            s.synchronize()
+            total_ms = ev[0].elapsed_time(ev[-1])
+            launches = s.launch_count() - l0
+        per_launch_s = total_ms / 1e3 / (steps * HALFSTEPS_2D)
+        cells = n * n
+        r = {"value": cells / per_launch_s, "ms_per_halfstep": per_launch_s * 1e3, "steps": steps,
+             "gpu_launches": launches}
+        gbs = BYTES_2D_PER_CELL[name] * cells / per_launch_s / 1e9
+        r["hbm"] = {"achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"], "frac": gbs / pk["hbm_gbs"],
+                    "bytes_per_cell": BYTES_2D_PER_CELL[name], "traffic": TRAFFIC_2D_PER_CELL[name] * cells}
+        if FLOPS_2D_PER_CELL[name]:
+            tf = FLOPS_2D_PER_CELL[name] * cells / per_launch_s / 1e12
+            peak = fp32_peak if name == "fp32" else FP64_PEAK_TFLOPS
+            r["arith"] = {"achieved_tflops": tf, "peak_tflops": peak, "frac": tf / peak,
+                          "flops_per_cell": FLOPS_2D_PER_CELL[name]}
+        results[name] = r
+    clk = clocks.stop()
+    # CPU oracle on a bounded sample: the same vortex at 64 x 64, FP64, a few half-steps
+    m = 64
+    prs = inputs.isentropic_vortex(m, P)
+    sol = oracle.Solver2D(oracle.make_law2d(oracle.EULER, P), prs.q0, prs.dx, prs.dy)
+    t0 = time.perf_counter()
+    k = 0
+    while time.perf_counter() - t0 < args.cpu_seconds / 4 or k < 2:
+        sol.step_cfl(1, CFL_2D)
+        k += 1
+    cpu_rate = m * m * k / (time.perf_counter() - t0)
+    head = results["fp32"]
+    bound = "hbm" if head["hbm"]["frac"] >= head.get("arith", {"frac": 0})["frac"] else "fp32"
+    line = {
+        "metric": "2D Euler P=3 cell-updates/s (isentropic vortex, WCCS-4)", "value": head["value"],
+        "unit": "cell-updates/s", "n_gpus": 1, "steps": head["steps"], "warmup": args.warmup,
+        "ms_per_step": head["ms_per_halfstep"] * HALFSTEPS_2D, "higher_is_better": True, "dtype": "f32",
+        "data": "synthetic", "config": {"workload": f"2D Euler isentropic vortex {n}x{n}, P=3, limiter on, CFL 0.25, "
+                                                    f"{HALFSTEPS_2D} half-steps per step; state larger than L2"},
+        "roofline": {"bound": bound, "achieved": head["hbm"]["achieved_gbs"], "peak": pk["hbm_gbs"],
+                     "unit": "GB/s", "frac": head["hbm"]["frac"], "traffic": head["hbm"]["traffic"],
+                     "fp32_tflops": head.get("arith", {}).get("achieved_tflops"),
+                     "fp32_frac": head.get("arith", {}).get("frac"), "peak_source": pk_src,
+                     "fp32_peak_tflops": fp32_peak},
+        "variants": results,
+        "cpu_baseline": {"value": cpu_rate, "unit": "cell-updates/s", "cores": oracle.get_threads(), "kind": "oracle",
+                         "sample": f"FP64 oracle, same vortex at {m}x{m}, {k} half-steps"},
+        "clocks": clk,
+        "gpu_launches": head["gpu_launches"],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.two_d:
+        two_d_bench(args)
+        return
     if args.sweep:
         precision_sweep(args.sweep_max_log2n)
         return
