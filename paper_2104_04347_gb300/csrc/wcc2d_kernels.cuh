@@ -66,14 +66,13 @@ struct RingReader {
     __device__ __forceinline__ T get(int r, int f) const {
         return r == 0 ? lo[f * TW + t] : r == 1 ? lo[f * TW + t + 1] : r == 2 ? hi[f * TW + t + 1] : hi[f * TW + t];
     }
-    __device__ __forceinline__ T qa(int r, int v, int s) const { return get(r, v * 4 + s); }
-    __device__ __forceinline__ T fl(int r, int v, int s) const { return get(r, NV * 4 + v * 4 + s); }
-    __device__ __forceinline__ T V(int r, int v, int q) const { return get(r, NV * 8 + v * NQ1 + q); }
+    __device__ __forceinline__ T c(int r, int v) const { return get(r, v * 4 + r); }
+    __device__ __forceinline__ T V(int r, int v, int q) const { return get(r, NV * 4 + v * NQ1 + q); }
 };
 
 template <int SYS, int P>
 __host__ __device__ constexpr int record_fields() {
-    return nvars(SYS) * (8 + nq(P - 1));
+    return nvars(SYS) * (4 + nq(P - 1));
 }
 
 template <class T, int TW>
@@ -129,8 +128,16 @@ __device__ __forceinline__ void finish2d(T rate, unsigned err, double dt, const 
     }
 }
 
+// Resident CTAs the FP32 kernels are compiled for (caps their registers at
+// 65536 / (4 x TW)); FP64 kernels are bound by the FP64 pipe and keep their
+// registers.
+template <class T>
+constexpr int min_ctas2d() {
+    return sizeof(T) == 4 ? 4 : 1;
+}
+
 template <int SYS, int P, class T, int TW>
-__global__ void __launch_bounds__(TW) halfstep2d(const Step2D a) {
+__global__ void __launch_bounds__(TW, min_ctas2d<T>()) halfstep2d(const Step2D a) {
     constexpr int NV = nvars(SYS), NQ = nq(P), NQ1 = nq(P - 1);
     constexpr int NF = record_fields<SYS, P>();
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -175,19 +182,16 @@ __global__ void __launch_bounds__(TW) halfstep2d(const Step2D a) {
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    r[(v * 4 + k) * TW + t] = par.qa[v][k];
-                    r[(NV * 4 + v * 4 + k) * TW + t] = par.fl[v][k];
-                }
+                for (int k = 0; k < 4; ++k) r[(v * 4 + k) * TW + t] = par.c[v][k];
 #pragma unroll
-                for (int qq = 0; qq < NQ1; ++qq) r[(NV * 8 + v * NQ1 + qq) * TW + t] = par.V[v][qq];
+                for (int qq = 0; qq < NQ1; ++qq) r[(NV * 4 + v * NQ1 + qq) * TW + t] = par.V[v][qq];
             }
         }
         __syncthreads();
         if (s >= 1 && t < TW - 1 && i0 + t < a.nx_new) {
             const RingReader<T, TW, NV, NQ1> rd{ring + ((s - 1) & 1) * NF * TW, ring + (s & 1) * NF * TW, t};
             T D[NV][NQ], ub[NV];
-            linear_cell<SYS, P, T>(rd, lamx, lamy, D, ub);
+            linear_cell<SYS, P, T>(rd, D, ub);
             if (a.law.limiter) {
                 if constexpr (SYS == EULER) {
                     T vv[4][4];

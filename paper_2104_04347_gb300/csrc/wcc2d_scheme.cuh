@@ -77,20 +77,22 @@ __device__ __forceinline__ T weight_pow(T x, T alpha) {
 
 // ------------------------------------------------------------------ parent
 
-// What an old cell contributes to the new cells it touches (Appendix B,
-// Eq. SubEq:2DUij), per variable v:
-//   qa[v][0..3]: quarter averages RU, RD, LU, LD at t^n;
-//   fl[v][0..3]: time-averaged edge fluxes f_U, f_D (line x = x_i) and
-//                g_R, g_L (line y = y_j) over [t^n, t^{n+1/2}];
-//   V[v][q]:     scaled derivatives at the centre at t^{n+1/2}, k + l <= P - 1
-//                (the entries Eqs. SubEq:2DUx, SubEq:2DUy read; q = 0 is the
-//                vertex value of the limiter).
+// What an old cell contributes to the four new cells it touches, per
+// variable v:
+//   c[v][r]: its share of the cell average of Eq. 2DIntegral in the new cell
+//            of which it is vertex r (0: lower left, 1: lower right, 2: upper
+//            right, 3: upper left), i.e. a quarter of the quarter average
+//            (Eqs. SubEq:2DCellAVGRU ... LD) plus lamx/2 and lamy/2 times its
+//            time-averaged edge fluxes (Eqs. SubEq:2DFluxFU ... GL) with the
+//            signs of Eq. 2DIntegral;
+//   V[v][q]: scaled derivatives at the centre at t^{n+1/2}, k + l <= P - 1
+//            (the entries Eqs. SubEq:2DUx, SubEq:2DUy read; q = 0 is the
+//            vertex value of the limiter), Eq. SubEq:2DUij.
 template <int SYS, int P, class T>
 struct Parent {
     static constexpr int NV = nvars(SYS);
     static constexpr int NQ1 = nq(P - 1);
-    T qa[NV][4];
-    T fl[NV][4];
+    T c[NV][4];
     T V[NV][NQ1];
 };
 
@@ -116,7 +118,10 @@ template <int SYS, int P, class T>
 __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T lamx, T lamy, const Law2D& law,
                                              Parent<SYS, P, T>& out) {
     constexpr int NV = nvars(SYS);
-    // quarter averages: mean of xi^k over [0, 1/2] is 1/((k+1) 2^k), (-1)^k that over [-1/2, 0]
+    // qa[v]: quarter averages RU, RD, LU, LD at t^n (mean of xi^k over [0, 1/2]
+    // is 1/((k+1) 2^k), (-1)^k that over [-1/2, 0]); fl[v]: f_U, f_D on the
+    // line x = x_i and g_R, g_L on the line y = y_j, averaged over the half step
+    T qa[NV][4], fl[NV][4];
     unroll<NV>([&](auto vc) {
         constexpr int v = vc;
         T ru = 0, rd = 0, lu = 0, ld = 0;
@@ -131,11 +136,11 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
                 ld += (T)(sgnd(k) * sgnd(l)) * cd;
             });
         });
-        out.qa[v][0] = ru;
-        out.qa[v][1] = rd;
-        out.qa[v][2] = lu;
-        out.qa[v][3] = ld;
-        out.fl[v][0] = out.fl[v][1] = out.fl[v][2] = out.fl[v][3] = 0;
+        qa[v][0] = ru;
+        qa[v][1] = rd;
+        qa[v][2] = lu;
+        qa[v][3] = ld;
+        fl[v][0] = fl[v][1] = fl[v][2] = fl[v][3] = 0;
     });
 
     T U[NV][P + 1][P + 1][P + 1];
@@ -231,17 +236,27 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
                     // Eqs. SubEq:2DFluxFU ... GL: one space direction along the edge, and time
                     if constexpr (k == 0) {
                         const T cs = (T)(pow2m(l) / factd(l + 1) / factd(m + 1)) * F[v];
-                        out.fl[v][0] += cs;
-                        out.fl[v][1] += (T)sgnd(l) * cs;
+                        fl[v][0] += cs;
+                        fl[v][1] += (T)sgnd(l) * cs;
                     }
                     if constexpr (l == 0) {
                         const T cs = (T)(pow2m(k) / factd(k + 1) / factd(m + 1)) * G[v];
-                        out.fl[v][2] += cs;
-                        out.fl[v][3] += (T)sgnd(k) * cs;
+                        fl[v][2] += cs;
+                        fl[v][3] += (T)sgnd(k) * cs;
                     }
                 });
             });
         });
+    });
+    // shares of the new cell averages (Eq. 2DIntegral): as vertex 1 the parent
+    // gives RU, +f_U, +g_R; as 2: LU, -f_U, +g_L; as 3: LD, -f_D, -g_L; as 4: RD, +f_D, -g_R
+    unroll<NV>([&](auto vc) {
+        constexpr int v = vc;
+        const T hx = (T)0.5 * lamx, hy = (T)0.5 * lamy;
+        out.c[v][0] = (T)0.25 * qa[v][0] + hx * fl[v][0] + hy * fl[v][2];
+        out.c[v][1] = (T)0.25 * qa[v][2] - hx * fl[v][0] + hy * fl[v][3];
+        out.c[v][2] = (T)0.25 * qa[v][3] - hx * fl[v][1] - hy * fl[v][3];
+        out.c[v][3] = (T)0.25 * qa[v][1] + hx * fl[v][1] - hy * fl[v][2];
     });
     // Eq. SubEq:2DUij
     unroll<NV>([&](auto vc) {
@@ -262,18 +277,14 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
 // vertex order of Eq. 2DTaylorSeries (1 lower left, 2 lower right, 3 upper
 // right, 4 upper left): the cell average (Eq. 2DIntegral), the derivatives
 // from the highest degree down (Eqs. SubEq:2DUx, SubEq:2DUy, mixed ones as
-// the mean of both), the point value (Eq. SubEq:2DCellAVG).  rd.qa(r, v, s),
-// rd.fl(r, v, s) and rd.V(r, v, q) read the terms of parent r.
+// the mean of both), the point value (Eq. SubEq:2DCellAVG).  rd.c(r, v) and
+// rd.V(r, v, q) read the terms of parent r (struct Parent).
 template <int SYS, int P, class T, class Rd>
-__device__ __forceinline__ void linear_cell(const Rd& rd, T lamx, T lamy, T (&D)[nvars(SYS)][nq(P)],
-                                            T (&ubar)[nvars(SYS)]) {
+__device__ __forceinline__ void linear_cell(const Rd& rd, T (&D)[nvars(SYS)][nq(P)], T (&ubar)[nvars(SYS)]) {
     constexpr int NV = nvars(SYS);
     unroll<NV>([&](auto vc) {
         constexpr int v = vc;
-        const T quarters = rd.qa(0, v, 0) + rd.qa(3, v, 1) + rd.qa(1, v, 2) + rd.qa(2, v, 3);
-        const T fx = (rd.fl(0, v, 0) + rd.fl(3, v, 1)) - (rd.fl(1, v, 0) + rd.fl(2, v, 1));
-        const T gy = (rd.fl(0, v, 2) + rd.fl(1, v, 3)) - (rd.fl(3, v, 2) + rd.fl(2, v, 3));
-        ubar[v] = (T)0.25 * quarters + (T)0.5 * lamx * fx + (T)0.5 * lamy * gy;
+        ubar[v] = (rd.c(0, v) + rd.c(1, v)) + (rd.c(2, v) + rd.c(3, v));
         // degree d = P down to 1; within a degree b = d - a runs 0..d
         unroll<P>([&](auto dd) {
             constexpr int d = P - dd;
