@@ -676,10 +676,10 @@ BYTES_2D_PER_CELL = {"fp32": 2 * 40 * 4, "fp64": 2 * 40 * 8}
 # FP64 instructions, 5 per cell, are left out).
 FLOPS_2D_PER_CELL = {"fp32": (481089204 + 2 * 2261558038 + 276111604) / 1048576.0,
                      "fp64": (437243905 + 2 * 2366963976 + 336018465) / 1048576.0}
-# DRAM bytes (read + write) of one launch per cell, same captures.  The
-# writes undercount the stored DOFs: part of the output is still in L2 when
-# the kernel ends.
-TRAFFIC_2D_PER_CELL = {"fp32": (178842112 + 120581888) / 1048576.0, "fp64": (359289344 + 295520768) / 1048576.0}
+# DRAM bytes (read + write) of one launch per cell from an ncu capture of the
+# current kernels, or None until one is taken (the counters of an earlier
+# layout no longer apply).
+TRAFFIC_2D_PER_CELL = {"fp32": None, "fp64": None}
 
 
 def two_d_bench(args):
@@ -722,7 +722,8 @@ def two_d_bench(args):
              "gpu_launches": launches}
         gbs = BYTES_2D_PER_CELL[name] * cells / per_launch_s / 1e9
         r["hbm"] = {"achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"], "frac": gbs / pk["hbm_gbs"],
-                    "bytes_per_cell": BYTES_2D_PER_CELL[name], "traffic": TRAFFIC_2D_PER_CELL[name] * cells}
+                    "bytes_per_cell": BYTES_2D_PER_CELL[name],
+                    "traffic": TRAFFIC_2D_PER_CELL[name] * cells if TRAFFIC_2D_PER_CELL[name] else None}
         if FLOPS_2D_PER_CELL[name]:
             tf = FLOPS_2D_PER_CELL[name] * cells / per_launch_s / 1e12
             peak = fp32_peak if name == "fp32" else FP64_PEAK_TFLOPS
