@@ -670,16 +670,17 @@ CFL_2D = 0.25
 # once (FP32: 4 B each, FP64: 8 B).
 BYTES_2D_PER_CELL = {"fp32": 2 * 40 * 4, "fp64": 2 * 40 * 8}
 # Arithmetic per cell-update of halfstep2d<EULER, 3>, from ncu's executed
-# FADD/FMUL/FFMA (FP32 kernel) and DADD/DMUL/DFMA (FP64 kernel) thread
-# instructions of one launch at n = 1024 divided by the 1024^2 cells (FMA = 2
-# flops; min/max, compares and conversions not counted; the FP32 kernel's few
-# FP64 instructions, 5 per cell, are left out).
-FLOPS_2D_PER_CELL = {"fp32": (481089204 + 2 * 2261558038 + 276111604) / 1048576.0,
-                     "fp64": (437243905 + 2 * 2366963976 + 336018465) / 1048576.0}
-# DRAM bytes (read + write) of one launch per cell from an ncu capture of the
-# current kernels, or None until one is taken (the counters of an earlier
-# layout no longer apply).
-TRAFFIC_2D_PER_CELL = {"fp32": None, "fp64": None}
+# FADD/FMUL/FFMA (FP32 kernel, 128-thread strips) and DADD/DMUL/DFMA (FP64
+# kernel, 64-thread strips) thread instructions of one launch at n = 1024
+# divided by the 1024^2 cells (FMA = 2 flops; min/max, compares and
+# conversions not counted; the FP32 kernel's few FP64 instructions, 6 per
+# cell, are left out).
+FLOPS_2D_PER_CELL = {"fp32": (467432989 + 2 * 2406384696 + 288406782) / 1048576.0,
+                     "fp64": (412078081 + 2 * 2396458776 + 341564899) / 1048576.0}
+# DRAM bytes (read + write) of one launch per cell, same captures; scaled by
+# cells to the bench size.  The writes undercount the stored DOFs: part of
+# the output is still in L2 when the kernel ends.
+TRAFFIC_2D_PER_CELL = {"fp32": (179895552 + 122344448) / 1048576.0, "fp64": (358728448 + 294830336) / 1048576.0}
 
 
 def two_d_bench(args):
