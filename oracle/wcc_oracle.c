@@ -35,7 +35,7 @@
 #include <omp.h>
 #endif
 
-#define OR_MAXP 4
+#define OR_MAXP 6
 #define OR_MAXV 3
 #define OR_NK (OR_MAXP + 1)
 
