@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--two-d", action="store_true",
                     help="the 2D Euler half-step (isentropic vortex, P = 3) instead")
     ap.add_argument("--n2d", type=int, default=2048, help="cells per axis of the 2D workload")
+    ap.add_argument("--high-order", action="store_true",
+                    help="FP64 Euler half-steps at P = 3..6 (seeded Riemann data) instead")
     return ap.parse_args()
 
 
@@ -764,8 +766,70 @@ def two_d_bench(args):
     print(json.dumps(line), flush=True)
 
 
+# Degrees above the paper's tables: CFL 0.8 of the von Neumann limit of the
+# linear scheme (0.2116 at P = 5, 0.1851 at P = 6; Sec. 2.3), the bench's 0.2
+# below that.
+CFL_HIGH = {3: 0.2, 4: 0.2, 5: 0.16, 6: 0.14}
+# FP64 flops per cell-update of halfstep_fp64<EULER, P> (ncu DADD + DMUL +
+# 2 DFMA thread instructions of one launch over the launch's cells); P = 3 is
+# FP64_FLOPS_PER_CELL_UPDATE, P = 4..6 from one launch each at N = 2^20
+# (e.g. P = 6: (132561538 + 271580931 + 2 x 1108567950) / 1048576.5).
+FP64_FLOPS_HIGH = {3: None,
+                   4: (101969794 + 187162371 + 2 * 522598030) / 1048576.5,
+                   5: (120968962 + 232542339 + 2 * 766449806) / 1048576.5,
+                   6: (132561538 + 271580931 + 2 * 1108567950) / 1048576.5}
+
+
+def high_order_bench(args):
+    """FP64 Euler half-steps at P = 3..6 on the bench's seeded Riemann data:
+    cell-updates/s (CUDA events, graphs of 32 half-steps, inputs resident)
+    and the share of the FP64 peak where the flop count is known."""
+    import torch
+
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    FP64_FLOPS_HIGH[3] = FP64_FLOPS_PER_CELL_UPDATE
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler()
+    clocks.start()
+    rows = []
+    for P in (3, 4, 5, 6):
+        pr = inputs.euler_riemann_seeded(1 << args.log2n, P)
+        with wcc.Solver(pr.system, pr.N, P, (pr.x_l, pr.x_r), pr.bc, precision=wcc.FP64,
+                        stream=stream.cuda_stream) as s:
+            s.set_initial(pr.q0)
+            for _ in range(args.warmup):
+                s.step(HALFSTEPS_PER_STEP, CFL_HIGH[P])
+            s.synchronize()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+            with torch.cuda.stream(stream):
+                ev[0].record(stream)
+                for k in range(args.steps):
+                    s.step(HALFSTEPS_PER_STEP, CFL_HIGH[P])
+                    ev[k + 1].record(stream)
+            s.synchronize()
+            ms = ev[0].elapsed_time(ev[-1]) / (args.steps * HALFSTEPS_PER_STEP)
+            cells = s.num_cells()
+        row = {"P": P, "N": pr.N, "cfl": CFL_HIGH[P], "ms_per_halfstep": ms, "cell_updates_per_s": cells / (ms / 1e3)}
+        if FP64_FLOPS_HIGH[P]:
+            tf = FP64_FLOPS_HIGH[P] * cells / (ms / 1e3) / 1e12
+            row.update({"fp64_flops_per_cell": FP64_FLOPS_HIGH[P], "fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS})
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"clocks": clocks.stop()}), flush=True)
+    print("| P | CFL | ms / half-step | cell-updates/s | FP64 flops / cell | of the FP64 peak |")
+    print("|---|---|---|---|---|---|")
+    for r in rows:
+        fl = "" if "fp64_flops_per_cell" not in r else f"{r['fp64_flops_per_cell']:.0f}"
+        fr = "" if "fp64_frac" not in r else f"{r['fp64_frac']:.3f}"
+        print(f"| {r['P']} | {r['cfl']} | {r['ms_per_halfstep']:.3f} | {r['cell_updates_per_s'] / 1e9:.3f} G | {fl} | {fr} |")
+
+
 def main():
     args = parse()
+    if args.high_order:
+        high_order_bench(args)
+        return
     if args.two_d:
         two_d_bench(args)
         return

@@ -93,7 +93,11 @@ typedef struct wcc_ctx* wcc_handle;
 void wcc_default_options(wcc_options* opt);
 
 /* Create a solver for `system` on [domain[0], domain[1]] with N cells of
- * width dx and polynomial degree P (1 <= P <= 4; order P+1, Sec. 2.1).
+ * width dx and polynomial degree P (order P+1, Sec. 2.1): 1 <= P <= 6 with
+ * WCC_FP64, 1 <= P <= 4 with WCC_FP32_MIXED and WCC_FP32 (WCC_E_INVAL
+ * otherwise).  The paper prints CFL numbers up to P = 3; the von Neumann
+ * limits of the linear scheme (Sec. 2.3) are 0.282, 0.212 and 0.185 at
+ * P = 4, 5, 6, and the CFL number must stay below them.
  * N >= 4; bc is WCC_BC_PERIODIC or WCC_BC_TRANSMISSIVE.  opt may be NULL.
  * On success *out holds the handle (free with wcc_destroy). */
 int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domain[2], int bc,

@@ -29,21 +29,20 @@ thread_local std::string g_create_error;
 // kConvCells cells through shared memory: the host-layout side of the tile is
 // one contiguous run of doubles and the plane side one run per plane, so both
 // global sides are coalesced.
-// 1/k! and 1/((k+1) 2^k) for k = 0..4, rounded once to double (the layout
-// conversions multiply by these instead of dividing: FP64 division is slow on
-// this GPU).
+// 1/k! and k! for k = 0..6, rounded once to double (the layout conversions
+// multiply by these instead of dividing: FP64 division is slow on this GPU).
 __device__ __forceinline__ double inv_fact_k(int k) {
-    const double t[5] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0};
+    const double t[7] = {1.0, 1.0, 0.5, 1.0 / 6.0, 1.0 / 24.0, 1.0 / 120.0, 1.0 / 720.0};
     return t[k];
 }
 __device__ __forceinline__ double fact_k(int k) {
-    const double t[5] = {1.0, 1.0, 2.0, 6.0, 24.0};
+    const double t[7] = {1.0, 1.0, 2.0, 6.0, 24.0, 120.0, 720.0};
     return t[k];
 }
 
 constexpr int kConvCells = 128;                 // cells per tile
 constexpr int kConvThreads = 256;
-constexpr int kConvMaxElems = kConvCells * 3 * 5;  // nv <= 3, K <= 5
+constexpr int kConvMaxElems = kConvCells * 3 * 7;  // nv <= 3, K <= 7
 
 // Copies cells [c0, c0 + m) of the host-layout array to / from smem (as
 // doubles, or as their bit patterns for the FP32-mixed conversions).
@@ -353,7 +352,7 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     if (!out) return fail(nullptr, WCC_E_INVAL, "out is NULL");
     *out = nullptr;
     if (system < WCC_ADVECTION || system > WCC_EULER) return fail(nullptr, WCC_E_INVAL, "unknown system");
-    if (P < 1 || P > 4) return fail(nullptr, WCC_E_INVAL, "P must be in 1..4");
+    if (P < 1 || P > 6) return fail(nullptr, WCC_E_INVAL, "P must be in 1..6");
     if (N < 4 || N > (1ll << 31)) return fail(nullptr, WCC_E_INVAL, "N must be in 4..2^31");
     if (!domain || !(domain[1] > domain[0])) return fail(nullptr, WCC_E_INVAL, "domain must satisfy x_L < x_R");
     if (bc != WCC_BC_PERIODIC && bc != WCC_BC_TRANSMISSIVE) return fail(nullptr, WCC_E_INVAL, "unknown bc");
@@ -362,6 +361,7 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     if (opt) o = *opt;
     if (o.precision != WCC_FP64 && o.precision != WCC_FP32_MIXED && o.precision != WCC_FP32)
         return fail(nullptr, WCC_E_INVAL, "precision must be WCC_FP64, WCC_FP32_MIXED or WCC_FP32");
+    if (o.precision != WCC_FP64 && P > 4) return fail(nullptr, WCC_E_INVAL, "P > 4 needs WCC_FP64");
     if (!(o.eps >= 0.0) || !(o.alpha > 0.0) || !(o.gamma > 1.0))
         return fail(nullptr, WCC_E_INVAL, "need eps >= 0, alpha > 0, gamma > 1");
     if (o.graph_chunk < 0) return fail(nullptr, WCC_E_INVAL, "graph_chunk must be >= 0");

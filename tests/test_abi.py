@@ -40,7 +40,7 @@ def test_default_options():
 @pytest.mark.parametrize("args,needle", [
     ((7, 64, 2, (0.0, 1.0), 0), "system"),
     ((0, 64, 0, (0.0, 1.0), 0), "P must"),
-    ((0, 64, 5, (0.0, 1.0), 0), "P must"),
+    ((0, 64, 7, (0.0, 1.0), 0), "P must"),
     ((0, 2, 2, (0.0, 1.0), 0), "N must"),
     ((0, 64, 2, (1.0, 0.0), 0), "domain"),
     ((0, 64, 2, (0.0, 1.0), 9), "bc"),
@@ -51,8 +51,34 @@ def test_create_rejects_bad_arguments(args, needle):
     assert ei.value.code == -1 and needle in str(ei.value)
 
 
+@pytest.mark.parametrize("precision", [wcc.FP32_MIXED, wcc.FP32])
+def test_p_above_4_needs_fp64(precision):
+    with pytest.raises(wcc.WCCError) as ei:
+        wcc.Solver(2, 64, 5, (0.0, 1.0), 1, precision=precision)
+    assert ei.value.code == -1 and "needs WCC_FP64" in str(ei.value)
+
+
+@pytest.mark.parametrize("args,kw,code,needle", [
+    ((7, 64, 64, 2, (0.0, 1.0, 0.0, 1.0), 0), {}, -1, "system"),
+    ((2, 64, 64, 4, (0.0, 1.0, 0.0, 1.0), 0), {}, -1, "P must"),
+    ((2, 3, 64, 2, (0.0, 1.0, 0.0, 1.0), 0), {}, -1, "nx and ny"),
+    ((2, 64, 1 << 16, 2, (0.0, 1.0, 0.0, 1.0), 0), {}, -7, "2^15"),
+    ((2, 64, 64, 2, (0.0, 1.0, 1.0, 0.0), 0), {}, -1, "domain"),
+    ((2, 64, 64, 2, (0.0, 1.0, 0.0, 1.0), 5), {}, -1, "bc"),
+    ((2, 64, 64, 2, (0.0, 1.0, 0.0, 1.0), 0), {"precision": wcc.FP32_MIXED}, -1, "precision"),
+    ((2, 64, 64, 2, (0.0, 1.0, 0.0, 1.0), 0), {"rows_per_cta": 0}, -1, "options"),
+])
+def test_create2d_rejects_bad_arguments(args, kw, code, needle):
+    with pytest.raises(wcc.WCCError) as ei:
+        wcc.Solver2D(*args, **kw)
+    assert ei.value.code == code and needle in str(ei.value)
+
+
 def test_null_handle_calls_fail_cleanly():
     lib = wcc.load()
     assert lib.wcc_step(None, 1, 0.3) == -1
     assert lib.wcc_synchronize(None) == -1
     lib.wcc_destroy(None)
+    assert lib.wcc2d_step(None, 1, 0.3) == -1
+    assert lib.wcc2d_synchronize(None) == -1
+    assert lib.wcc2d_destroy(None) == 0
