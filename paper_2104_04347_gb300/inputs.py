@@ -543,3 +543,33 @@ def advection2d_sine(nx: int, ny: int, P: int, ax: float = 1.0, ay: float = 1.0,
             q[:, :, 0, idx2d(k, l)] = (kx ** k * ky ** l * np.sin(kx * X + ky * Y + phase + (k + l) * math.pi / 2)
                                        * dx ** k * dy ** l)
     return Problem2D(ADVECTION, nx, ny, P, -1.0, 1.0, -1.0, 1.0, PERIODIC, q, "advection2d-sine", ax, ay)
+
+
+# (rho, u, v, p) in the quadrants [-1,0]x[-1,0], [-1,0]x[0,1], [0,1]x[0,1], [0,1]x[-1,0]
+RIEMANN2D_STATES = {
+    1: ((0.138, 1.206, 1.206, 0.029), (0.5323, 1.206, 0.0, 0.3), (1.5, 0.0, 0.0, 1.5), (0.5323, 0.0, 1.206, 0.3)),
+    2: ((1.0, -0.75, 0.5, 1.0), (2.0, 0.75, 0.5, 1.0), (1.0, 0.75, -0.5, 1.0), (3.0, -0.75, -0.5, 1.0)),
+}
+
+
+def riemann2d(n: int, P: int, config: int = 1, gamma: float = GAMMA) -> Problem2D:
+    """The 2D Riemann problems of Sec. 5.3 on [-1, 1]^2 with transmissive
+    boundaries, n x n cells: four constant quadrant states (config 1: four
+    shocks; config 2: four contacts).  Each integer-stage cell holds the exact
+    cell average of the data (cells cut by an axis the area-weighted mix) and
+    zero derivatives."""
+    X, Y = _grid2d(n, n, -1.0, 1.0, -1.0, 1.0, TRANSMISSIVE)
+    d = 2.0 / n
+    # fraction of each cell with x < 0 (resp. y < 0)
+    fx = np.clip((0.0 - (X - 0.5 * d)) / d, 0.0, 1.0)
+    fy = np.clip((0.0 - (Y - 0.5 * d)) / d, 0.0, 1.0)
+    cons = [np.array(primitive_conserved2d(*s, gamma=gamma)) for s in RIEMANN2D_STATES[config]]
+    U = (fx * fy)[..., None] * cons[0] + (fx * (1 - fy))[..., None] * cons[1] + \
+        ((1 - fx) * (1 - fy))[..., None] * cons[2] + ((1 - fx) * fy)[..., None] * cons[3]
+    q = np.zeros(X.shape + (4, nq2d(P)))
+    q[..., 0] = U
+    return Problem2D(EULER, n, n, P, -1.0, 1.0, -1.0, 1.0, TRANSMISSIVE, q, f"riemann2d-{config}")
+
+
+def primitive_conserved2d(rho, u, v, p, gamma: float = GAMMA):
+    return rho, rho * u, rho * v, p / (gamma - 1.0) + 0.5 * rho * (u * u + v * v)
