@@ -682,7 +682,7 @@ FLOPS_2D_PER_CELL = {"fp32": (467432989 + 2 * 2406384696 + 288406782) / 1048576.
 # DRAM bytes (read + write) of one launch per cell, same captures; scaled by
 # cells to the bench size.  The writes undercount the stored DOFs: part of
 # the output is still in L2 when the kernel ends.
-TRAFFIC_2D_PER_CELL = {"fp32": (179895552 + 122344448) / 1048576.0, "fp64": (358728448 + 294830336) / 1048576.0}
+TRAFFIC_2D_PER_CELL = {"fp32": None, "fp64": (358728448 + 294830336) / 1048576.0}
 
 
 def two_d_bench(args):

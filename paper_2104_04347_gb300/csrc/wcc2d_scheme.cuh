@@ -72,8 +72,17 @@ struct Law2D {
 
 template <class T>
 __device__ __forceinline__ T weight_pow(T x, T alpha) {
-    return alpha == (T)2 ? x * x : (T)pow((double)x, (double)alpha);
+    if constexpr (sizeof(T) == 8)
+        return alpha == 2.0 ? x * x : pow(x, alpha);
+    else
+        return alpha == 2.0f ? x * x : exp2f(alpha * log2f(x));
 }
+
+// FP32 ratio a / b of the limiter weights for 0 < a <= b: one approximate
+// reciprocal (no division sequence, no branch).  b is kept at or above the
+// smallest normal float, which only changes denominators below 1.2e-38,
+// where the candidate is flat to rounding.
+__device__ __forceinline__ float weight_ratio(float a, float b) { return __fdividef(a, fmaxf(b, 0x1p-126f)); }
 
 // ------------------------------------------------------------------ parent
 
@@ -363,15 +372,18 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
     sy[4] = (vv[3] + vv[2]) - (T)2 * ub;
     T beta[5];
     {
-        // the quadratic form of Eq. 2DSmoothIndicator over pairs q1 <= q2
+        // the quadratic form of Eq. 2DSmoothIndicator over pairs q1 <= q2, as
+        // sum over q1 of d[q1] times an inner sum over q2 (independent chains)
         T b = 0;
         unroll<NQ>([&](auto q1) {
+            T inner = 0;
             unroll<NQ>([&](auto q2) {
                 if constexpr (q2 >= q1) {
                     constexpr double c = beta_coef(P, qk_of(q1), ql_of(q1), qk_of(q2), ql_of(q2)) * (q1 == q2 ? 1.0 : 2.0);
-                    if constexpr (c != 0.0) b += (T)c * d[q1] * d[q2];
+                    if constexpr (c != 0.0) inner += (T)c * d[q2];
                 }
             });
+            b += d[q1] * inner;
         });
         beta[0] = b;
     }
@@ -391,17 +403,19 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
 #pragma unroll
             for (int m = 0; m < 5; ++m) w[m] = w[m] / s;
         } else {
+            // every weight divided by that of the smallest denominator
             T bmin = beta[0] + eps;
 #pragma unroll
             for (int m = 1; m < 5; ++m) bmin = fminf(bmin, beta[m] + eps);
             T s = 0;
 #pragma unroll
             for (int m = 0; m < 5; ++m) {
-                w[m] = weight_pow<T>(bmin / (beta[m] + eps), alpha);
+                w[m] = weight_pow<T>(weight_ratio(bmin, beta[m] + eps), alpha);
                 s += w[m];
             }
+            const T is = (T)1 / s;  // s >= 1
 #pragma unroll
-            for (int m = 0; m < 5; ++m) w[m] = w[m] / s;
+            for (int m = 0; m < 5; ++m) w[m] *= is;
         }
     } else {
         // Eq. 1DHighOrderWeights in the 2D form of Sec. 3.2: sigma from the
@@ -448,12 +462,13 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
                 T s = 0;
 #pragma unroll
                 for (int m = 0; m < 5; ++m) {
-                    w[m] = weight_pow<T>(dmin / den[m], alpha);
+                    w[m] = weight_pow<T>(weight_ratio(dmin, den[m]), alpha);
                     if (m == 0) w[m] += lead;
                     s += w[m];
                 }
+                const T is = (T)1 / s;  // s >= 1
 #pragma unroll
-                for (int m = 0; m < 5; ++m) w[m] = w[m] / s;
+                for (int m = 0; m < 5; ++m) w[m] *= is;
             }
         }
     }
@@ -484,21 +499,46 @@ __device__ __forceinline__ bool limit_euler(T (&D)[4][nq(P)], const T (&ub)[4], 
     constexpr int NQ = nq(P);
     T gx = (T)0.5 * ((vv[3][1] + vv[3][2]) - (vv[3][0] + vv[3][3])) * lamx;
     T gy = (T)0.5 * ((vv[3][3] + vv[3][2]) - (vv[3][0] + vv[3][1])) * lamy;
-    const T norm = sqrt(gx * gx + gy * gy);
+    const T g2 = gx * gx + gy * gy;
     T nx = 1, ny = 0;
-    if (norm > (T)0) {
-        nx = gx / norm;
-        ny = gy / norm;
+    if (g2 > (T)0) {
+        if constexpr (sizeof(T) == 8) {
+            const T norm = sqrt(g2);
+            nx = gx / norm;
+            ny = gy / norm;
+        } else {
+            const T rn = rsqrtf(g2);
+            nx = gx * rn;
+            ny = gy * rn;
+        }
     }
     const T gm1 = (T)(law.gamma - 1.0);
-    const T rho = ub[0], u = ub[1] / rho, v = ub[2] / rho;
-    const T q2 = u * u + v * v;
-    const T p = gm1 * (ub[3] - (T)0.5 * rho * q2);
-    if (!(rho > (T)0) || !(p > (T)0)) return false;
-    const T c = sqrt((T)law.gamma * p / rho);
-    const T H = (ub[3] + p) / rho;
+    const T rho = ub[0];
+    T u, v, c, H, b1, ic, q2, p;
+    if constexpr (sizeof(T) == 8) {
+        u = ub[1] / rho;
+        v = ub[2] / rho;
+        q2 = u * u + v * v;
+        p = gm1 * (ub[3] - (T)0.5 * rho * q2);
+        if (!(rho > (T)0) || !(p > (T)0)) return false;
+        c = sqrt((T)law.gamma * p / rho);
+        H = (ub[3] + p) / rho;
+        b1 = gm1 / (c * c);
+        ic = (T)1 / c;
+    } else {
+        const T irho = (T)1 / rho;
+        u = ub[1] * irho;
+        v = ub[2] * irho;
+        q2 = u * u + v * v;
+        p = gm1 * (ub[3] - (T)0.5 * rho * q2);
+        if (!(rho > (T)0) || !(p > (T)0)) return false;
+        c = sqrtf((T)law.gamma * p * irho);
+        H = (ub[3] + p) * irho;
+        ic = (T)1 / c;
+        b1 = gm1 * ic * ic;
+    }
     const T un = u * nx + v * ny, ut = -u * ny + v * nx;
-    const T b1 = gm1 / (c * c), b2 = (T)0.5 * b1 * q2, ic = (T)1 / c;
+    const T b2 = (T)0.5 * b1 * q2;
     const T R[4][4] = {{1, 1, 0, 1},
                        {u - c * nx, u, -ny, u + c * nx},
                        {v - c * ny, v, nx, v + c * ny},
