@@ -677,12 +677,12 @@ BYTES_2D_PER_CELL = {"fp32": 2 * 40 * 4, "fp64": 2 * 40 * 8}
 # divided by the 1024^2 cells (FMA = 2 flops; min/max, compares and
 # conversions not counted; the FP32 kernel's few FP64 instructions, 6 per
 # cell, are left out).
-FLOPS_2D_PER_CELL = {"fp32": (467432989 + 2 * 2406384696 + 288406782) / 1048576.0,
+FLOPS_2D_PER_CELL = {"fp32": (474529627 + 2 * 2199850085 + 288415269) / 1048576.0,
                      "fp64": (412078081 + 2 * 2396458776 + 341564899) / 1048576.0}
 # DRAM bytes (read + write) of one launch per cell, same captures; scaled by
 # cells to the bench size.  The writes undercount the stored DOFs: part of
 # the output is still in L2 when the kernel ends.
-TRAFFIC_2D_PER_CELL = {"fp32": None, "fp64": (358728448 + 294830336) / 1048576.0}
+TRAFFIC_2D_PER_CELL = {"fp32": (178708480 + 119950336) / 1048576.0, "fp64": (358728448 + 294830336) / 1048576.0}
 
 
 def two_d_bench(args):
