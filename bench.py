@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--two-d", action="store_true",
                     help="the 2D Euler half-step (isentropic vortex, P = 3) instead")
     ap.add_argument("--n2d", type=int, default=2048, help="cells per axis of the 2D workload")
+    ap.add_argument("--workloads2d", action="store_true",
+                    help="the paper's 2D Riemann problems at 1200^2 to t_end instead")
     ap.add_argument("--high-order", action="store_true",
                     help="FP64 Euler half-steps at P = 3..6 (seeded Riemann data) instead")
     return ap.parse_args()
@@ -825,8 +827,51 @@ def high_order_bench(args):
         print(f"| {r['P']} | {r['cfl']} | {r['ms_per_halfstep']:.3f} | {r['cell_updates_per_s'] / 1e9:.3f} G | {fl} | {fr} |")
 
 
+def paper_workloads_2d(n=1200):
+    """The 2D Riemann problems of Sec. 5.3 at the paper's resolution (n x n
+    cells on [-1, 1]^2, transmissive): configuration 1 (four shocks) to
+    t = 1.1 and configuration 2 (four contacts) to t = 1, P = 1..3 with the
+    Sec. 5 CFL numbers, limiter on, through wcc2d_step_until.  Reports the
+    half-steps, the time to solution (second pass on the handle, host clock
+    around the synchronous call) and the density range.  FP32 at every P;
+    FP64 at P = 1."""
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    nu = {1: 0.4, 2: 0.3, 3: 0.25}
+    rows = []
+    for cfg, t_end in ((1, 1.1), (2, 1.0)):
+        for P in (1, 2, 3):
+            pr = inputs.riemann2d(n, P, cfg)
+            precs = ((wcc.FP32, "fp32"), (wcc.FP64, "fp64")) if P == 1 else ((wcc.FP32, "fp32"),)
+            for prec, name in precs:
+                with wcc.Solver2D(pr.system, n, n, P, (pr.x_l, pr.x_r, pr.y_l, pr.y_r), pr.bc, precision=prec,
+                                  rows_per_cta=16) as s:
+                    s.set_initial(pr.q0)
+                    s.step_until(t_end, nu[P])  # first pass: history growth, warm caches
+                    s.set_initial(pr.q0)
+                    t0 = time.perf_counter()
+                    k = s.step_until(t_end, nu[P])
+                    secs = time.perf_counter() - t0
+                    q = s.get_dofs()
+                    launches = s.launch_count()
+                rho = q[:, :, 0, 0]
+                row = {"workload": f"riemann2d-{cfg}", "n": n, "P": P, "precision": name, "t_end": t_end,
+                       "halfsteps": k, "seconds": secs, "ms_per_halfstep": 1e3 * secs / k,
+                       "cell_updates_per_s": n * n * k / secs, "rho_min": float(rho.min()), "rho_max": float(rho.max())}
+                rows.append(row)
+                print(json.dumps(row), flush=True)
+    print("| problem | P | precision | half-steps | time to t_end | ms / half-step | cell-updates/s | density range |")
+    print("|---|---|---|---|---|---|---|---|")
+    for r in rows:
+        print(f"| {r['workload']} (t = {r['t_end']}) | {r['P']} | {r['precision']} | {r['halfsteps']} | {r['seconds']:.2f} s | "
+              f"{r['ms_per_halfstep']:.3f} | {r['cell_updates_per_s'] / 1e9:.2f} G | {r['rho_min']:.3f} .. {r['rho_max']:.3f} |")
+
+
 def main():
     args = parse()
+    if args.workloads2d:
+        paper_workloads_2d()
+        return
     if args.high_order:
         high_order_bench(args)
         return
