@@ -157,7 +157,15 @@ def test_fp32_follows_the_oracle(P):
     assert l1 <= 2e-6, l1
 
 
-def test_table3_mesh_1_10_on_gpu(golden_dir):
+@pytest.mark.parametrize("precision", [wcc.FP64, wcc.FP32])
+def test_table3_mesh_1_10_on_gpu(golden_dir, precision):
+    # FP64 reproduces every printed row within 5 %.  FP32 (every value in
+    # float) has a rounding floor: the cell averages round by ~6e-8 per
+    # half-step, which random-walks to an L1 of ~1e-6 over the ~430 half-steps
+    # of the run, so its L1 is checked only where the printed L1 is above 1e-5
+    # (P <= 2); its L-inf is checked on every row.  With the limiter at P = 2
+    # the weights switch where a candidate's slope is at rounding level (the
+    # limiter's P = 2 sensitivity), so FP32 gets 15 % there.
     rows = []
     with open(f"{golden_dir}/table3_vortex.txt") as f:
         for line in f:
@@ -165,16 +173,22 @@ def test_table3_mesh_1_10_on_gpu(golden_dir):
                 sch, P, inv, l1, linf = line.split()
                 if int(inv) == 10:
                     rows.append((sch, int(P), float(l1), float(linf)))
+    bad = []
     for sch, P, l1, linf in rows:
         pr = inputs.isentropic_vortex(100, P)
-        with _solver(pr, limiter=sch == "WCCS") as s:
+        with _solver(pr, precision=precision, limiter=sch == "WCCS") as s:
             s.set_initial(pr.q0)
             s.step_until(2.0, CFL[P])
             q = s.get_dofs()
             t = s.state()[0]
         X, Y = inputs._grid2d(100, 100, -5.0, 5.0, -5.0, 5.0, inputs.PERIODIC)
         e = np.abs(q[:, :, 0, 0] - inputs.vortex_exact(X, Y, t)[0])
-        assert abs(e.mean() / l1 - 1) < 0.05 and abs(e.max() / linf - 1) < 0.05, (sch, P, e.mean(), e.max())
+        tol = 0.15 if (precision == wcc.FP32 and sch == "WCCS" and P == 2) else 0.05
+        r1, rinf = e.mean() / l1 - 1, e.max() / linf - 1
+        check_l1 = precision == wcc.FP64 or l1 > 1e-5
+        if not ((abs(r1) < tol or not check_l1) and abs(rinf) < tol):
+            bad.append((sch, P, round(r1, 4), round(rinf, 4)))
+    assert not bad, bad
 
 
 def test_errors_are_reported():
