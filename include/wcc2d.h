@@ -47,7 +47,7 @@ extern "C" {
 
 /* Options.  wcc2d_default_options fills: precision = WCC_FP64, limiter = 1,
  * alpha = 2, eps = 1e-40 (Eq. 2D2ndOrderWeights), gamma = 1.4, ax = ay = 1,
- * rows_per_cta = 32 (new rows one CTA marches through), cuda_stream = NULL
+ * rows_per_cta = 16 (new rows one CTA marches through), cuda_stream = NULL
  * (the handle creates its own non-blocking stream).  precision is WCC_FP64 or
  * WCC_FP32 (every value and operation in float). */
 typedef struct {

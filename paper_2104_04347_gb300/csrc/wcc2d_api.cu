@@ -124,7 +124,7 @@ void wcc2d_default_options(wcc2d_options* o) {
     o->gamma = 1.4;
     o->ax = 1.0;
     o->ay = 1.0;
-    o->rows_per_cta = 32;
+    o->rows_per_cta = 16;
     o->cuda_stream = nullptr;
 }
 

@@ -421,7 +421,7 @@ class Solver2D:
 
     def __init__(self, system: int, nx: int, ny: int, P: int, domain, bc: int, *, precision: int = FP64,
                  limiter: bool = True, alpha: float = 2.0, eps: float = 1e-40, gamma: float = 1.4,
-                 ax: float = 1.0, ay: float = 1.0, rows_per_cta: int = 32, stream: int | None = None):
+                 ax: float = 1.0, ay: float = 1.0, rows_per_cta: int = 16, stream: int | None = None):
         self.lib = load()
         o = Options2D()
         self.lib.wcc2d_default_options(ctypes.byref(o))
