@@ -651,19 +651,23 @@ def paper_workloads():
                        "l1_vs_oracle": None}
                 if prec != wcc.FP32:
                     sol = oracle.Solver(oracle.make_law(pr.system, P, limiter=True, bc=pr.bc), pr.q0, pr.dx)
+                    t1 = time.perf_counter()
                     sol.step_dt(dts)
+                    row["oracle_seconds"] = time.perf_counter() - t1
+                    row["oracle_cores"] = oracle.get_threads()
                     row["l1_vs_oracle"] = float(length * np.mean(np.abs(rho - avg(sol.q)[:, 0])))
                 rows.append(row)
                 print(json.dumps(row), flush=True)
     print("| workload | P | precision | half-steps | time to t_end | µs / half-step | L1 vs exact | "
-          "entropy-wave std | L1 vs oracle |")
-    print("|---|---|---|---|---|---|---|---|---|")
+          "entropy-wave std | L1 vs oracle | oracle time (same half-steps) |")
+    print("|---|---|---|---|---|---|---|---|---|---|")
     for r in rows:
         le = "" if r["l1_exact"] is None else f"{r['l1_exact']:.3e}"
         ws = "" if r["wave_std"] is None else f"{r['wave_std']:.4f}"
         lo = "" if r["l1_vs_oracle"] is None else f"{r['l1_vs_oracle']:.1e}"
+        ot = "" if "oracle_seconds" not in r else f"{r['oracle_seconds']:.2f} s ({r['oracle_cores']} cores)"
         print(f"| {r['workload']} | {r['P']} | {r['precision']} | {r['halfsteps']} | {1e3 * r['seconds']:.1f} ms | "
-              f"{r['us_per_halfstep']:.2f} | {le} | {ws} | {lo} |")
+              f"{r['us_per_halfstep']:.2f} | {le} | {ws} | {lo} | {ot} |")
 
 
 # 2D path (Sec. 3, Sec. 4): the isentropic vortex of Sec. 5.3 on n x n cells,
@@ -813,18 +817,31 @@ def high_order_bench(args):
             ms = ev[0].elapsed_time(ev[-1]) / (args.steps * HALFSTEPS_PER_STEP)
             cells = s.num_cells()
         row = {"P": P, "N": pr.N, "cfl": CFL_HIGH[P], "ms_per_halfstep": ms, "cell_updates_per_s": cells / (ms / 1e3)}
+        # the oracle on a bounded sample of the same workload: a 2^14-cell
+        # window around the jump, CFL half-steps for about cpu_seconds / 8
+        import oracle
+        win = inputs.euler_riemann_seeded(1 << 14, P)
+        sol = oracle.Solver(oracle.make_law(oracle.EULER, P, limiter=True, bc=oracle.TRANSMISSIVE), win.q0, win.dx)
+        t0 = time.perf_counter()
+        k = 0
+        while k < 2 or time.perf_counter() - t0 < args.cpu_seconds / 8:
+            sol.step_cfl(1, CFL_HIGH[P])
+            k += 1
+        row["oracle_cell_updates_per_s"] = sol.q.shape[0] * k / (time.perf_counter() - t0)
+        row["oracle_cores"] = oracle.get_threads()
         if FP64_FLOPS_HIGH[P]:
             tf = FP64_FLOPS_HIGH[P] * cells / (ms / 1e3) / 1e12
             row.update({"fp64_flops_per_cell": FP64_FLOPS_HIGH[P], "fp64_tflops": tf, "fp64_frac": tf / FP64_PEAK_TFLOPS})
         rows.append(row)
         print(json.dumps(row), flush=True)
     print(json.dumps({"clocks": clocks.stop()}), flush=True)
-    print("| P | CFL | ms / half-step | cell-updates/s | FP64 flops / cell | of the FP64 peak |")
-    print("|---|---|---|---|---|---|")
+    print("| P | CFL | ms / half-step | cell-updates/s | FP64 flops / cell | of the FP64 peak | oracle (2^14-cell window) |")
+    print("|---|---|---|---|---|---|---|")
     for r in rows:
         fl = "" if "fp64_flops_per_cell" not in r else f"{r['fp64_flops_per_cell']:.0f}"
         fr = "" if "fp64_frac" not in r else f"{r['fp64_frac']:.3f}"
-        print(f"| {r['P']} | {r['cfl']} | {r['ms_per_halfstep']:.3f} | {r['cell_updates_per_s'] / 1e9:.3f} G | {fl} | {fr} |")
+        print(f"| {r['P']} | {r['cfl']} | {r['ms_per_halfstep']:.3f} | {r['cell_updates_per_s'] / 1e9:.3f} G | {fl} | {fr} | "
+              f"{r['oracle_cell_updates_per_s'] / 1e6:.2f} M ({r['oracle_cores']} cores) |")
 
 
 def paper_workloads_2d(n=1200):
