@@ -89,6 +89,43 @@ def test_one_halfstep_each_parity_fp64(system, P, bc):
                 q = want
 
 
+@pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
+@pytest.mark.parametrize("P", [1, 2, 3])
+@pytest.mark.parametrize("system", [ADV, BURG, EULER])
+def test_one_halfstep_each_parity_fp32(system, P, bc):
+    # every value in float: one half-step from the state the FP32 path holds
+    # (the oracle's input rounded to float), in L1 per variable (over its
+    # scale) within max(2e-7, 50 x the oracle's L1 spread under 1e-7 relative
+    # input noise) -- the limiter's weights can switch on rounding-level
+    # slopes, so single entries are not compared (FP64 does that) -- on
+    # 127-cell FP32 strips with ragged tails
+    nx, ny = (300, 300) if (system == EULER and bc == inputs.PERIODIC) else (300, 45)
+    pr = _problem(system, nx, ny, P, bc)
+    law = _law(pr, True)
+    rng = np.random.default_rng(system * 10 + P)
+    with _solver(pr, precision=wcc.FP32) as s:
+        s.set_initial(pr.q0)
+        q = pr.q0.astype(np.float32).astype(np.float64)  # what the FP32 path stores
+        for parity in (0, 1):
+            dt = 0.6 * oracle.cfl_dt2d(law, q, pr.dx, pr.dy, 1.0) * CFL[P]
+            s.step_dt([dt])
+            got = s.get_dofs()
+            lx, ly = dt / pr.dx, dt / pr.dy
+            want = oracle.halfstep2d(law, parity, q, lx, ly)
+            sc = np.maximum(np.max(np.abs(want[:, :, :, 0]), axis=(0, 1)), 1e-300)
+
+            def l1(a):
+                return np.mean(np.abs(a - want), axis=(0, 1, 3)) / sc  # per variable
+
+            spread = np.zeros(want.shape[2])
+            for _ in range(3):
+                pert = q * (1.0 + 1e-7 * rng.standard_normal(q.shape))
+                spread = np.maximum(spread, l1(oracle.halfstep2d(law, parity, pert, lx, ly)))
+            ratio = float(np.max(l1(got) / np.maximum(2e-7, 50.0 * spread)))
+            assert ratio <= 1.0, (system, P, bc, parity, ratio)
+            q = got  # continue from the GPU's own (float) state
+
+
 @pytest.mark.parametrize("P", [1, 2, 3])
 def test_strip_and_row_tails(P):
     # meshes of one strip and a bit, rows per CTA that do not divide ny
