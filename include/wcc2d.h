@@ -28,7 +28,8 @@
  *     (|ax|, |ay|; |u|; |u| + c, |v| + c) at the cell centre; the paper does
  *     not state a 2D rule, and this one reproduces its Table 3.
  *   - The device layout is private: planes [var][q][row][col] of FP64
- *     (WCC_FP64) or FP32 (WCC_FP32) values.
+ *     (WCC_FP64) or FP32 values; WCC_FP32_MIXED keeps the cell average (as
+ *     a float-float pair) in place of the point value.
  *
  * Ownership and threads: as in wcc.h.  The handle owns its device memory;
  * caller buffers are borrowed for the call only; one call at a time per
@@ -48,8 +49,10 @@ extern "C" {
 /* Options.  wcc2d_default_options fills: precision = WCC_FP64, limiter = 1,
  * alpha = 2, eps = 1e-40 (Eq. 2D2ndOrderWeights), gamma = 1.4, ax = ay = 1,
  * rows_per_cta = 16 (new rows one CTA marches through), cuda_stream = NULL
- * (the handle creates its own non-blocking stream).  precision is WCC_FP64 or
- * WCC_FP32 (every value and operation in float). */
+ * (the handle creates its own non-blocking stream).  precision is WCC_FP64,
+ * WCC_FP32 (every value and operation in float) or WCC_FP32_MIXED (float
+ * arithmetic, with the cell average, the leading flux terms and the vertex
+ * point values in float-float, so that the averages keep about 48 bits). */
 typedef struct {
     int precision;
     int limiter;

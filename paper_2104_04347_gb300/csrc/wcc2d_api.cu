@@ -20,7 +20,8 @@ thread_local std::string g_create_error2d;
 
 struct wcc2d_ctx {
     int system = 0, P = 1, bc = 0, nv = 1, nq = 3;
-    int fp32 = 0;
+    int fp32 = 0;   // float storage (WCC_FP32 or WCC_FP32_MIXED)
+    int mixed = 0;  // WCC_FP32_MIXED: float-float cell averages
     int device = 0;
     int64_t nx = 0, ny = 0;
     double x0 = 0, x1 = 1, y0 = 0, y1 = 1, dx = 1, dy = 1;
@@ -146,8 +147,8 @@ int wcc2d_create(wcc2d_handle* out, int system, int64_t nx, int64_t ny, int P, c
         o = *opt;
     else
         wcc2d_default_options(&o);
-    if (o.precision != WCC_FP64 && o.precision != WCC_FP32)
-        return fail2(nullptr, WCC_E_INVAL, "precision must be WCC_FP64 or WCC_FP32");
+    if (o.precision != WCC_FP64 && o.precision != WCC_FP32 && o.precision != WCC_FP32_MIXED)
+        return fail2(nullptr, WCC_E_INVAL, "precision must be WCC_FP64, WCC_FP32_MIXED or WCC_FP32");
     if (!(o.alpha > 0) || !(o.eps >= 0) || !(o.gamma > 1) || o.rows_per_cta < 1 || o.rows_per_cta > 4096 ||
         !std::isfinite(o.ax) || !std::isfinite(o.ay))
         return fail2(nullptr, WCC_E_INVAL, "bad options");
@@ -165,7 +166,8 @@ int wcc2d_create(wcc2d_handle* out, int system, int64_t nx, int64_t ny, int P, c
     h->bc = bc;
     h->nv = system == WCC_EULER ? 4 : 1;
     h->nq = (P + 1) * (P + 2) / 2;
-    h->fp32 = o.precision == WCC_FP32;
+    h->fp32 = o.precision != WCC_FP64;
+    h->mixed = o.precision == WCC_FP32_MIXED;
     h->nx = nx;
     h->ny = ny;
     h->x0 = domain[0];
@@ -191,7 +193,9 @@ int wcc2d_create(wcc2d_handle* out, int system, int64_t nx, int64_t ny, int P, c
     // what the kernel needs before its first launch.
     {
         size_t need = 0, have = 0;
-        if (halfstep2d_local_bytes(system, P, o.precision == WCC_FP32, &need) != cudaSuccess ||
+        const cudaError_t qe = h->mixed ? halfstep2d_mx_local_bytes(system, P, &need)
+                                        : halfstep2d_local_bytes(system, P, h->fp32 != 0, &need);
+        if (qe != cudaSuccess ||
             cudaDeviceGetLimit(&have, cudaLimitStackSize) != cudaSuccess ||
             (need > have && cudaDeviceSetLimit(cudaLimitStackSize, (need + 255) / 256 * 256) != cudaSuccess)) {
             cudaGetLastError();
@@ -205,7 +209,8 @@ int wcc2d_create(wcc2d_handle* out, int system, int64_t nx, int64_t ny, int P, c
     h->pitch = (maxx + align - 1) / align * align;
     h->rows_alloc = maxy;
     h->plane = h->pitch * h->rows_alloc;
-    const size_t stage_bytes = (size_t)(h->nv * h->nq) * (size_t)h->plane * elem_size(h);
+    // FP32-mixed: one more plane per variable for the low part of the average
+    const size_t stage_bytes = (size_t)(h->nv * (h->nq + (h->mixed ? 1 : 0))) * (size_t)h->plane * elem_size(h);
     const size_t staging_bytes = (size_t)(maxx * maxy) * (size_t)(h->nv * h->nq) * sizeof(double);
     bool ok = true;
     for (int i = 0; i < 2 && ok; ++i) ok = cudaMalloc(&h->planes[i], stage_bytes) == cudaSuccess;
@@ -265,7 +270,10 @@ int wcc2d_set_initial(wcc2d_handle h, const double* dofs, int64_t count) {
     WCC2D_CHECK(h, cudaMemcpyAsync(h->staging, dofs, (size_t)count * sizeof(double), cudaMemcpyHostToDevice,
                                    h->stream));
     const int g = conv_grid(cx * cy * nd);
-    if (h->fp32)
+    if (h->mixed)
+        WCC2D_CHECK(h, launch_convert2d_mx(h->P, true, h->staging, static_cast<float*>(h->planes[0]), (int)cx, (int)cy,
+                                           h->nv, h->pitch, h->plane, h->stream));
+    else if (h->fp32)
         aos_to_planes2d<float><<<g, 256, 0, h->stream>>>(h->staging, static_cast<float*>(h->planes[0]), (int)cx,
                                                          (int)cy, nd, h->pitch, h->plane);
     else
@@ -273,8 +281,12 @@ int wcc2d_set_initial(wcc2d_handle h, const double* dofs, int64_t count) {
                                                           (int)cy, nd, h->pitch, h->plane);
     WCC2D_CHECK(h, cudaGetLastError());
     WCC2D_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState2D), h->stream));
-    WCC2D_CHECK(h, launch_stage_rate2d(h->system, h->fp32, h->planes[0], h->pitch, h->plane, (int)cx, (int)cy, h->nq,
-                                       h->law, h->dx, h->dy, h->st, h->stream));
+    if (h->mixed)
+        WCC2D_CHECK(h, launch_stage_rate2d_mx(h->system, h->P, static_cast<const float*>(h->planes[0]), h->pitch,
+                                              h->plane, (int)cx, (int)cy, h->law, h->dx, h->dy, h->st, h->stream));
+    else
+        WCC2D_CHECK(h, launch_stage_rate2d(h->system, h->fp32, h->planes[0], h->pitch, h->plane, (int)cx, (int)cy,
+                                           h->nq, h->law, h->dx, h->dy, h->st, h->stream));
     h->launches += 2;
     h->cur = 0;
     h->parity = 0;
@@ -313,7 +325,8 @@ int launch_one(wcc2d_ctx* h, double dt_given, double cfl) {
     a.st = h->st;
     a.hist = h->hist;
     a.hist_cap = h->hist_cap;
-    cudaError_t e = launch_halfstep2d(h->system, h->P, h->fp32 != 0, a, h->stream);
+    cudaError_t e = h->mixed ? launch_halfstep2d_mx(h->system, h->P, a, h->stream)
+                             : launch_halfstep2d(h->system, h->P, h->fp32 != 0, a, h->stream);
     if (e != cudaSuccess) return cuda_fail2(h, e, "2D half-step launch");
     h->cur ^= 1;
     h->parity ^= 1;
@@ -425,7 +438,10 @@ int wcc2d_get_dofs(wcc2d_handle h, double* dofs, int64_t count) {
     int rc = read_state(h, &s);
     if (rc != WCC_OK) return rc;
     const int g = conv_grid(cx * cy * nd);
-    if (h->fp32)
+    if (h->mixed)
+        WCC2D_CHECK(h, launch_convert2d_mx(h->P, false, h->staging, static_cast<float*>(h->planes[h->cur]), (int)cx,
+                                           (int)cy, h->nv, h->pitch, h->plane, h->stream));
+    else if (h->fp32)
         planes_to_aos2d<float><<<g, 256, 0, h->stream>>>(static_cast<const float*>(h->planes[h->cur]), h->staging,
                                                          (int)cx, (int)cy, nd, h->pitch, h->plane);
     else

@@ -298,7 +298,7 @@ __global__ void planes_to_aos2d(const T* planes, double* aos, int nx, int ny, in
 template <int SYS, int P, class T>
 constexpr int strip_width() {
     int tw = sizeof(T) == 8 ? 64 : 128;
-    while (tw > 32 && ring_bytes<T, 1>(record_fields<SYS, P>()) * tw > 48 * 1024) tw -= 32;
+    while (tw > 32 && ring_bytes<T, 1>(record_fields<SYS, P>()) * tw > 48 * 1024 - 256) tw -= 32;
     return tw;
 }
 
@@ -307,7 +307,7 @@ template <int SYS, int P, class T>
 cudaError_t launch_halfstep2d_t(const Step2D& a, cudaStream_t stream) {
     constexpr int TW = strip_width<SYS, P, T>();
     constexpr size_t smem = ring_bytes<T, TW>(record_fields<SYS, P>());
-    static_assert(smem <= 48 * 1024, "the shared ring must fit without the opt-in attribute");
+    static_assert(smem <= 48 * 1024 - 256, "the shared ring and the static shared words must fit without the opt-in attribute");
     const dim3 grid((a.nx_new + TW - 2) / (TW - 1), (a.ny_new + a.rows_per_cta - 1) / a.rows_per_cta);
     halfstep2d<SYS, P, T, TW><<<grid, TW, smem, stream>>>(a);
     return cudaGetLastError();
@@ -357,6 +357,272 @@ cudaError_t launch_stage_rate2d_sys(bool fp32, const void* planes, long long pit
     return cudaGetLastError();
 }
 
+// --------------------------------------------------------- FP32-mixed kernel
+
+// Stage layout of the FP32-mixed path: plane (v, 0) holds the high part of
+// the cell average (not the point value), planes (v, q >= 1) the scaled
+// derivatives in float, and plane NV * NQ + v the low part of the average.
+// A parent record: per variable its four shares of the children's averages
+// (hi[4], lo[4]), its vertex point value at t^{n+1/2} (hi, lo), and the
+// vertex derivatives q = 1 .. NQ1 - 1 (float).
+template <int SYS, int P>
+__host__ __device__ constexpr int record_fields_mx() {
+    return nvars(SYS) * (10 + nq(P - 1) - 1);
+}
+
+template <int SYS, int P>
+constexpr int strip_width_mx() {
+    int tw = 128;
+    while (tw > 32 && ring_bytes<float, 1>(record_fields_mx<SYS, P>()) * tw > 48 * 1024 - 256) tw -= 32;
+    return tw;
+}
+
+template <int TW, int NV, int NQ1>
+struct RingReaderMx {
+    const float* lo;
+    const float* hi;
+    int t;
+    __device__ __forceinline__ float get(int r, int f) const {
+        return r == 0 ? lo[f * TW + t] : r == 1 ? lo[f * TW + t + 1] : r == 2 ? hi[f * TW + t + 1] : hi[f * TW + t];
+    }
+    __device__ __forceinline__ ff cf(int r, int v) const { return ff{get(r, v * 8 + r), get(r, v * 8 + 4 + r)}; }
+    __device__ __forceinline__ ff v00(int r, int v) const {
+        return ff{get(r, NV * 8 + 2 * v), get(r, NV * 8 + 2 * v + 1)};
+    }
+    __device__ __forceinline__ float V(int r, int v, int q) const {
+        return q == 0 ? get(r, NV * 8 + 2 * v) : get(r, NV * 10 + v * (NQ1 - 1) + q - 1);
+    }
+};
+
+template <int SYS, int P, int TW>
+__global__ void __launch_bounds__(TW, 4) halfstep2d_mx(const Step2D a) {
+    constexpr int NV = nvars(SYS), NQ = nq(P), NQ1 = nq(P - 1);
+    constexpr int NF = record_fields_mx<SYS, P>();
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float* ring = reinterpret_cast<float*>(smem_raw);  // [2][NF][TW]
+
+    const int t = threadIdx.x;
+    const int off = a.parity ? -1 : 0;
+    const int i0 = blockIdx.x * (TW - 1);
+    const int j0 = blockIdx.y * a.rows_per_cta;
+    const int rows = min(a.rows_per_cta, a.ny_new - j0);
+
+    double dt = a.dt_given;
+    if (!(dt > 0.0)) dt = a.cfl / __longlong_as_double((long long)a.st->rate_bits[a.parity]);
+    const float lamx = (float)(dt / a.dx), lamy = (float)(dt / a.dy);
+    const float hx = 0.5f * lamx, hy = 0.5f * lamy;
+    const float idx = (float)(1.0 / a.dx), idy = (float)(1.0 / a.dy);
+
+    const float* in = static_cast<const float*>(a.in);
+    float* out = static_cast<float*>(a.out);
+    const int pc = parent_index(i0 + t + off, a.nx_old, a.bc);
+    float rate_max = 0.f;
+    unsigned err = 0;
+
+    for (int s = 0; s <= rows; ++s) {
+        {
+            const int pr = parent_index(j0 + off + s, a.ny_old, a.bc);
+            const long long cell = (long long)pr * a.pitch + pc;
+            float q[NV][NQ];
+            ff ub[NV], u00[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                ub[v] = ff{in[(long long)(v * NQ) * a.plane + cell], in[(long long)(NV * NQ + v) * a.plane + cell]};
+                q[v][0] = 0.f;
+#pragma unroll
+                for (int qq = 1; qq < NQ; ++qq) q[v][qq] = in[(long long)(v * NQ + qq) * a.plane + cell];
+                u00[v] = wcc::ff_add(ub[v], -even_correction<P>(q[v]));
+                q[v][0] = u00[v].hi;
+            }
+            Parent<SYS, P, float, true> par;
+            parent_terms<SYS, P, float, true>(q, lamx, lamy, a.law, par);
+            ff F[NV], G[NV];
+            lead_flux_ff<SYS>(u00, a.law, F, G);
+            float* r = ring + (s & 1) * NF * TW;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                const ff fU = wcc::ff_add(F[v], par.fl[v][0]), fD = wcc::ff_add(F[v], par.fl[v][1]);
+                const ff gR = wcc::ff_add(G[v], par.fl[v][2]), gL = wcc::ff_add(G[v], par.fl[v][3]);
+                // quarter averages: ubar +- ox +- oy +- oxy with the signs of
+                // RU, LU, LD, RD (vertex roles 1..4); every term enters the
+                // four shares with opposite signs, so the parent's shares add
+                // up to its ubar to float-float rounding
+                const float ox = 0.25f * par.odd[v][0], oy = 0.25f * par.odd[v][1], oxy = 0.25f * par.odd[v][2];
+                const ff q4 = ffm(ub[v], 0.25f);
+                const ff tx = ffm(fU, hx), bx = ffm(fD, hx), ry = ffm(gR, hy), ly = ffm(gL, hy);
+                ff c[4];
+                c[0] = wcc::ff_add(wcc::ff_add(wcc::ff_add(wcc::ff_add(q4, ox), oy), oxy), wcc::ff_add(tx, ry));
+                c[1] = wcc::ff_add(wcc::ff_add(wcc::ff_add(wcc::ff_add(q4, -ox), oy), -oxy), wcc::ff_sub(ly, tx));
+                c[2] = wcc::ff_sub(wcc::ff_add(wcc::ff_add(wcc::ff_add(q4, -ox), -oy), oxy), wcc::ff_add(bx, ly));
+                c[3] = wcc::ff_add(wcc::ff_add(wcc::ff_add(wcc::ff_add(q4, ox), -oy), -oxy), wcc::ff_sub(bx, ry));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    r[(v * 8 + k) * TW + t] = c[k].hi;
+                    r[(v * 8 + 4 + k) * TW + t] = c[k].lo;
+                }
+                const ff v00 = wcc::ff_add(u00[v], par.V[v][0]);
+                r[(NV * 8 + 2 * v) * TW + t] = v00.hi;
+                r[(NV * 8 + 2 * v + 1) * TW + t] = v00.lo;
+#pragma unroll
+                for (int qq = 1; qq < NQ1; ++qq) r[(NV * 10 + v * (NQ1 - 1) + qq - 1) * TW + t] = par.V[v][qq];
+            }
+        }
+        __syncthreads();
+        if (s >= 1 && t < TW - 1 && i0 + t < a.nx_new) {
+            const RingReaderMx<TW, NV, NQ1> rd{ring + ((s - 1) & 1) * NF * TW, ring + (s & 1) * NF * TW, t};
+            float D[NV][NQ];
+            ff ub[NV];
+            linear_cell_mx<SYS, P>(rd, D, ub);
+            if (a.law.limiter) {
+                if constexpr (SYS == EULER) {
+                    float vv[4][4], ubf[4];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) {
+                        ubf[v] = ub[v].hi;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) vv[v][k] = rd.V(k, v, 0);
+                    }
+                    if (!limit_euler<P, float>(D, ubf, vv, lamx, lamy, a.law)) err |= ERR_POSITIVITY;
+                } else {
+                    float vv[4];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) vv[k] = rd.V(k, 0, 0);
+                    limit_scalar<P, float>(D[0], ub[0].hi, vv, a.law);
+                }
+            }
+            // the limiter keeps the cell average (every candidate has mean ubar)
+            const long long cell = (long long)(j0 + s - 1) * a.pitch + (i0 + t);
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+                out[(long long)(v * NQ) * a.plane + cell] = ub[v].hi;
+                out[(long long)(NV * NQ + v) * a.plane + cell] = ub[v].lo;
+#pragma unroll
+                for (int qq = 1; qq < NQ; ++qq) out[(long long)(v * NQ + qq) * a.plane + cell] = D[v][qq];
+            }
+            float centre[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) centre[v] = D[v][0];
+            const float rate = cfl_rate<SYS, float>(centre, a.law, idx, idy);
+            if (rate != rate) {
+                err |= (SYS == EULER && ub[0].hi == ub[0].hi) ? ERR_POSITIVITY : ERR_NONFINITE;
+                rate_max = INFINITY;
+            } else {
+                rate_max = rate > rate_max ? rate : rate_max;
+            }
+        }
+        __syncthreads();
+    }
+    finish2d<float, TW>(rate_max, err, dt, a);
+}
+
+// host [row][col][v][q] FP64 point values and derivatives <-> FP32-mixed
+// planes; one thread per cell (set-up and read-back only)
+template <int P>
+__global__ void aos_to_planes2d_mx(const double* aos, float* planes, int nx, int ny, int nv, long long pitch,
+                                   long long plane) {
+    constexpr int NQ = nq(P);
+    const long long n = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const long long cell = (c / nx) * pitch + (c % nx);
+        for (int v = 0; v < nv; ++v) {
+            const double* d = aos + (c * nv + v) * NQ;
+            double ub = d[0];
+            unroll<P + 1>([&](auto kc) {
+                unroll<P + 1 - kc>([&](auto lc) {
+                    constexpr int k = kc, l = lc;
+                    if constexpr (k + l > 0 && !(k & 1) && !(l & 1))
+                        ub += pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1) * d[qidx(k, l)];
+                });
+            });
+            const float hi = (float)ub;
+            planes[(long long)(v * NQ) * plane + cell] = hi;
+            planes[(long long)(nv * NQ + v) * plane + cell] = (float)(ub - (double)hi);
+            for (int qq = 1; qq < NQ; ++qq) planes[(long long)(v * NQ + qq) * plane + cell] = (float)d[qq];
+        }
+    }
+}
+
+template <int P>
+__global__ void planes_to_aos2d_mx(const float* planes, double* aos, int nx, int ny, int nv, long long pitch,
+                                   long long plane) {
+    constexpr int NQ = nq(P);
+    const long long n = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const long long cell = (c / nx) * pitch + (c % nx);
+        for (int v = 0; v < nv; ++v) {
+            double* d = aos + (c * nv + v) * NQ;
+            for (int qq = 1; qq < NQ; ++qq) d[qq] = (double)planes[(long long)(v * NQ + qq) * plane + cell];
+            double u = (double)planes[(long long)(v * NQ) * plane + cell] + (double)planes[(long long)(nv * NQ + v) * plane + cell];
+            unroll<P + 1>([&](auto kc) {
+                unroll<P + 1 - kc>([&](auto lc) {
+                    constexpr int k = kc, l = lc;
+                    if constexpr (k + l > 0 && !(k & 1) && !(l & 1))
+                        u -= pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1) * d[qidx(k, l)];
+                });
+            });
+            d[0] = u;
+        }
+    }
+}
+
+// CFL rate of a loaded FP32-mixed stage: the point value from the average
+template <int SYS, int P>
+__global__ void __launch_bounds__(256) stage_rate2d_mx(const float* planes, long long pitch, long long plane, int nx,
+                                                       int ny, Law2D law, double dx, double dy, DevState2D* st) {
+    constexpr int NV = nvars(SYS), NQ = nq(P);
+    float m = 0.f;
+    unsigned err = 0;
+    const long long n = (long long)nx * ny;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+        const long long cell = (c / nx) * pitch + (c % nx);
+        float centre[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            float d[NQ];
+            d[0] = 0.f;
+#pragma unroll
+            for (int qq = 1; qq < NQ; ++qq) d[qq] = planes[(long long)(v * NQ + qq) * plane + cell];
+            const ff ub{planes[(long long)(v * NQ) * plane + cell], planes[(long long)(NV * NQ + v) * plane + cell]};
+            centre[v] = wcc::ff_add(ub, -even_correction<P>(d)).hi;
+        }
+        const float r = cfl_rate<SYS, float>(centre, law, (float)(1.0 / dx), (float)(1.0 / dy));
+        if (r != r) {
+            err |= SYS == EULER ? ERR_POSITIVITY : ERR_NONFINITE;
+            m = INFINITY;
+        } else if (r > m) {
+            m = r;
+        }
+    }
+    double r = (double)m;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    err = __reduce_or_sync(0xffffffffu, err);
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&st->rate_bits[0], (unsigned long long)__double_as_longlong(r));
+        if (err) atomicOr(&st->err, err);
+    }
+}
+
+template <int SYS, int P>
+cudaError_t launch_halfstep2d_mx_t(const Step2D& a, cudaStream_t stream) {
+    constexpr int TW = strip_width_mx<SYS, P>();
+    constexpr size_t smem = ring_bytes<float, TW>(record_fields_mx<SYS, P>());
+    static_assert(smem <= 48 * 1024 - 256, "the shared ring and the static shared words must fit without the opt-in attribute");
+    const dim3 grid((a.nx_new + TW - 2) / (TW - 1), (a.ny_new + a.rows_per_cta - 1) / a.rows_per_cta);
+    halfstep2d_mx<SYS, P, TW><<<grid, TW, smem, stream>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace wcc2d
+
+namespace wcc2d {
+// Instantiated in wcc2d_mixed.cu.
+cudaError_t launch_halfstep2d_mx(int system, int P, const Step2D& a, cudaStream_t stream);
+cudaError_t launch_stage_rate2d_mx(int system, int P, const float* planes, long long pitch, long long plane, int nx,
+                                   int ny, const Law2D& law, double dx, double dy, DevState2D* st, cudaStream_t stream);
+cudaError_t launch_convert2d_mx(int P, bool to_planes, double* aos, float* planes, int nx, int ny, int nv,
+                                long long pitch, long long plane, cudaStream_t stream);
+cudaError_t halfstep2d_mx_local_bytes(int system, int P, size_t* bytes);
 }  // namespace wcc2d
 
 namespace wcc2d {

@@ -16,6 +16,8 @@
 #include <type_traits>
 #include <utility>
 
+#include "wcc_ff.cuh"
+
 namespace wcc2d {
 
 enum { ADVECTION = 0, BURGERS = 1, EULER = 2 };
@@ -97,12 +99,21 @@ __device__ __forceinline__ float weight_ratio(float a, float b) { return __fdivi
 //   V[v][q]: scaled derivatives at the centre at t^{n+1/2}, k + l <= P - 1
 //            (the entries Eqs. SubEq:2DUx, SubEq:2DUy read; q = 0 is the
 //            vertex value of the limiter), Eq. SubEq:2DUij.
-template <int SYS, int P, class T>
+template <int SYS, int P, class T, bool MX = false>
 struct Parent {
     static constexpr int NV = nvars(SYS);
     static constexpr int NQ1 = nq(P - 1);
     T c[NV][4];
     T V[NV][NQ1];
+    // FP32-mixed (MX): the parts left in float once the leading terms are
+    // taken out to be added in float-float.  The quarter averages of Eqs.
+    // SubEq:2DCellAVGRU ... LD are the cell average (their even terms) plus
+    // +-odd[v][0] +- odd[v][1] +- odd[v][2], the sums over the terms odd in
+    // xi only, in eta only and in both; fl[v][0..3] = the edge fluxes f_U, f_D,
+    // g_R, g_L without their leading term f(u_00) (resp. g(u_00)); V[v][0]
+    // is without the point value u_00 itself.
+    T odd[NV][4];
+    T fl[NV][4];
 };
 
 // Compile-time loop: f(std::integral_constant<int, I>{}) for I = 0 .. N-1, so
@@ -123,9 +134,9 @@ __device__ __forceinline__ void unroll(F&& f) {
 // Leibniz rule for products and quotients (Dyson / Dumbser-Munz).  Each flux
 // entry is used as soon as it is formed: for the next time level of U and
 // for the edge-flux integrals of Appendix B.
-template <int SYS, int P, class T>
+template <int SYS, int P, class T, bool MX = false>
 __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T lamx, T lamy, const Law2D& law,
-                                             Parent<SYS, P, T>& out) {
+                                             Parent<SYS, P, T, MX>& out) {
     constexpr int NV = nvars(SYS);
     // qa[v]: quarter averages RU, RD, LU, LD at t^n (mean of xi^k over [0, 1/2]
     // is 1/((k+1) 2^k), (-1)^k that over [-1/2, 0]); fl[v]: f_U, f_D on the
@@ -139,10 +150,17 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
             unroll<P + 1 - k>([&](auto lc) {
                 constexpr int l = lc;
                 const T cd = (T)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1)) * q[v][qidx(k, l)];
-                ru += cd;
-                rd += (T)sgnd(l) * cd;
-                lu += (T)sgnd(k) * cd;
-                ld += (T)(sgnd(k) * sgnd(l)) * cd;
+                if constexpr (MX) {
+                    // ru, rd, lu collect the terms odd in xi only, in eta only, in both
+                    if constexpr ((k & 1) && !(l & 1)) ru += cd;
+                    if constexpr (!(k & 1) && (l & 1)) rd += cd;
+                    if constexpr ((k & 1) && (l & 1)) lu += cd;
+                } else {
+                    ru += cd;
+                    rd += (T)sgnd(l) * cd;
+                    lu += (T)sgnd(k) * cd;
+                    ld += (T)(sgnd(k) * sgnd(l)) * cd;
+                }
             });
         });
         qa[v][0] = ru;
@@ -239,16 +257,17 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
                 }
                 unroll<NV>([&](auto vc) {
                     constexpr int v = vc;
+                    (void)v;
                     // (k + l >= 1 implies m + 1 <= P)
                     if constexpr (k >= 1) U[v][k - 1][l][m + 1] -= lamx * F[v];
                     if constexpr (l >= 1) U[v][k][l - 1][m + 1] -= lamy * G[v];
                     // Eqs. SubEq:2DFluxFU ... GL: one space direction along the edge, and time
-                    if constexpr (k == 0) {
+                    if constexpr (k == 0 && (!MX || l + m > 0)) {
                         const T cs = (T)(pow2m(l) / factd(l + 1) / factd(m + 1)) * F[v];
                         fl[v][0] += cs;
                         fl[v][1] += (T)sgnd(l) * cs;
                     }
-                    if constexpr (l == 0) {
+                    if constexpr (l == 0 && (!MX || k + m > 0)) {
                         const T cs = (T)(pow2m(k) / factd(k + 1) / factd(m + 1)) * G[v];
                         fl[v][2] += cs;
                         fl[v][3] += (T)sgnd(k) * cs;
@@ -261,11 +280,19 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
     // gives RU, +f_U, +g_R; as 2: LU, -f_U, +g_L; as 3: LD, -f_D, -g_L; as 4: RD, +f_D, -g_R
     unroll<NV>([&](auto vc) {
         constexpr int v = vc;
-        const T hx = (T)0.5 * lamx, hy = (T)0.5 * lamy;
-        out.c[v][0] = (T)0.25 * qa[v][0] + hx * fl[v][0] + hy * fl[v][2];
-        out.c[v][1] = (T)0.25 * qa[v][2] - hx * fl[v][0] + hy * fl[v][3];
-        out.c[v][2] = (T)0.25 * qa[v][3] - hx * fl[v][1] - hy * fl[v][3];
-        out.c[v][3] = (T)0.25 * qa[v][1] + hx * fl[v][1] - hy * fl[v][2];
+        if constexpr (MX) {
+            out.odd[v][0] = qa[v][0];  // odd in xi only
+            out.odd[v][1] = qa[v][1];  // odd in eta only
+            out.odd[v][2] = qa[v][2];  // odd in both
+#pragma unroll
+            for (int s = 0; s < 4; ++s) out.fl[v][s] = fl[v][s];
+        } else {
+            const T hx = (T)0.5 * lamx, hy = (T)0.5 * lamy;
+            out.c[v][0] = (T)0.25 * qa[v][0] + hx * fl[v][0] + hy * fl[v][2];
+            out.c[v][1] = (T)0.25 * qa[v][2] - hx * fl[v][0] + hy * fl[v][3];
+            out.c[v][2] = (T)0.25 * qa[v][3] - hx * fl[v][1] - hy * fl[v][3];
+            out.c[v][3] = (T)0.25 * qa[v][1] + hx * fl[v][1] - hy * fl[v][2];
+        }
     });
     // Eq. SubEq:2DUij
     unroll<NV>([&](auto vc) {
@@ -273,7 +300,9 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
             unroll<P - kc>([&](auto lc) {
                 constexpr int k = kc, l = lc;
                 T s = 0;
-                unroll<P + 1 - k - l>([&](auto mc) { s += (T)(1.0 / factd(mc)) * U[vc][k][l][mc]; });
+                unroll<P + 1 - k - l>([&](auto mc) {
+                    if constexpr (!MX || k + l + mc > 0) s += (T)(1.0 / factd(mc)) * U[vc][k][l][mc];
+                });
                 out.V[vc][qidx(k, l)] = s;
             });
         });
@@ -593,6 +622,135 @@ __device__ __forceinline__ T cfl_rate(const T* centre, const Law2D& law, T idx, 
         const T c = sqrt((T)law.gamma * p / rho);
         return (fabs(u) + c) * idx + (fabs(v) + c) * idy;
     }
+}
+
+// ------------------------------------------------------------- FP32-mixed
+
+// Float-float pieces of the FP32-mixed 2D path: the cell average, the leading
+// flux terms and the vertex point values carry about 48 bits, everything else
+// is float (as in the 1D FP32-mixed path).
+using wcc::ff;
+
+__device__ __forceinline__ ff ffm(ff a, float b) {  // a * b
+    ff p = wcc::two_prod(a.hi, b);
+    return wcc::fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
+}
+__device__ __forceinline__ ff ffdiv(ff a, ff b) {  // a / b for a normal b
+    const float q1 = __fdividef(a.hi, b.hi);
+    const ff r = wcc::ff_sub(a, wcc::ff_mul(b, ff{q1, 0.f}));
+    const float q2 = __fdividef(r.hi, b.hi);
+    return wcc::fast_two_sum(q1, q2);
+}
+
+// f(u) and g(u) at a point value u given in float-float (the (0,0,0) entries
+// of the flux tables, the leading terms of Eqs. SubEq:2DFluxFU ... GL).
+template <int SYS>
+__device__ __forceinline__ void lead_flux_ff(const ff (&u)[nvars(SYS)], const Law2D& law, ff (&F)[nvars(SYS)],
+                                             ff (&G)[nvars(SYS)]) {
+    if constexpr (SYS == ADVECTION) {
+        F[0] = ffm(u[0], (float)law.ax);
+        G[0] = ffm(u[0], (float)law.ay);
+    } else if constexpr (SYS == BURGERS) {
+        F[0] = ffm(wcc::ff_mul(u[0], u[0]), 0.5f);
+        G[0] = F[0];
+    } else {
+        const ff vx = ffdiv(u[1], u[0]), vy = ffdiv(u[2], u[0]);
+        const ff mu = wcc::ff_mul(u[1], vx), mv = wcc::ff_mul(u[1], vy), nv = wcc::ff_mul(u[2], vy);
+        const ff p = ffm(wcc::ff_sub(u[3], ffm(wcc::ff_add(mu, nv), 0.5f)), (float)(law.gamma - 1.0));
+        const ff Ep = wcc::ff_add(u[3], p);
+        F[0] = u[1];
+        F[1] = wcc::ff_add(mu, p);
+        F[2] = mv;
+        F[3] = wcc::ff_mul(Ep, vx);
+        G[0] = u[2];
+        G[1] = mv;
+        G[2] = wcc::ff_add(nv, p);
+        G[3] = wcc::ff_mul(Ep, vy);
+    }
+}
+
+// Sum over the even (k, l) != (0, 0) of the weights of Eq. SubEq:2DCellAVG
+// times u_{kx,ly}: the cell average is u_00 plus this.
+template <int P>
+__device__ __forceinline__ float even_correction(const float (&d)[nq(P)]) {
+    float s = 0.f;
+    unroll<P + 1>([&](auto kc) {
+        unroll<P + 1 - kc>([&](auto lc) {
+            constexpr int k = kc, l = lc;
+            if constexpr (k + l > 0 && !(k & 1) && !(l & 1))
+                s += (float)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1)) * d[qidx(k, l)];
+        });
+    });
+    return s;
+}
+
+// The new cell's linear part in the FP32-mixed form: the cell average as the
+// float-float sum of the four parents' shares, the degree-1 derivatives from
+// float-float differences of the vertex point values, the rest as
+// linear_cell.  rd.cf(r, v), rd.v00(r, v) (float-float) and rd.V(r, v, q)
+// (float, q >= 1) read parent r.  D[v][0] receives the point value (hi).
+template <int SYS, int P, class Rd>
+__device__ __forceinline__ void linear_cell_mx(const Rd& rd, float (&D)[nvars(SYS)][nq(P)], ff (&ubar)[nvars(SYS)]) {
+    constexpr int NV = nvars(SYS);
+    unroll<NV>([&](auto vc) {
+        constexpr int v = vc;
+        ubar[v] = wcc::ff_add(wcc::ff_add(rd.cf(0, v), rd.cf(1, v)), wcc::ff_add(rd.cf(2, v), rd.cf(3, v)));
+        unroll<P>([&](auto dd) {
+            constexpr int d = P - dd;
+            unroll<d + 1>([&](auto bc) {
+                constexpr int b = bc, a = d - b;
+                float sum = 0.f;
+                if constexpr (a >= 1) {
+                    constexpr int k = a - 1, l = b, r = P - k - l;
+                    constexpr int q0 = qidx(k, l);
+                    float s;
+                    if constexpr (q0 == 0)
+                        s = ffm(wcc::ff_sub(wcc::ff_add(rd.v00(1, v), rd.v00(2, v)), wcc::ff_add(rd.v00(0, v), rd.v00(3, v))),
+                                0.5f).hi;
+                    else
+                        s = 0.5f * ((rd.V(1, v, q0) + rd.V(2, v, q0)) - (rd.V(0, v, q0) + rd.V(3, v, q0)));
+                    unroll<r - 2>([&](auto s3c) {
+                        constexpr int s3 = s3c + 3;
+                        s -= (float)((pow2m(s3) - ipow(-0.5, s3)) / factd(s3)) * D[v][qidx(k + s3, l)];
+                    });
+                    unroll<r - 1>([&](auto tc) {
+                        constexpr int t = tc + 2;
+                        unroll<r - t>([&](auto sc) {
+                            constexpr int s1 = sc + 1;
+                            if constexpr ((s1 & 1) && !(t & 1))
+                                s -= (float)(2.0 * pow2m(s1 + t) / (factd(s1) * factd(t))) * D[v][qidx(k + s1, l + t)];
+                        });
+                    });
+                    sum += s;
+                }
+                if constexpr (b >= 1) {
+                    constexpr int k = a, l = b - 1, r = P - k - l;
+                    constexpr int q0 = qidx(k, l);
+                    float s;
+                    if constexpr (q0 == 0)
+                        s = ffm(wcc::ff_sub(wcc::ff_add(rd.v00(3, v), rd.v00(2, v)), wcc::ff_add(rd.v00(0, v), rd.v00(1, v))),
+                                0.5f).hi;
+                    else
+                        s = 0.5f * ((rd.V(3, v, q0) + rd.V(2, v, q0)) - (rd.V(0, v, q0) + rd.V(1, v, q0)));
+                    unroll<r - 2>([&](auto t3c) {
+                        constexpr int t3 = t3c + 3;
+                        s -= (float)((pow2m(t3) - ipow(-0.5, t3)) / factd(t3)) * D[v][qidx(k, l + t3)];
+                    });
+                    unroll<r>([&](auto tc) {
+                        constexpr int t = tc + 1;
+                        unroll<r - t - 1>([&](auto sc) {
+                            constexpr int s2 = sc + 2;
+                            if constexpr ((t & 1) && !(s2 & 1))
+                                s -= (float)(2.0 * pow2m(s2 + t) / (factd(s2) * factd(t))) * D[v][qidx(k + s2, l + t)];
+                        });
+                    });
+                    sum += s;
+                }
+                D[v][qidx(a, b)] = (a >= 1 && b >= 1) ? 0.5f * sum : sum;
+            });
+        });
+        D[v][0] = wcc::ff_add(ubar[v], -even_correction<P>(D[v])).hi;
+    });
 }
 
 }  // namespace wcc2d
