@@ -65,7 +65,7 @@ def test_p_above_4_needs_fp64(precision):
     ((2, 64, 1 << 16, 2, (0.0, 1.0, 0.0, 1.0), 0), {}, -7, "2^15"),
     ((2, 64, 64, 2, (0.0, 1.0, 1.0, 0.0), 0), {}, -1, "domain"),
     ((2, 64, 64, 2, (0.0, 1.0, 0.0, 1.0), 5), {}, -1, "bc"),
-    ((2, 64, 64, 2, (0.0, 1.0, 0.0, 1.0), 0), {"precision": wcc.FP32_MIXED}, -1, "precision"),
+    ((2, 64, 64, 2, (0.0, 1.0, 0.0, 1.0), 0), {"precision": 7}, -1, "precision"),
     ((2, 64, 64, 2, (0.0, 1.0, 0.0, 1.0), 0), {"rows_per_cta": 0}, -1, "options"),
 ])
 def test_create2d_rejects_bad_arguments(args, kw, code, needle):
