@@ -8,8 +8,9 @@ characteristic limiter is active.
   max(1e-11 x scale, 50 x the oracle's own spread under 4e-16 input noise)
   (the limiter's weights are ill-conditioned at a discontinuity, as in 1D);
   the GPU's dt is the oracle's CFL step of that state.
-* FP32: the trajectory's L1 against the oracle replaying the same half-step
-  sizes, within max(1e-5, 50 x the oracle's L1 spread under 1e-7 noise).
+* FP32 and FP32-mixed: the trajectory's L1 against the oracle replaying the
+  same half-step sizes, within max(1e-5, 50 x the oracle's L1 spread under
+  1e-7 noise).
 """
 import numpy as np
 import pytest
@@ -62,12 +63,13 @@ def test_every_halfstep_fp64(config, P):
     assert worst <= 1.0, worst
 
 
+@pytest.mark.parametrize("precision", [wcc.FP32, wcc.FP32_MIXED])
 @pytest.mark.parametrize("P", [1, 2, 3])
 @pytest.mark.parametrize("config", [1, 2])
-def test_trajectory_fp32(config, P):
+def test_trajectory_fp32(config, P, precision):
     pr = inputs.riemann2d(N, P, config)
     law = _law(P)
-    with _solver(pr, wcc.FP32) as s:
+    with _solver(pr, precision) as s:
         s.set_initial(pr.q0)
         s.step(STEPS, CFL[P])
         got = s.get_dofs()
