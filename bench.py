@@ -856,8 +856,8 @@ def paper_workloads_2d(n=1200):
     t = 1.1 and configuration 2 (four contacts) to t = 1, P = 1..3 with the
     Sec. 5 CFL numbers, limiter on, through wcc2d_step_until.  Reports the
     half-steps, the time to solution (second pass on the handle, host clock
-    around the synchronous call) and the density range.  FP32 at every P;
-    FP64 at P = 1."""
+    around the synchronous call) and the density range.  FP32-mixed and FP32
+    at every P; FP64 at P = 1."""
     from paper_2104_04347_gb300 import inputs, wcc
 
     nu = {1: 0.4, 2: 0.3, 3: 0.25}
@@ -865,7 +865,9 @@ def paper_workloads_2d(n=1200):
     for cfg, t_end in ((1, 1.1), (2, 1.0)):
         for P in (1, 2, 3):
             pr = inputs.riemann2d(n, P, cfg)
-            precs = ((wcc.FP32, "fp32"), (wcc.FP64, "fp64")) if P == 1 else ((wcc.FP32, "fp32"),)
+            precs = ((wcc.FP32_MIXED, "fp32-mixed"), (wcc.FP32, "fp32"))
+            if P == 1:
+                precs += ((wcc.FP64, "fp64"),)
             for prec, name in precs:
                 with wcc.Solver2D(pr.system, n, n, P, (pr.x_l, pr.x_r, pr.y_l, pr.y_r), pr.bc, precision=prec,
                                   rows_per_cta=16) as s:
