@@ -18,6 +18,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle import exact
 from paper_2104_04347_gb300 import inputs
 
 CFL = {1: 0.4, 2: 0.3, 3: 0.25}
@@ -321,3 +322,55 @@ def test_smoothness_indicator_against_quadrature(P):
             vals = np.vectorize(lambda x, y: _poly_deriv(D, P, k, l, x, y))(X, Y)
             ref += float(np.sum(W * vals ** 2))
     assert abs(oracle.smoothness2d(D, P) - ref) <= 1e-12 * ref
+
+
+def _diag_dofs(n, P, u0_derivs):
+    """DOFs of u0(x + y) on periodic [-1, 1]^2: u_{kx,ly} = dx^k dy^l u0^(k+l)(x + y)."""
+    X, Y = inputs._grid2d(n, n, -1.0, 1.0, -1.0, 1.0, inputs.PERIODIC)
+    d = 2.0 / n
+    q = np.zeros((n, n, 1, inputs.nq2d(P)))
+    for k in range(P + 1):
+        for l in range(P + 1 - k):
+            q[:, :, 0, inputs.idx2d(k, l)] = d ** (k + l) * u0_derivs(X + Y, k + l)
+    return q, X, Y, d
+
+
+def _orders(errs, ns):
+    return [math.log(errs[i] / errs[i + 1]) / math.log(ns[i + 1] / ns[i]) for i in range(len(errs) - 1)]
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_advection_converges_at_order_p_plus_1(P):
+    # u0 = sin(pi (x + y)) carried by (ax, ay) = (1, 0.5) to t = 0.5 (linear scheme)
+    ax, ay, t_end = 1.0, 0.5, 0.5
+    law = oracle.make_law2d(oracle.ADVECTION, P, limiter=False, ax=ax, ay=ay)
+    ns, errs = (16, 32, 64), []
+    for n in ns:
+        q, X, Y, d = _diag_dofs(n, P, lambda s, k: math.pi ** k * np.sin(math.pi * s + k * math.pi / 2))
+        s = oracle.Solver2D(law, q, d, d)
+        s.step_until(t_end, CFL[P])
+        errs.append(float(np.mean(np.abs(s.q[:, :, 0, 0] - np.sin(math.pi * (X - ax * s.t + Y - ay * s.t))))))
+    o = _orders(errs, ns)
+    assert all(P + 1 - 0.25 < oi < P + 1 + 0.8 for oi in o), (errs, o)
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_burgers_converges_before_the_shock(P):
+    # f = g = u^2/2 with u0 = 0.5 + 0.25 sin(pi (x + y)): u depends on s = x + y
+    # only and solves u_t + 2 u u_s = 0, so u = u0(xi) with xi + 2 t u0(xi) = s
+    # (shock at t = 2 / pi); the linear scheme to t = 0.2 against it
+    t_end = 0.2
+    law = oracle.make_law2d(oracle.BURGERS, P, limiter=False)
+
+    def u0d(s, k):
+        return (0.5 if k == 0 else 0.0) + 0.25 * math.pi ** k * np.sin(math.pi * s + k * math.pi / 2)
+
+    ns, errs = (16, 32, 64), []
+    for n in ns:
+        q, X, Y, d = _diag_dofs(n, P, u0d)
+        s = oracle.Solver2D(law, q, d, d)
+        s.step_until(t_end, CFL[P])
+        ex = exact.burgers_characteristics(lambda z: u0d(z, 0), lambda z: u0d(z, 1), X + Y, 2.0 * s.t)
+        errs.append(float(np.mean(np.abs(s.q[:, :, 0, 0] - ex))))
+    o = _orders(errs, ns)
+    assert all(P + 1 - 0.35 < oi < P + 1 + 0.6 for oi in o), (errs, o)
