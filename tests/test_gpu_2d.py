@@ -276,3 +276,47 @@ def test_errors_are_reported():
         with pytest.raises(wcc.WCCError) as ei:
             s.step_until(t - 0.1, 0.3)
         assert ei.value.code == -1
+
+
+@pytest.mark.parametrize("system", [ADV, BURG])
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_scalar_convergence_like_the_oracle(system, P):
+    # the oracle's convergence pins (advection of sin(pi (x + y)); Burgers with
+    # data of x + y before its shock) through the C ABI: FP64 errors against
+    # the exact solution equal the oracle's, FP32-mixed ones follow them
+    # where they are well above float rounding (n <= 32)
+    t_end = 0.5 if system == ADV else 0.2
+    ax, ay = (1.0, 0.5) if system == ADV else (1.0, 1.0)
+
+    def u0d(s, k):
+        if system == ADV:
+            return math.pi ** k * np.sin(math.pi * s + k * math.pi / 2)
+        return (0.5 if k == 0 else 0.0) + 0.25 * math.pi ** k * np.sin(math.pi * s + k * math.pi / 2)
+
+    law = oracle.make_law2d(system, P, limiter=False, ax=ax, ay=ay)
+    for n in (16, 32, 64):
+        X, Y = inputs._grid2d(n, n, -1.0, 1.0, -1.0, 1.0, inputs.PERIODIC)
+        d = 2.0 / n
+        q = np.zeros((n, n, 1, inputs.nq2d(P)))
+        for k in range(P + 1):
+            for l in range(P + 1 - k):
+                q[:, :, 0, inputs.idx2d(k, l)] = d ** (k + l) * u0d(X + Y, k + l)
+        if system == ADV:
+            ex = np.sin(math.pi * (X - ax * t_end + Y - ay * t_end))
+        else:
+            from oracle import exact
+            ex = exact.burgers_characteristics(lambda z: u0d(z, 0), lambda z: u0d(z, 1), X + Y, 2.0 * t_end)
+        ref = oracle.Solver2D(law, q, d, d)
+        ref.step_until(t_end, CFL[P])
+        e_ora = float(np.mean(np.abs(ref.q[:, :, 0, 0] - ex)))
+        for prec in (wcc.FP64, wcc.FP32_MIXED):
+            if prec == wcc.FP32_MIXED and n > 32:
+                continue
+            with wcc.Solver2D(system, n, n, P, (-1.0, 1.0, -1.0, 1.0), inputs.PERIODIC, precision=prec,
+                              limiter=False, ax=ax, ay=ay) as s:
+                s.set_initial(q)
+                s.step_until(t_end, CFL[P])
+                got = s.get_dofs()
+            e = float(np.mean(np.abs(got[:, :, 0, 0] - ex)))
+            tol = 1e-6 if prec == wcc.FP64 else 0.02
+            assert abs(e - e_ora) <= tol * e_ora, (system, P, n, prec, e, e_ora)
