@@ -79,7 +79,7 @@ void wcc2d_default_options(wcc2d_options* opt);
  * limit; create raises cudaLimitStackSize of the calling process's current
  * context to what the kernel needs (never lowers it), a process-wide effect
  * that outlives the handle.  Errors: WCC_E_INVAL, WCC_E_CAPACITY (nx or ny
- * out of range), WCC_E_NOMEM, WCC_E_CUDA (no device, stream or stack
+ * above 2^15), WCC_E_NOMEM, WCC_E_CUDA (no device, stream or stack
  * limit); *out is set to NULL on every error but a NULL out. */
 int wcc2d_create(wcc2d_handle* out, int system, int64_t nx, int64_t ny, int P, const double domain[4], int bc,
                  const wcc2d_options* opt);
