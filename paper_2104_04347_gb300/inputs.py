@@ -363,9 +363,11 @@ def idx2d(k: int, l: int) -> int:
 
 class Taylor2:
     """Truncated Taylor series in two variables (X, Y), one per point:
-    ``c[..., k, l]`` is the coefficient of X^k Y^l, kept for k + l <= P.
-    Enough arithmetic (+, -, *, exp, real powers) to evaluate initial data
-    and read off every mixed derivative at once: d^k_x d^l_y u = k! l! c_kl."""
+    ``c[k, l, ...]`` is the coefficient of X^k Y^l, kept for k + l <= P (the
+    coefficient axes come first, so that every operation on one coefficient
+    runs over contiguous memory).  Enough arithmetic (+, -, *, exp, real
+    powers) to evaluate initial data and read off every mixed derivative at
+    once: d^k_x d^l_y u = k! l! c_kl."""
 
     def __init__(self, c: np.ndarray, P: int):
         self.c = c
@@ -374,17 +376,17 @@ class Taylor2:
     @staticmethod
     def variable(x0, which: int, P: int) -> "Taylor2":
         x0 = np.asarray(x0, dtype=np.float64)
-        c = np.zeros(x0.shape + (P + 1, P + 1))
-        c[..., 0, 0] = x0
+        c = np.zeros((P + 1, P + 1) + x0.shape)
+        c[0, 0] = x0
         if P >= 1:
-            c[..., (1, 0)[which], (0, 1)[which]] = 1.0
+            c[(1, 0)[which], (0, 1)[which]] = 1.0
         return Taylor2(c, P)
 
     def _lift(self, o) -> "Taylor2":
         if isinstance(o, Taylor2):
             return o
         c = np.zeros_like(self.c)
-        c[..., 0, 0] = o
+        c[0, 0] = o
         return Taylor2(c, self.P)
 
     def __add__(self, o):
@@ -403,14 +405,15 @@ class Taylor2:
 
     def __mul__(self, o):
         if not isinstance(o, Taylor2):
-            return Taylor2(self.c * np.asarray(o)[..., None, None], self.P)
+            return Taylor2(self.c * np.asarray(o), self.P)  # a number per point
         P = self.P
-        out = np.zeros(np.broadcast_shapes(self.c.shape, o.c.shape))
+        a, b = self.c, o.c
+        out = np.zeros((P + 1, P + 1) + np.broadcast_shapes(a.shape[2:], b.shape[2:]))
         for k in range(P + 1):
             for l in range(P + 1 - k):
                 for i in range(k + 1):
                     for j in range(l + 1):
-                        out[..., k, l] += self.c[..., i, j] * o.c[..., k - i, l - j]
+                        out[k, l] += a[i, j] * b[k - i, l - j]
         return Taylor2(out, P)
 
     __rmul__ = __mul__
@@ -418,7 +421,7 @@ class Taylor2:
     def _series(self, coef) -> "Taylor2":
         """sum_n coef[n] h^n with h = self - self(0), which vanishes to order
         P + 1 after P factors."""
-        h = self - self.c[..., 0, 0]
+        h = self - self.c[0, 0]
         term = self._lift(1.0)
         acc = term * coef[0]
         for n in range(1, self.P + 1):
@@ -427,11 +430,11 @@ class Taylor2:
         return acc
 
     def exp(self) -> "Taylor2":
-        a0 = self.c[..., 0, 0]
+        a0 = self.c[0, 0]
         return self._series([1.0 / math.factorial(n) for n in range(self.P + 1)]) * np.exp(a0)
 
     def pow(self, s: float) -> "Taylor2":
-        a0 = self.c[..., 0, 0]
+        a0 = self.c[0, 0]
         coef = []
         b = 1.0
         for n in range(self.P + 1):
@@ -443,10 +446,10 @@ class Taylor2:
     def scaled_dofs(self, dx: float, dy: float) -> np.ndarray:
         """[..., nq] scaled derivatives dx^k dy^l d^k_x d^l_y."""
         P = self.P
-        out = np.zeros(self.c.shape[:-2] + (nq2d(P),))
+        out = np.zeros(self.c.shape[2:] + (nq2d(P),))
         for k in range(P + 1):
             for l in range(P + 1 - k):
-                out[..., idx2d(k, l)] = (self.c[..., k, l] * math.factorial(k) * math.factorial(l)
+                out[..., idx2d(k, l)] = (self.c[k, l] * math.factorial(k) * math.factorial(l)
                                          * dx ** k * dy ** l)
         return out
 
