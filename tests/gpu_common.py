@@ -141,3 +141,28 @@ def oracle_l1_spread(pr, dts, perturb, *, trials=3, seed=0):
         q = run(pr.q0 * (1.0 + perturb * rng.standard_normal(pr.q0.shape)))
         worst = max(worst, float(np.max(np.mean(np.abs(q[:, :, 0] - ref[:, :, 0]), axis=0) / sc)))
     return ref, worst
+
+
+def sampled_new_cells2d(law, q, parity, cells, lamx, lamy, *, rng=None, noise=0.0):
+    """The oracle's new cells (j, i) of one 2D half-step from the stage q
+    [ny, nx, nv, nq], one at a time (oracle.new_cell2d) from their four
+    parents, so that a few cells of a mesh too large for the whole-stage
+    oracle can be checked.  New cell i of parity 0 lies between old cells
+    i and i + 1, of parity 1 between i - 1 and i (Sec. 3.1); periodic meshes
+    wrap, transmissive ones repeat the edge cell.  With ``rng`` each parent
+    is multiplied by (1 + noise x N(0, 1)) entry by entry (the spread of the
+    parity bound).  Returns [len(cells), nv, nq]."""
+    ny, nx = q.shape[:2]
+
+    def parent(j, n):
+        return j % n if law.bc == oracle.PERIODIC else min(max(j, 0), n - 1)
+
+    out = []
+    for j, i in cells:
+        il, jl = (i, j) if parity == 0 else (i - 1, j - 1)
+        x0, x1, y0, y1 = parent(il, nx), parent(il + 1, nx), parent(jl, ny), parent(jl + 1, ny)
+        ps = [q[y0, x0], q[y0, x1], q[y1, x1], q[y1, x0]]
+        if rng is not None:
+            ps = [p * (1.0 + noise * rng.standard_normal(p.shape)) for p in ps]
+        out.append(oracle.new_cell2d(law, *ps, lamx, lamy))
+    return np.array(out)

@@ -439,3 +439,20 @@ def test_mirror_symmetry_with_limiter(P):
                 am = _mirror_y(_mirror_x(a, False, -1.0), False)[::-1, ::-1][idx][:, idx]
                 assert np.max(np.abs(am - b) / scale) <= 1e-12, (P, parity, "xy")
             q = a
+
+
+@pytest.mark.parametrize("bc", [oracle.PERIODIC, oracle.TRANSMISSIVE])
+def test_sampled_new_cells_match_the_whole_stage(bc):
+    # the one-cell route the full-size GPU tests use gives the whole-stage
+    # half-step's cells bit for bit, corners and edges included
+    from tests.gpu_common import sampled_new_cells2d
+    P = 2
+    pr = inputs.isentropic_vortex(12, P)
+    q = np.roll(pr.q0, (2, -3), axis=(0, 1))
+    law = oracle.make_law2d(oracle.EULER, P, limiter=True, bc=bc)
+    for parity in (0, 1):
+        want = oracle.halfstep2d(law, parity, q, 0.13, 0.09)
+        cells = [(j, i) for j in range(want.shape[0]) for i in range(want.shape[1])]
+        got = sampled_new_cells2d(law, q, parity, cells, 0.13, 0.09)
+        assert np.array_equal(got.reshape(want.shape), want), (bc, parity)
+        q = want  # transmissive: 11 x 11 cells, then 12 x 12 again
