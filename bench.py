@@ -298,10 +298,11 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": rate, "unit": "cell-updates/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": dt * 1e3 / max(1, args.steps), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": workload_name(args.log2n), "N": N, "P": P,
-                   "precision": "fp64", "halfsteps_per_step": HALFSTEPS_PER_STEP,
-                   "sample_cells": win + 1},
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded Riemann initial data, splitmix64 seed 2104043471)",
+        "config": {"workload": workload_name(args.log2n), "N": N, "P": P, "cells_integer_stage": N + 1,
+                   "precision": "fp64", "halfsteps_per_step": HALFSTEPS_PER_STEP, "cfl": CFL,
+                   "limiter": True, "parallelism": f"host cores x{cores}", "sample_cells": win + 1},
         "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
