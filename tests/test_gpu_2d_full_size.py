@@ -10,8 +10,11 @@ minutes at this size, so
   new cell from its four parents, the parents read back from the GPU's own
   stage, within max(tol x scale, 50 x the oracle's spread when the parents
   carry relative noise): tol 1e-11 with 4e-16 noise for FP64, 2e-6 with
-  1e-7 noise for FP32-mixed and FP32 (whose averages are single floats,
-  a few ulps of the scale), both parities;
+  1e-7 noise for FP32-mixed, both parities.  Plain FP32 (every value in
+  float) is compared in L1 per variable over the samples, within
+  max(2e-7, 50 x the oracle's L1 spread), as in the FP32 tests at small
+  sizes: its limiter weights can switch on rounding-level slopes, so single
+  entries are not compared;
 * the CFL half-step equals the oracle's CFL step of the whole stage;
 * over one bench step (8 half-steps) the FP32-mixed path keeps the summed
   cell averages to float-float rounding.
@@ -47,16 +50,25 @@ def _cells(seed):
     return [(j, i) for j in rows for i in cols] + rand
 
 
-def _check(law, prev, got, parity, lx, ly, tol, noise, seed):
+def _check(law, prev, got, parity, lx, ly, tol, noise, seed, entrywise=True):
     cells = _cells(seed)
     want = sampled_new_cells2d(law, prev, parity, cells, lx, ly)
     rng = np.random.default_rng(seed + 1)
+    g = np.array([got[j, i] for j, i in cells])
+    sc = np.max(np.abs(prev[:, :, :, 0]), axis=(0, 1))[None, :, None]
+    if not entrywise:  # L1 per variable over the samples
+        spread = np.zeros(want.shape[1])
+        for _ in range(3):
+            pert = sampled_new_cells2d(law, prev, parity, cells, lx, ly, rng=rng, noise=noise)
+            spread = np.maximum(spread, np.mean(np.abs(pert - want) / sc, axis=(0, 2)))
+        l1 = np.mean(np.abs(g - want) / sc, axis=(0, 2))
+        ratio = float(np.max(l1 / np.maximum(tol, 50.0 * spread)))
+        assert ratio <= 1.0, (parity, l1, spread, ratio)
+        return
     spread = np.zeros_like(want)
     for _ in range(3):
         pert = sampled_new_cells2d(law, prev, parity, cells, lx, ly, rng=rng, noise=noise)
         spread = np.maximum(spread, np.abs(pert - want))
-    sc = np.max(np.abs(prev[:, :, :, 0]), axis=(0, 1))[None, :, None]
-    g = np.array([got[j, i] for j, i in cells])
     ratio = np.abs(g - want) / np.maximum(tol * sc, 50.0 * spread)
     k = int(np.argmax(ratio.max(axis=(1, 2))))
     assert float(ratio.max()) <= 1.0, (parity, cells[k], float(ratio.max()))
@@ -66,7 +78,8 @@ def _check(law, prev, got, parity, lx, ly, tol, noise, seed):
 def test_sampled_cells_at_full_size(vortex, precision):
     pr = vortex
     law = oracle.make_law2d(oracle.EULER, P, limiter=True)
-    tol, noise, dt_tol = (1e-11, 4e-16, 1e-12) if precision == wcc.FP64 else (2e-6, 1e-7, 1e-5)
+    tol, noise, dt_tol = {wcc.FP64: (1e-11, 4e-16, 1e-12), wcc.FP32_MIXED: (2e-6, 1e-7, 1e-5),
+                          wcc.FP32: (2e-7, 1e-7, 1e-5)}[precision]
     with wcc.Solver2D(pr.system, N, N, P, (pr.x_l, pr.x_r, pr.y_l, pr.y_r), pr.bc, precision=precision,
                       rows_per_cta=ROWS) as s:
         s.set_initial(pr.q0)
@@ -79,7 +92,8 @@ def test_sampled_cells_at_full_size(vortex, precision):
             got = s.get_dofs()
             assert got.shape == prev.shape
             assert np.all(np.isfinite(got))
-            _check(law, prev, got, parity, dt / pr.dx, dt / pr.dy, tol, noise, 100 * precision + parity)
+            _check(law, prev, got, parity, dt / pr.dx, dt / pr.dy, tol, noise, 100 * precision + parity,
+                   entrywise=precision != wcc.FP32)
             prev = got
 
 
