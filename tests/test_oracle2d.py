@@ -12,7 +12,10 @@ outside it:
     reflection with u -> -u) of the limited half-step on discontinuous data,
     conservation, and the rotated eigenvectors against a complex-step
     Jacobian;
-  * the smoothness indicator of Eq. 2DSmoothIndicator against quadrature."""
+  * the smoothness indicator of Eq. 2DSmoothIndicator against quadrature;
+  * order P + 1 against exact solutions (advection; Burgers before its
+    shock), and Sod's tube along x against the exact Riemann solution with
+    the rotated limiter on (first-order L1 rate, rows kept identical)."""
 import math
 import os
 
@@ -456,3 +459,30 @@ def test_sampled_new_cells_match_the_whole_stage(bc):
         got = sampled_new_cells2d(law, q, parity, cells, 0.13, 0.09)
         assert np.array_equal(got.reshape(want.shape), want), (bc, parity)
         q = want  # transmissive: 11 x 11 cells, then 12 x 12 again
+
+
+def test_sod_along_x_against_the_exact_riemann_solution():
+    # Sod's tube (Sec. 5.2: [0, 2], jump at 1, t = 0.4) laid along x on a
+    # 2D mesh of three rows, transmissive on every side, limiter on (rotated
+    # characteristic limiting, Sec. 4): the rows stay bitwise identical, the
+    # y-momentum stays at rounding level, the density's L1 error against the
+    # exact Riemann solution falls at the first-order rate of a captured shock
+    # and contact, and the higher degrees resolve it better (Sec. 5)
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    errs = {}
+    for P in (1, 2, 3):
+        law = oracle.make_law2d(oracle.EULER, P, limiter=True, bc=oracle.TRANSMISSIVE)
+        for N in (100, 200, 400):
+            pr1 = inputs.sod(N, P)
+            s = oracle.Solver2D(law, _lift_1d(pr1.q0, 4), pr1.dx, pr1.dx)
+            s.step_until(0.4, CFL[P])
+            assert s.parity == 0 and abs(s.t - 0.4) < 1e-12
+            assert np.array_equal(s.q[1:], np.broadcast_to(s.q[:1], s.q[1:].shape))
+            assert np.max(np.abs(s.q[:, :, 2])) <= 1e-14
+            x = inputs.centres(N, 0.0, 2.0, inputs.TRANSMISSIVE)
+            rho = exact.riemann_sample(left, right, (x - 1.0) / s.t)[0]
+            errs[P, N] = float(np.mean(np.abs(s.q[0, :, 0, 0] - rho)))
+        orders = [math.log2(errs[P, N] / errs[P, 2 * N]) for N in (100, 200)]
+        assert all(0.6 < o < 1.2 for o in orders), (P, orders)
+    for N in (100, 200, 400):
+        assert errs[3, N] < errs[2, N] < errs[1, N], errs
