@@ -320,3 +320,50 @@ def test_scalar_convergence_like_the_oracle(system, P):
             e = float(np.mean(np.abs(got[:, :, 0, 0] - ex)))
             tol = 1e-6 if prec == wcc.FP64 else 0.02
             assert abs(e - e_ora) <= tol * e_ora, (system, P, n, prec, e, e_ora)
+
+
+@pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
+@pytest.mark.parametrize("system", [ADV, BURG, EULER])
+def test_minimum_mesh(system, bc):
+    # the smallest mesh the ABI accepts, 4 x 4 cells: one CTA, every cell
+    # next to a boundary, the data barely resolved.  The scalar laws carry
+    # the sine s of _problem; Euler a density wave rho = 1 + 0.2 s with
+    # (u, v) = (0.5, -0.3) and p = 1, whose conserved variables are affine in
+    # rho (so their DOFs are those of s, scaled).  Three half-steps against
+    # the oracle: FP64 per entry within max(1e-11 x scale, 50 x the oracle's
+    # spread under 4e-16 noise), as the limiter is active on such coarse
+    # data; FP32-mixed in L1 within max(1e-5, 50 x the oracle's L1 spread
+    # under 1e-7 noise)
+    P = 3
+    pr = _problem(ADV if system == EULER else system, 4, 4, P, bc)
+    if system == EULER:
+        rho = 0.2 * pr.q0[:, :, 0]
+        rho[..., 0] += 1.0
+        E = 0.5 * (0.5 ** 2 + 0.3 ** 2) * rho
+        E[..., 0] += 1.0 / 0.4
+        q0 = np.stack([rho, 0.5 * rho, -0.3 * rho, E], axis=2)
+        pr = inputs.Problem2D(EULER, 4, 4, P, pr.x_l, pr.x_r, pr.y_l, pr.y_r, bc, q0, "density-wave-min")
+    law = _law(pr)
+    rng = np.random.default_rng(system * 3 + bc)
+    for precision in (wcc.FP64, wcc.FP32_MIXED):
+        with _solver(pr, precision=precision, rows_per_cta=1) as s:
+            s.set_initial(pr.q0)
+            s.step(3, 0.5 * CFL[P])
+            got = s.get_dofs()
+            dts = s.dt_history()
+        want = oracle.Solver2D(law, pr.q0, pr.dx, pr.dy)
+        want.step_dt(dts)
+        sc = np.maximum(np.max(np.abs(want.q[:, :, :, 0]), axis=(0, 1)), 1e-300)[None, None, :, None]
+        noise = 4e-16 if precision == wcc.FP64 else 1e-7
+        spread = np.zeros_like(want.q)
+        for _ in range(3):
+            r2 = oracle.Solver2D(law, pr.q0 * (1.0 + noise * rng.standard_normal(pr.q0.shape)), pr.dx, pr.dy)
+            r2.step_dt(dts)
+            spread = np.maximum(spread, np.abs(r2.q - want.q))
+        assert got.shape == want.q.shape
+        if precision == wcc.FP64:
+            ratio = float(np.max(np.abs(got - want.q) / np.maximum(1e-11 * sc, 50.0 * spread)))
+        else:
+            l1 = np.mean(np.abs(got - want.q) / sc, axis=(0, 1, 3))
+            ratio = float(np.max(l1 / np.maximum(1e-5, 50.0 * np.mean(spread / sc, axis=(0, 1, 3)))))
+        assert ratio <= 1.0, (system, bc, precision, ratio)
