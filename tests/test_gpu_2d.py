@@ -7,6 +7,8 @@
 * Trajectories through wcc2d_step_until, the oracle replaying the same
   half-step sizes: FP64 within 1e-10 on smooth data; FP32 in L1.
 * Table 3 (Sec. 5.3) on the GPU at mesh 1/10: the same errors as the oracle.
+* Scalar convergence: the errors against exact solutions equal the oracle's.
+* The minimum mesh (4 x 4) for every system and boundary.
 * Errors: non-physical data, out-of-order calls.
 """
 import math
