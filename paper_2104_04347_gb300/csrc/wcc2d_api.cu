@@ -10,6 +10,7 @@
 #include "wcc2d.h"
 #include "wcc2d_kernels.cuh"
 #include "wcc_launch.h"
+#include "wcc_trace.h"
 
 using wcc::DeviceScope;
 using namespace wcc2d;
@@ -262,6 +263,7 @@ int wcc2d_stage_dims(wcc2d_handle h, int64_t* nx, int64_t* ny) {
 }
 
 int wcc2d_set_initial(wcc2d_handle h, const double* dofs, int64_t count) {
+    WccTraceRange trace_("wcc2d_set_initial");
     if (!h || !dofs) return fail2(h, WCC_E_INVAL, "NULL argument");
     DeviceScope ds_(h->device);
     const int64_t cx = stage_cells_x(h, 0), cy = stage_cells_y(h, 0);
@@ -346,6 +348,7 @@ double cfl_dt_of(const DevState2D& s, int parity, double cfl) {
 }  // namespace
 
 int wcc2d_step(wcc2d_handle h, int64_t nsteps, double cfl) {
+    WccTraceRange trace_("wcc2d_step");
     if (!h) return fail2(h, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (!h->loaded) return fail2(h, WCC_E_STATE, "wcc2d_set_initial has not succeeded");
@@ -358,6 +361,7 @@ int wcc2d_step(wcc2d_handle h, int64_t nsteps, double cfl) {
 }
 
 int wcc2d_step_dt(wcc2d_handle h, int64_t nsteps, const double* dts) {
+    WccTraceRange trace_("wcc2d_step_dt");
     if (!h) return fail2(h, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (!h->loaded) return fail2(h, WCC_E_STATE, "wcc2d_set_initial has not succeeded");
@@ -372,6 +376,7 @@ int wcc2d_step_dt(wcc2d_handle h, int64_t nsteps, const double* dts) {
 }
 
 int wcc2d_step_until(wcc2d_handle h, double t_end, double cfl, int64_t* nsteps_taken) {
+    WccTraceRange trace_("wcc2d_step_until");
     if (!h) return fail2(h, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (nsteps_taken) *nsteps_taken = 0;
@@ -428,6 +433,7 @@ int wcc2d_step_until(wcc2d_handle h, double t_end, double cfl, int64_t* nsteps_t
 }
 
 int wcc2d_get_dofs(wcc2d_handle h, double* dofs, int64_t count) {
+    WccTraceRange trace_("wcc2d_get_dofs");
     if (!h || !dofs) return fail2(h, WCC_E_INVAL, "NULL argument");
     DeviceScope ds_(h->device);
     if (!h->loaded) return fail2(h, WCC_E_STATE, "wcc2d_set_initial has not succeeded");

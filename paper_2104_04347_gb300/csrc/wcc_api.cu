@@ -15,6 +15,7 @@
 #include "wcc_convert.cuh"
 #include "wcc_ff.cuh"
 #include "wcc_scheme.cuh"
+#include "wcc_trace.h"
 
 using namespace wcc;
 
@@ -443,6 +444,7 @@ int wcc_num_cells(wcc_handle h, int64_t* ncells) {
 }
 
 int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
+    WccTraceRange trace_("wcc_set_initial");
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (!dofs) return fail(h, WCC_E_INVAL, "dofs is NULL");
@@ -493,6 +495,7 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
 }
 
 int wcc_step(wcc_handle h, int64_t nsteps, double cfl) {
+    WccTraceRange trace_("wcc_step");
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
@@ -523,6 +526,7 @@ int wcc_step(wcc_handle h, int64_t nsteps, double cfl) {
 }
 
 int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts) {
+    WccTraceRange trace_("wcc_step_dt");
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
@@ -539,6 +543,7 @@ int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts) {
 }
 
 int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
+    WccTraceRange trace_("wcc_get_dofs");
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (!dofs) return fail(h, WCC_E_INVAL, "dofs is NULL");
@@ -561,6 +566,7 @@ int wcc_get_dofs(wcc_handle h, double* dofs, int64_t count) {
 }
 
 int wcc_step_until(wcc_handle h, double t_end, double cfl, int64_t* nsteps_taken) {
+    WccTraceRange trace_("wcc_step_until");
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (nsteps_taken) *nsteps_taken = 0;

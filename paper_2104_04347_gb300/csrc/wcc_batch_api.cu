@@ -11,6 +11,7 @@
 #include "../../include/wcc.h"
 #include "wcc_batch.cuh"
 #include "wcc_launch.h"
+#include "wcc_trace.h"
 
 using namespace wcc;
 
@@ -442,6 +443,7 @@ int wcc_batch_dof_count(wcc_batch b, int64_t* count) {
 }
 
 int wcc_batch_set_initial(wcc_batch b, const double* dofs, int64_t count) {
+    WccTraceRange trace_("wcc_batch_set_initial");
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
     DeviceScope ds_(b->device);
     if (!dofs) return bfail(b, WCC_E_INVAL, "dofs is NULL");
@@ -466,6 +468,7 @@ int wcc_batch_set_initial(wcc_batch b, const double* dofs, int64_t count) {
 }
 
 int wcc_batch_step(wcc_batch b, int64_t nsteps, double cfl) {
+    WccTraceRange trace_("wcc_batch_step");
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
     DeviceScope ds_(b->device);
     if (!b->initialised) return bfail(b, WCC_E_STATE, "wcc_batch_set_initial has not been called");
@@ -474,6 +477,7 @@ int wcc_batch_step(wcc_batch b, int64_t nsteps, double cfl) {
 }
 
 int wcc_batch_get_dofs(wcc_batch b, double* dofs, int64_t count) {
+    WccTraceRange trace_("wcc_batch_get_dofs");
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
     DeviceScope ds_(b->device);
     if (!dofs) return bfail(b, WCC_E_INVAL, "dofs is NULL");
