@@ -417,7 +417,8 @@ class Solver2D:
 
     ``dofs`` arrays are float64 [rows, cols, nv, nq] of the scaled
     derivatives u_{kx,ly}, nq = (P+1)(P+2)/2, position (k+l)(k+l+1)/2 + l.
-    ``domain`` is (x_S, x_E, y_S, y_E).  precision is FP64 or FP32."""
+    ``domain`` is (x_S, x_E, y_S, y_E).  precision is FP64, FP32_MIXED
+    (float arithmetic, float-float cell averages) or FP32."""
 
     def __init__(self, system: int, nx: int, ny: int, P: int, domain, bc: int, *, precision: int = FP64,
                  limiter: bool = True, alpha: float = 2.0, eps: float = 1e-40, gamma: float = 1.4,
