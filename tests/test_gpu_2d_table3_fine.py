@@ -1,0 +1,72 @@
+"""Table 3 (Sec. 5.3) at its finer meshes on the GPU (FP64), against the
+paper's printed density errors of the isentropic vortex at t = 2.
+
+* P <= 2 (LCCS/WCCS-2, -3) at meshes 1/20 and 1/40 on the printed periodic
+  domain [-5, 5]^2: L1 and L-inf within 5 %.
+* P = 3 (LCCS/WCCS-4): the printed domain cuts the vortex's tail (its
+  velocity is 2.4e-5 at the boundary), and at these meshes the resulting
+  far-field error exceeds the scheme's own.  On [-10, 10]^2 with the same
+  mesh size, where the tail is negligible, the errors over the 10 x 10
+  window centred on the vortex at t = 2 (the printed domain's extent around
+  the vortex) are compared: L1 and L-inf within 5 % at 1/20, and at 1/40
+  the LCCS-4 L-inf.
+These meshes take minutes in the CPU oracle, seconds here; the GPU's FP64
+path equals the oracle to 1e-11 on the same problems at coarser meshes.
+"""
+import numpy as np
+import pytest
+
+from paper_2104_04347_gb300 import inputs, wcc
+
+pytestmark = pytest.mark.gpu
+
+CFL = {1: 0.4, 2: 0.3, 3: 0.25}
+
+
+def _table3(golden_dir):
+    rows = {}
+    with open(f"{golden_dir}/table3_vortex.txt") as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                sch, P, inv, l1, linf = line.split()
+                rows[sch, int(P), int(inv)] = (float(l1), float(linf))
+    return rows
+
+
+def _run(sch, P, n, half):
+    X, Y = inputs._grid2d(n, n, -half, half, -half, half, inputs.PERIODIC)
+    dx = 2.0 * half / n
+    U = inputs.vortex_conserved(inputs.Taylor2.variable(X, 0, P), inputs.Taylor2.variable(Y, 1, P))
+    q0 = np.stack([u.scaled_dofs(dx, dx) for u in U], axis=2)
+    with wcc.Solver2D(inputs.EULER, n, n, P, (-half, half, -half, half), inputs.PERIODIC, precision=wcc.FP64,
+                      limiter=sch == "WCCS") as s:
+        s.set_initial(q0)
+        s.step_until(2.0, CFL[P])
+        rho = s.get_dofs()[:, :, 0, 0]
+        t = s.state()[0]
+    assert abs(t - 2.0) < 1e-12
+    ex = inputs.vortex_conserved(inputs._wrap(X - t, -half, half), inputs._wrap(Y - t, -half, half))[0]
+    return np.abs(rho - ex), X, Y, t
+
+
+def test_table3_fine_meshes(golden_dir):
+    paper = _table3(golden_dir)
+    got = []  # (row, which, ours, paper)
+    for P in (1, 2):
+        for sch in ("LCCS", "WCCS"):
+            for inv in (20, 40):
+                e = _run(sch, P, 10 * inv, 5.0)[0]
+                l1, linf = paper[sch, P, inv]
+                got += [((sch, P, inv), "L1", e.mean(), l1), ((sch, P, inv), "Linf", e.max(), linf)]
+    for sch, inv, which in (("LCCS", 20, ("L1", "Linf")), ("WCCS", 20, ("L1", "Linf")), ("LCCS", 40, ("Linf",))):
+        e, X, Y, t = _run(sch, 3, 20 * inv, 10.0)
+        win = (np.abs(X - t) < 5.0) & (np.abs(Y - t) < 5.0)
+        l1, linf = paper[sch, 3, inv]
+        if "L1" in which:
+            got.append(((sch, 3, inv), "L1 window", e[win].mean(), l1))
+        got.append(((sch, 3, inv), "Linf", e.max(), linf))
+    report = [(row, w, f"{ours:.3e}", f"{pap:.3e}", round(ours / pap - 1.0, 4)) for row, w, ours, pap in got]
+    for r in report:
+        print(*r)
+    bad = [r for r in report if abs(r[4]) >= 0.05]
+    assert not bad, (bad, report)
