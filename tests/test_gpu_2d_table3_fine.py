@@ -33,12 +33,12 @@ def _table3(golden_dir):
     return rows
 
 
-def _run(sch, P, n, half):
+def _run(sch, P, n, half, precision):
     X, Y = inputs._grid2d(n, n, -half, half, -half, half, inputs.PERIODIC)
     dx = 2.0 * half / n
     U = inputs.vortex_conserved(inputs.Taylor2.variable(X, 0, P), inputs.Taylor2.variable(Y, 1, P))
     q0 = np.stack([u.scaled_dofs(dx, dx) for u in U], axis=2)
-    with wcc.Solver2D(inputs.EULER, n, n, P, (-half, half, -half, half), inputs.PERIODIC, precision=wcc.FP64,
+    with wcc.Solver2D(inputs.EULER, n, n, P, (-half, half, -half, half), inputs.PERIODIC, precision=precision,
                       limiter=sch == "WCCS") as s:
         s.set_initial(q0)
         s.step_until(2.0, CFL[P])
@@ -49,17 +49,18 @@ def _run(sch, P, n, half):
     return np.abs(rho - ex), X, Y, t
 
 
-def test_table3_fine_meshes(golden_dir):
+@pytest.mark.parametrize("precision", [wcc.FP64])
+def test_table3_fine_meshes(golden_dir, precision):
     paper = _table3(golden_dir)
     got = []  # (row, which, ours, paper)
     for P in (1, 2):
         for sch in ("LCCS", "WCCS"):
             for inv in (20, 40):
-                e = _run(sch, P, 10 * inv, 5.0)[0]
+                e = _run(sch, P, 10 * inv, 5.0, precision)[0]
                 l1, linf = paper[sch, P, inv]
                 got += [((sch, P, inv), "L1", e.mean(), l1), ((sch, P, inv), "Linf", e.max(), linf)]
     for sch, inv, which in (("LCCS", 20, ("L1", "Linf")), ("WCCS", 20, ("L1", "Linf")), ("LCCS", 40, ("Linf",))):
-        e, X, Y, t = _run(sch, 3, 20 * inv, 10.0)
+        e, X, Y, t = _run(sch, 3, 20 * inv, 10.0, precision)
         win = (np.abs(X - t) < 5.0) & (np.abs(Y - t) < 5.0)
         l1, linf = paper[sch, 3, inv]
         if "L1" in which:
