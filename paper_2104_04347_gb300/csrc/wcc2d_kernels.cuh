@@ -474,20 +474,30 @@ __global__ void __launch_bounds__(TW, 4) halfstep2d_mx(const Step2D a) {
             ff ub[NV];
             linear_cell_mx<SYS, P>(rd, D, ub);
             if (a.law.limiter) {
+                // deviation form: the point value and the vertex values less
+                // the average, taken in float-float and rounded, so that the
+                // limiter's slopes and residuals near smooth extrema are not
+                // float cancellations of O(1) values; the limited point value
+                // comes back as a deviation
                 if constexpr (SYS == EULER) {
                     float vv[4][4], ubf[4];
 #pragma unroll
                     for (int v = 0; v < 4; ++v) {
                         ubf[v] = ub[v].hi;
+                        D[v][0] = -even_correction<P>(D[v]);
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) vv[v][k] = rd.V(k, v, 0);
+                        for (int k = 0; k < 4; ++k) vv[v][k] = wcc::ff_sub(rd.v00(k, v), ub[v]).hi;
                     }
-                    if (!limit_euler<P, float>(D, ubf, vv, lamx, lamy, a.law)) err |= ERR_POSITIVITY;
+                    if (!limit_euler<P, float, true>(D, ubf, vv, lamx, lamy, a.law)) err |= ERR_POSITIVITY;
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) D[v][0] += ubf[v];
                 } else {
                     float vv[4];
+                    D[0][0] = -even_correction<P>(D[0]);
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) vv[k] = rd.V(k, 0, 0);
-                    limit_scalar<P, float>(D[0], ub[0].hi, vv, a.law);
+                    for (int k = 0; k < 4; ++k) vv[k] = wcc::ff_sub(rd.v00(k, 0), ub[0]).hi;
+                    limit_scalar<P, float>(D[0], 0.f, vv, a.law);
+                    D[0][0] += ub[0].hi;
                 }
             }
             // the limiter keeps the cell average (every candidate has mean ubar)

@@ -521,8 +521,12 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
 // RotatedNormal), eigenvectors of cos(theta) dF/dU + sin(theta) dG/dU at the
 // cell average in closed form, the scalar limiter on each characteristic
 // component, and back.  Returns false if the average has non-positive
-// density or pressure.
-template <int P, class T>
+// density or pressure.  With DEV, D[.][0] and vv hold the point and vertex
+// values less the average ub (deviation form): the limiter is unchanged by
+// a common shift of the average, the point value and the vertex values, so
+// the average's projection is left out and the limited D[.][0] is again a
+// deviation from ub (which still sets the eigenvectors).
+template <int P, class T, bool DEV = false>
 __device__ __forceinline__ bool limit_euler(T (&D)[4][nq(P)], const T (&ub)[4], const T (&vv)[4][4], T lamx,
                                             T lamy, const Law2D& law) {
     constexpr int NQ = nq(P);
@@ -586,7 +590,7 @@ __device__ __forceinline__ bool limit_euler(T (&D)[4][nq(P)], const T (&ub)[4], 
         for (int qq = 0; qq < NQ; ++qq) cd[i][qq] = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-            cub[i] += L[i][j] * ub[j];
+            if constexpr (!DEV) cub[i] += L[i][j] * ub[j];
 #pragma unroll
             for (int r = 0; r < 4; ++r) cvv[i][r] += L[i][j] * vv[j][r];
 #pragma unroll
