@@ -12,10 +12,12 @@ paper's printed density errors of the isentropic vortex at t = 2.
   the LCCS-4 L-inf.
 These meshes take minutes in the CPU oracle, seconds here; the GPU's FP64
 path equals the oracle to 1e-11 on the same problems at coarser meshes.
-FP32-mixed is not checked at these meshes: with the limiter at P >= 2 its
-float weights leave the linear ones near the vortex's smooth extrema (WCCS-3
-L-inf 14 x the paper's at 1/40, in the core at r ~ 1), while every row with
-the limiter off matches as FP64 does.
+FP32-mixed (float derivatives, float-float averages, the limiter fed with
+float-float deviations from the average) is held to the rules of the 1/10
+test -- 5 %, 15 % for the limited P = 2 rows -- plus an absolute 1e-8: the
+derivative DOFs are stored in float, and their rounding (2^-24 of scaled
+derivatives of order 1e-2 per half-step) accumulates to about that over the
+~3200 half-steps of the 1/40 runs, the size of the finest printed errors.
 """
 import numpy as np
 import pytest
@@ -53,7 +55,7 @@ def _run(sch, P, n, half, precision):
     return np.abs(rho - ex), X, Y, t
 
 
-@pytest.mark.parametrize("precision", [wcc.FP64])
+@pytest.mark.parametrize("precision", [wcc.FP64, wcc.FP32_MIXED])
 def test_table3_fine_meshes(golden_dir, precision):
     paper = _table3(golden_dir)
     got = []  # (row, which, ours, paper)
@@ -73,5 +75,13 @@ def test_table3_fine_meshes(golden_dir, precision):
     report = [(row, w, f"{ours:.3e}", f"{pap:.3e}", round(ours / pap - 1.0, 4)) for row, w, ours, pap in got]
     for r in report:
         print(*r)
-    bad = [r for r in report if abs(r[4]) >= 0.05]
+    bad = [r for r, (row, w, ours, pap) in zip(report, got) if abs(ours - pap) > allowed(row, pap, precision)]
     assert not bad, (bad, report)
+
+
+def allowed(row, paper, precision):
+    """The deviation from a printed error that a row may show."""
+    if precision == wcc.FP64:
+        return 0.05 * paper
+    sch, P, _ = row
+    return (0.15 if (sch == "WCCS" and P == 2) else 0.05) * paper + 1e-8
