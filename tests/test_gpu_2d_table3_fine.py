@@ -1,5 +1,5 @@
-"""Table 3 (Sec. 5.3) at its finer meshes on the GPU (FP64), against the
-paper's printed density errors of the isentropic vortex at t = 2.
+"""Table 3 (Sec. 5.3) at its finer meshes on the GPU (FP64 and FP32-mixed),
+against the paper's printed density errors of the isentropic vortex at t = 2.
 
 * P <= 2 (LCCS/WCCS-2, -3) at meshes 1/20 and 1/40 on the printed periodic
   domain [-5, 5]^2: L1 and L-inf within 5 %.
