@@ -15,7 +15,9 @@ outside it:
   * the smoothness indicator of Eq. 2DSmoothIndicator against quadrature;
   * order P + 1 against exact solutions (advection; Burgers before its
     shock), and Sod's tube along x against the exact Riemann solution with
-    the rotated limiter on (first-order L1 rate, rows kept identical)."""
+    the rotated limiter on (first-order L1 rate, rows kept identical);
+  * the limited advection half-step commutes with adding a constant (the
+    limiter sees differences only), on rough data where it is active."""
 import math
 import os
 
@@ -486,3 +488,24 @@ def test_sod_along_x_against_the_exact_riemann_solution():
         assert all(0.6 < o < 1.2 for o in orders), (P, orders)
     for N in (100, 200, 400):
         assert errs[3, N] < errs[2, N] < errs[1, N], errs
+
+
+@pytest.mark.parametrize("P", [1, 2, 3])
+def test_limited_advection_commutes_with_a_constant_shift(P):
+    # linear advection is unchanged by u -> u + c, and the limiter of Sec. 3.2
+    # sees the data only through differences (one-sided slopes, vertex
+    # residuals, derivatives) and keeps the average: the limited half-step
+    # of the shifted data is the shifted half-step, on rough data where the
+    # weights are far from the linear ones
+    rng = np.random.default_rng(P)
+    n = 20
+    q = 0.3 * rng.standard_normal((n, n, 1, inputs.nq2d(P)))
+    law = oracle.make_law2d(oracle.ADVECTION, P, limiter=True, ax=0.8, ay=-0.55)
+    for parity in (0, 1):
+        a = oracle.halfstep2d(law, parity, q, 0.2, 0.15)
+        for c in (1.0, -37.5):
+            qc = q.copy()
+            qc[..., 0] += c
+            b = oracle.halfstep2d(law, parity, qc, 0.2, 0.15)
+            b[..., 0] -= c
+            assert np.max(np.abs(b - a)) <= 1e-12 * (1.0 + abs(c)), (P, parity, c)
