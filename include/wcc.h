@@ -98,8 +98,14 @@ void wcc_default_options(wcc_options* opt);
  * otherwise).  The paper prints CFL numbers up to P = 3; the von Neumann
  * limits of the linear scheme (Sec. 2.3) are 0.282, 0.212 and 0.185 at
  * P = 4, 5, 6, and the CFL number must stay below them.
- * N >= 4; bc is WCC_BC_PERIODIC or WCC_BC_TRANSMISSIVE.  opt may be NULL.
- * On success *out holds the handle (free with wcc_destroy). */
+ * 4 <= N <= 2^31; bc is WCC_BC_PERIODIC or WCC_BC_TRANSMISSIVE.  opt may
+ * be NULL.  On success *out holds the handle (free with wcc_destroy).
+ * Allocates, on the current device, two stages (FP64: nv (P+1) doubles per
+ * cell; FP32 variants: nv (P+2) floats), a host-layout staging buffer and
+ * the device-side state (wcc_device_bytes reports the total).  Errors:
+ * WCC_E_INVAL (arguments), WCC_E_CUDA (no device, stream), WCC_E_NOMEM (the
+ * state does not fit, e.g. N = 2^31 at P = 6 in FP64); *out is set to NULL
+ * on every error but a NULL out. */
 int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domain[2], int bc,
                const wcc_options* opt);
 
