@@ -4,7 +4,8 @@ element by element, on the same seeded inputs with the same half-step sizes.
 Bound (see tests/gpu_common.py): per cell max(1e-11 x scale, 50 x the
 oracle's own spread under few-ulp input perturbations); where the scheme is
 well conditioned this is the plain 1e-11 bound, asserted separately for the
-limiter-off runs."""
+limiter-off runs.  Every comparison also caps the share of entries the
+spread term excuses and the largest plain difference (the *_CAPS below)."""
 import math
 
 import numpy as np
@@ -12,13 +13,35 @@ import pytest
 
 import oracle
 from paper_2104_04347_gb300 import inputs, wcc
-from tests.gpu_common import (TOL64, gpu_run, gpu_solver, law_of, oracle_run, oracle_spread, parity_violation,
-                              scaled_error, trajectory_check)
+from tests.gpu_common import (TOL64, assert_parity, gpu_run, gpu_solver, law_of, merge, oracle_run, oracle_spread,
+                              parity_report, scaled_error, trajectory_check)
 
 pytestmark = pytest.mark.gpu
 
 TILE = 127  # new cells per CTA
 CFL = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2}
+
+# Caps on what the spread term of the bound may excuse (gpu_common.Parity):
+# the share of entries beyond 1e-11 x scale and the largest plain relative
+# difference, about 2-3 x the values measured on GB300.  Trajectories not
+# listed are well conditioned and held to the plain 1e-11 bound (nothing
+# excused); the listed ones carry the limiter's conditioning near shocks,
+# jumps and (P = 2) smooth extrema.  Per half-step the spread term excuses
+# at most 0.02 % of the entries, none by more than 1.2e-11.
+PLAIN = dict(excused_max=0.0, raw_max=TOL64)
+TRAJECTORY_CAPS = {
+    (inputs.BURGERS, 2, inputs.PERIODIC): dict(excused_max=0.02, raw_max=1e-9),
+    (inputs.BURGERS, 2, inputs.TRANSMISSIVE): dict(excused_max=0.03, raw_max=1e-9),
+    (inputs.BURGERS, 3, inputs.PERIODIC): dict(excused_max=0.02, raw_max=1e-9),
+    (inputs.BURGERS, 3, inputs.TRANSMISSIVE): dict(excused_max=0.02, raw_max=1e-9),
+    (inputs.BURGERS, 4, inputs.TRANSMISSIVE): dict(excused_max=0.002, raw_max=1e-10),
+    (inputs.EULER, 2, inputs.TRANSMISSIVE): dict(excused_max=0.10, raw_max=3e-4),
+    (inputs.EULER, 3, inputs.TRANSMISSIVE): dict(excused_max=0.06, raw_max=1e-7),
+    (inputs.EULER, 4, inputs.TRANSMISSIVE): dict(excused_max=0.05, raw_max=2e-8),
+}
+STEP_CAPS = dict(excused_max=0.002, raw_max=5e-11)
+EDGE_CAPS = dict(excused_max=0.06, raw_max=1e-10)
+FULL_SIZE_CAPS = dict(excused_max=0.02, raw_max=1e-9)
 
 
 def _problem(system, P, N, bc):
@@ -53,8 +76,8 @@ def test_trajectory_100_halfsteps(case):
     assert len(dts) == 100 and parity == 0
     ref, tref, _ = oracle_run(pr, dts)
     assert abs(t - tref) <= 1e-14 * tref and q.shape == ref.shape
-    viol, err = trajectory_check(pr, q, dts)
-    assert viol <= 1.0, (viol, err)
+    rep = trajectory_check(pr, q, dts)
+    assert_parity(rep, **TRAJECTORY_CAPS.get(case, PLAIN))
 
 
 @pytest.mark.parametrize("case", ALL, ids=_id)
@@ -65,7 +88,7 @@ def test_every_halfstep_from_gpu_state(case):
     N = 3 * TILE + 17
     pr = _problem(system, P, N, bc)
     law = law_of(pr)
-    worst = 0.0
+    reps = []
     with gpu_solver(pr) as s:
         s.set_initial(pr.q0)
         prev = s.get_dofs()
@@ -80,9 +103,9 @@ def test_every_halfstep_from_gpu_state(case):
 
             ref = run(prev)
             spread = oracle_spread(run, prev, ref, seed=n)
-            worst = max(worst, parity_violation(cur, ref, spread))
+            reps.append(parity_report(cur, ref, spread))
             prev = cur
-    assert worst <= 1.0, worst
+    assert_parity(merge(reps), **STEP_CAPS)
 
 
 @pytest.mark.parametrize("system", [inputs.ADVECTION, inputs.BURGERS, inputs.EULER])
@@ -126,8 +149,7 @@ def test_config1_advection_exact_translate():
 def test_small_and_tile_edge_sizes(N, bc):
     pr = _problem(inputs.EULER, 3, N, bc)
     q, dts, _, _ = gpu_run(pr, 24, 0.2)
-    viol, _ = trajectory_check(pr, q, dts)
-    assert viol <= 1.0
+    assert_parity(trajectory_check(pr, q, dts), **EDGE_CAPS)
 
 
 @pytest.mark.parametrize("bc", [inputs.PERIODIC, inputs.TRANSMISSIVE])
@@ -210,6 +232,7 @@ def test_full_size_euler_sampled_windows():
     centres = [N // 2, N // 2 - 40, N // 2 + 40, 3, N - 3] + list(rng.integers(100, N - 100, 3))
     half = k // 2 + 8
     law = law_of(pr)
+    reps = []
     for c in centres:
         lo, hi = max(0, c - 2 * half), min(N + 1, c + 2 * half)
 
@@ -223,5 +246,6 @@ def test_full_size_euler_sampled_windows():
         # compare cells at least `half` away from an artificial window edge
         a = lo if lo == 0 else lo + half
         b = hi if hi == N + 1 else hi - half
-        viol = parity_violation(q[a:b], ref[a - lo:b - lo], spread[a - lo:b - lo])
-        assert viol <= 1.0, (c, viol)
+        reps.append(parity_report(q[a:b], ref[a - lo:b - lo], spread[a - lo:b - lo]))
+        assert reps[-1].violation <= 1.0, (c, reps[-1])
+    assert_parity(merge(reps), **FULL_SIZE_CAPS)
