@@ -26,6 +26,7 @@ exchange step here); value = cell-updates of all ranks / max time.
 from __future__ import annotations
 
 import argparse
+import math
 import json
 import os
 import statistics
@@ -56,6 +57,7 @@ def parse():
     ap.add_argument("--log2n", type=int, default=22)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--batch", type=int, default=1, help="also time the 4096-instance batch (1/0)")
+    ap.add_argument("--tb", type=int, default=1, help="also time two half-steps per launch (1/0)")
     ap.add_argument("--sweep", action="store_true", help="precision / convergence sweep (density wave) instead")
     ap.add_argument("--sweep-max-log2n", type=int, default=16)
     ap.add_argument("--workloads", action="store_true",
@@ -65,6 +67,8 @@ def parse():
     ap.add_argument("--n2d", type=int, default=2048, help="cells per axis of the 2D workload")
     ap.add_argument("--workloads2d", action="store_true",
                     help="the paper's 2D Riemann problems at 1200^2 to t_end instead")
+    ap.add_argument("--burgers", action="store_true",
+                    help="the Burgers workload: N = 2^10..2^20, P = 1..4, FP64 and FP32-mixed")
     ap.add_argument("--high-order", action="store_true",
                     help="FP64 Euler half-steps at P = 3..6 (seeded Riemann data) instead")
     return ap.parse_args()
@@ -147,14 +151,14 @@ def peaks():
 # launch at N = 2^21, DFMA counted as 2) divided by the cells of the launch:
 # (2 x 692675342 + 306816515 + 163894018) / 2097152.5.
 FP64_FLOPS_PER_CELL_UPDATE = 885.04
-# DRAM bytes (read + write) of one FP64 launch, from the same capture
-# (201425408 + 149216768 at N = 2^21), scaled by cells to N = 2^22.
-FP64_TRAFFIC_PER_CELL = (201425408 + 149216768) / 2097152.5
-# DRAM bytes (read + write) of one FP32-mixed launch per cell, from an ncu
-# capture of halfstep_mixed2<EULER, 3> at N = 2^21 (125892096 + 73494272; the
-# current kernel: 6 CTAs per SM, parked float-float terms, one-barrier
-# reduction), scaled by cells to N = 2^22.
-MIXED_TRAFFIC_PER_CELL = (125892096 + 73494272) / 2097152.5
+# DRAM bytes (read + write) of one launch at the bench size (N = 2^22), from
+# one ncu capture each (dram__bytes_read.sum + dram__bytes_write.sum, one
+# launch after three warm-up launches of the same kernel, graphs of 32
+# half-steps; profiles/halfstep_mixed_euler_p3.md).  The writes of the last
+# tiles are still in L2 when the kernel ends, so the figure is a little below
+# the algorithmic one read + one write of the state.
+FP64_TRAFFIC_2_22 = 402869760 + 352474368
+MIXED_TRAFFIC_2_22 = 251710976 + 200019456
 # FP32 flops per cell-update of the same kernel, from the same capture's
 # executed paired instructions (sm__sass_thread_inst_executed_op_f{add2,ffma2,
 # fmul2}): 158.1 FADD2, 144.6 FFMA2 and 81.8 FMUL2 thread instructions per
@@ -342,7 +346,10 @@ def l1_check(log2n_small=12, halfsteps=2000):
     oracle.set_threads(os.cpu_count() or 1)
     pr = inputs.euler_riemann_seeded(1 << log2n_small, P)
     law = oracle.make_law(oracle.EULER, P, limiter=True, bc=oracle.TRANSMISSIVE)
-    out = {"workload": f"euler1d-riemann-N2^{log2n_small}-P{P}, {halfsteps} half-steps, cfl {CFL}"}
+    out = {"workload": f"euler1d-riemann-N2^{log2n_small}-P{P}, {halfsteps} half-steps, cfl {CFL}",
+           "N": 1 << log2n_small, "halfsteps": halfsteps,
+           "note": "the bench grid itself (N = 2^22, 128 half-steps) is checked on sampled windows by "
+                   "tests/test_gpu_mixed.py::test_mixed_full_size_sampled_windows"}
     for name, prec in (("mixed", wcc.FP32_MIXED), ("fp64", wcc.FP64)):
         with wcc.Solver(pr.system, pr.N, P, (pr.x_l, pr.x_r), pr.bc, precision=prec) as s:
             s.set_initial(pr.q0)
@@ -415,6 +422,28 @@ def batch_bench(stream, steps, warmup, p3_rate, barrier):
             "single_grid_p3": p3_rate, "single_over_batch": single / value}
 
 
+def tb_bench(pr, stream, steps, warmup, barrier, dev, cells_per_step, cells_per_launch, pk):
+    """The headline workload with two half-steps per launch (tb_depth = 2):
+    one read and one write of the state per pair, so 60 B per cell-update in
+    FP32-mixed; same steps of 32 half-steps (16 launches), CUDA events."""
+    from paper_2104_04347_gb300 import wcc
+
+    with wcc.Solver(pr.system, pr.N, P, (pr.x_l, pr.x_r), pr.bc, precision=wcc.FP32_MIXED,
+                    graph_chunk=HALFSTEPS_PER_STEP, stream=stream.cuda_stream, tb_depth=2) as s:
+        s.set_initial(pr.q0)
+        total_ms, step_ms, launches = time_solver(s, stream, steps, warmup, barrier)
+        pairs, fallbacks, nu2 = s.tb_stats()
+    value = job_throughput(cells_per_step * steps, total_ms * 1e-3, dev)
+    kernel_ms = statistics.median(step_ms) / HALFSTEPS_PER_STEP
+    bpc = bytes_per_cell_update("mixed") / 2
+    gbs = bpc * cells_per_launch / (kernel_ms * 1e-3) / 1e9
+    return {"value": value, "unit": "cell-updates/s", "ms_per_step": total_ms / steps, "steps": steps,
+            "ms_per_halfstep": kernel_ms, "gpu_launches": launches, "bytes_per_cell_update": bpc,
+            "hbm_gbs": gbs, "hbm_frac": gbs / pk["hbm_gbs"], "pairs": pairs, "fallbacks": fallbacks,
+            "nu2_max": nu2, "cfl": CFL,
+            "dt_rule": "one dt per pair from the first stage's bound; second half-step's CFL number checked"}
+
+
 def run_wcc(args, rank, world):
     import torch
 
@@ -470,16 +499,19 @@ def run_wcc(args, rank, world):
             tf = FP64_FLOPS_PER_CELL_UPDATE * cells_per_launch / (kernel_ms * 1e-3) / 1e12
             res["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                "frac": tf / FP64_PEAK_TFLOPS,
-                               "traffic": FP64_TRAFFIC_PER_CELL * cells_per_launch if args.log2n == 22 else None,
+                               "traffic": FP64_TRAFFIC_2_22 if args.log2n == 22 else None,
                                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s (recipe)",
                                "flops_per_cell_update": FP64_FLOPS_PER_CELL_UPDATE, "kernel_ms": kernel_ms,
                                "hbm_frac": hbm["frac"]}
         else:
-            if MIXED_TRAFFIC_PER_CELL and args.log2n == 22:
-                hbm["traffic"] = MIXED_TRAFFIC_PER_CELL * cells_per_launch
+            if args.log2n == 22:
+                hbm["traffic"] = MIXED_TRAFFIC_2_22
             res["roofline"] = hbm
         results[name] = res
         solver.close()
+    if args.tb:
+        results["mixed_tb2"] = tb_bench(pr, stream, max(2, min(args.steps, 10)), args.warmup, barrier, dev,
+                                        cells_per_step, cells_per_launch, pk)
     if args.batch:
         results["batch"] = batch_bench(stream, max(2, min(args.steps, 5)), args.warmup,
                                        results["mixed"]["value"] / world, barrier)
@@ -856,6 +888,104 @@ def high_order_bench(args):
               f"{r['oracle_cell_updates_per_s'] / 1e6:.2f} M ({r['oracle_cores']} cores) |")
 
 
+# Floating-point operations per cell-update of the oracle's half-step as the
+# oracle writes it (derivative form, binomial Leibniz sums, each parent's
+# Cauchy-Kovalewski table counted once), limiter on: the output of
+# `python oracle/count_flops.py 1 P 1` (Burgers) and `2 P 1` (Euler).
+ORACLE_FLOPS = {(1, 1): 93.0, (1, 2): 191.0, (1, 3): 314.0, (1, 4): 502.0,
+                (2, 1): 517.0, (2, 2): 847.0, (2, 3): 1252.0, (2, 4): 1852.0, (2, 5): 2725.0, (2, 6): 3934.0}
+BURGERS_CFL = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2}
+
+
+def burgers_bench(args):
+    """The Burgers workload (u_t + (u^2/2)_x = 0, periodic [0, 2 pi], seeded
+    u0 = 0.5 + 8 Fourier modes, limiter on) at N = 2^10, 2^14, 2^18, 2^20,
+    P = 1..4 (CFL 0.4 / 0.3 / 0.25 / 0.2), FP64 and FP32-mixed.  Per case:
+    cell-updates/s over graphs of 32 half-steps with CUDA events (inputs
+    resident; from the initial data: the kernels' work does not depend on
+    the state), the HBM fraction at the algorithmic bytes (one read and one
+    write of the state: 16 (P + 1) B in FP64, 2 (8 + 4 P) B in FP32-mixed)
+    and, for FP64, the fraction of the FP64 peak at the oracle's flop count;
+    time to 2 t_s (past the shock) for N <= 2^18; and the oracle on the host
+    cores on a bounded sample (N = 2^14, CFL half-steps for about
+    cpu_seconds / 8 per degree)."""
+    import torch
+
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    pk, pk_kind = peaks()
+    stream = torch.cuda.Stream()
+    clocks = ClockSampler()
+    clocks.start()
+    rows = []
+    for P in (1, 2, 3, 4):
+        cfl = BURGERS_CFL[P]
+        for log2n in (10, 14, 18, 20):
+            N = 1 << log2n
+            pr = inputs.burgers_fourier(N, P)
+            t_s = inputs.shock_time(inputs.burgers_fourier_data())
+            for prec, name in ((wcc.FP64, "fp64"), (wcc.FP32_MIXED, "fp32-mixed")):
+                with wcc.Solver(pr.system, N, P, (pr.x_l, pr.x_r), pr.bc, precision=prec,
+                                stream=stream.cuda_stream) as s:
+                    s.set_initial(pr.q0)
+                    for _ in range(args.warmup):
+                        s.step(HALFSTEPS_PER_STEP, cfl)
+                    s.synchronize()
+                    reps = max(args.steps, 4 if log2n >= 18 else 40)
+                    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+                    with torch.cuda.stream(stream):
+                        ev[0].record(stream)
+                        for _ in range(reps):
+                            s.step(HALFSTEPS_PER_STEP, cfl)
+                        ev[1].record(stream)
+                    s.synchronize()
+                    ms = ev[0].elapsed_time(ev[1]) / (reps * HALFSTEPS_PER_STEP)
+                    tts = None
+                    if log2n <= 18:
+                        s.set_initial(pr.q0)
+                        t0 = time.perf_counter()
+                        k = s.step_until(2.0 * t_s, cfl)
+                        tts = {"t_end": 2.0 * t_s, "halfsteps": k, "seconds": time.perf_counter() - t0}
+                rate = N / (ms * 1e-3)
+                bpc = 16 * (P + 1) if prec == wcc.FP64 else 2 * (8 + 4 * P)
+                row = {"workload": f"burgers1d-fourier8-N2^{log2n}-P{P}-periodic-cfl{cfl}", "N": N, "P": P,
+                       "precision": name, "ms_per_halfstep": ms, "cell_updates_per_s": rate,
+                       "bytes_per_cell_update": bpc, "hbm_gbs": bpc * rate / 1e9,
+                       "hbm_frac": bpc * rate / 1e9 / pk["hbm_gbs"], "time_to_2ts": tts}
+                if prec == wcc.FP64:
+                    tf = ORACLE_FLOPS[(1, P)] * rate / 1e12
+                    row.update({"oracle_flops_per_cell_update": ORACLE_FLOPS[(1, P)], "fp64_tflops": tf,
+                                "fp64_frac": tf / FP64_PEAK_TFLOPS})
+                rows.append(row)
+                print(json.dumps(row), flush=True)
+    clk = clocks.stop()
+    # the oracle on the host cores (bounded sample)
+    import oracle
+    oracle.set_threads(os.cpu_count() or 1)
+    cpu = {}
+    for P in (1, 2, 3, 4):
+        win = inputs.burgers_fourier(1 << 14, P)
+        sol = oracle.Solver(oracle.make_law(oracle.BURGERS, P, limiter=True), win.q0, win.dx)
+        t0 = time.perf_counter()
+        k = 0
+        while k < 2 or time.perf_counter() - t0 < args.cpu_seconds / 8:
+            sol.step_cfl(1, BURGERS_CFL[P])
+            k += 1
+        cpu[P] = win.N * k / (time.perf_counter() - t0)
+    print(json.dumps({"clocks": clk, "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": pk_kind,
+                      "oracle_cell_updates_per_s": cpu, "oracle_cores": oracle.get_threads(),
+                      "oracle_sample": "N = 2^14, CFL half-steps from the initial data"}), flush=True)
+    print("| P | N | precision | ms / half-step | cell-updates/s | of HBM | of FP64 peak (oracle flops) | "
+          "time to 2 t_s | oracle (host) |")
+    print("|---|---|---|---|---|---|---|---|---|")
+    for r in rows:
+        fr = f"{r['fp64_frac']:.3f}" if "fp64_frac" in r else ""
+        tt = "" if r["time_to_2ts"] is None else f"{r['time_to_2ts']['seconds']:.3f} s ({r['time_to_2ts']['halfsteps']})"
+        print(f"| {r['P']} | 2^{int(math.log2(r['N']))} | {r['precision']} | {r['ms_per_halfstep']:.4f} | "
+              f"{r['cell_updates_per_s'] / 1e9:.2f} G | {r['hbm_frac']:.3f} | {fr} | {tt} | "
+              f"{cpu[r['P']] / 1e6:.2f} M |")
+
+
 def paper_workloads_2d(n=1200):
     """The 2D Riemann problems of Sec. 5.3 at the paper's resolution (n x n
     cells on [-1, 1]^2, transmissive): configuration 1 (four shocks) to
@@ -905,6 +1035,9 @@ def main():
         return
     if args.high_order:
         high_order_bench(args)
+        return
+    if args.burgers:
+        burgers_bench(args)
         return
     if args.two_d:
         two_d_bench(args)

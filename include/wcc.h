@@ -75,7 +75,21 @@ enum {
  *   value is used for P = 1, where the paper does not state it),
  *   eps = 1e-40 (Eq. 1D2ndOrderWeights), gamma = 1.4, adv_speed = 1,
  *   graph_chunk = 32 (half-steps per captured CUDA graph; 0 disables graphs),
- *   cuda_stream = NULL (the handle creates its own non-blocking stream). */
+ *   tb_depth = 1, tb_cfl_growth = 0.1 (see below),
+ *   cuda_stream = NULL (the handle creates its own non-blocking stream).
+ *
+ * tb_depth (temporal blocking): half-steps per pass over the state in
+ * device memory, 1 or 2 (0 reads as 1).  With 2 (FP32 variants only,
+ * WCC_E_INVAL with WCC_FP64 or a batch), wcc_step advances the stage two
+ * half-steps per launch, reading and writing the state once for both.  The
+ * pair shares one dt, the CFL step of its first stage (dt = cfl dx /
+ * a_max(t^n)); the second half-step's own CFL number dt a_max(t^{n+1/2}) /
+ * dx is checked on the device and must not exceed min(cfl (1 +
+ * tb_cfl_growth), wcc_stability_limit(P)).  A pair that would is not taken:
+ * wcc_step then advances from the last stage it reached with single CFL
+ * half-steps (wcc_tb_stats counts these fallbacks).  The realised dt of
+ * every half-step is in the history as usual.  With tb_depth = 2, wcc_step
+ * waits for its work before it returns (to check the pairs). */
 typedef struct {
     int precision;
     int limiter;
@@ -84,8 +98,9 @@ typedef struct {
     double gamma;
     double adv_speed;
     int graph_chunk;
-    int reserved;
+    int tb_depth;
     void* cuda_stream; /* cudaStream_t to run on, or NULL */
+    double tb_cfl_growth;
 } wcc_options;
 
 typedef struct wcc_ctx* wcc_handle;
@@ -120,8 +135,15 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count);
 /* Advance nsteps half-steps with dt = cfl * dx / a_max, a_max the largest
  * characteristic speed (|a|, |u| or |u| + c) over the centre point values of
  * the stage being advanced, evaluated on the device (no host round trip).
- * cfl > 0.  Asynchronous on the handle's stream. */
+ * cfl > 0.  Asynchronous on the handle's stream (with tb_depth = 2: the
+ * half-steps go in pairs and the call waits for them, see wcc_options). */
 int wcc_step(wcc_handle h, int64_t nsteps, double cfl);
+
+/* Two-half-step launches (tb_depth = 2) since wcc_set_initial: *pairs (may
+ * be NULL) receives the pairs taken, *fallbacks the pairs refused by the CFL
+ * check and re-done as single half-steps, *nu2_max the largest CFL number a
+ * taken pair's second half-step had.  Synchronises. */
+int wcc_tb_stats(wcc_handle h, int64_t* pairs, int64_t* fallbacks, double* nu2_max);
 
 /* Advance nsteps half-steps with the given half-step sizes (host array of
  * nsteps doubles, each > 0).  Asynchronous; dts is read before return. */
@@ -208,6 +230,25 @@ int wcc_batch_device_bytes(wcc_batch b, int64_t* bytes);
 const char* wcc_batch_last_error(wcc_batch b);
 void wcc_batch_destroy(wcc_batch b);
 
+/* Linear stability limit of degree P (1..6): the largest CFL number nu with
+ * which one half-step of linear advection (limiter off) keeps every Fourier
+ * mode bounded -- every eigenvalue of the half-step amplification matrix
+ * G(theta) = M_L e^{-i theta/2} + M_R e^{i theta/2} in the closed unit disk
+ * (Sec. 2.3, Eqs. 1DSchemeMatrixForm, 1DFourierAnalysis,
+ * LinearStabilityCondition), found by bisection over 2047 values of theta.
+ * Host code, no device needed; computed on the first call for each P (about
+ * 0.1-1 s) and kept.  The paper's Table 1 prints 0.5, 0.384 and 0.304 for
+ * P = 1, 2, 3; this scan gives 0.5, 0.384 and 0.289 (at 0.304 the radius
+ * exceeds 1 by about 1e-4).  Errors: WCC_E_INVAL (P out of range, NULL). */
+int wcc_stability_limit(int P, double* nu);
+
+/* Default CFL number (half-step nu = a_max dt / dx) of degree P (1..6):
+ * the values the paper's numerical tests use for P = 1, 2, 3 (0.4, 0.3,
+ * 0.25; Sec. 5), and for P >= 4, where the paper gives none, 0.8 of
+ * wcc_stability_limit(P) rounded down to two digits (0.22, 0.16, 0.14 for
+ * P = 4, 5, 6).  Errors: WCC_E_INVAL. */
+int wcc_default_cfl(int P, double* cfl);
+
 /* Measured fused-multiply-add throughput of the current device in TFLOP/s
  * (FP64 for WCC_FP64, FP32 for WCC_FP32_MIXED): a grid of 8 CTAs per SM,
  * 8 independent FMA chains per thread, timed with CUDA events (~40 ms).
@@ -227,7 +268,7 @@ int wcc_measure_fp_peak(int precision, double* tflops);
  * buffers the caller owns, and calls no cudaMalloc, cudaFree or other
  * allocating routine.
  *
- * Arguments: system, P (1..4), bc, N, domain as in wcc_create; opt may be
+ * Arguments: system, P (1..4), bc, N (4..2^31), domain as in wcc_create; opt may be
  * NULL (opt->precision must be WCC_FP64; opt->cuda_stream is the stream,
  * NULL = legacy default stream).  parity is the stage parity of the input.
  * stage_a (input) and stage_b are device buffers of nv*(P+1) FP64 planes,
@@ -243,7 +284,10 @@ int wcc_measure_fp_peak(int precision, double* tflops);
  * it until the process exits.  nsteps > WCC_STATIC_MAX_HALFSTEPS returns
  * WCC_E_CAPACITY.  The first call on a device looks up the array's device
  * address (cudaGetSymbolAddress, with that device current); make that first
- * call before any stream capture.  All calls share the array and each call
+ * call before any stream capture.  The lookup is repeated when the device's
+ * context has changed since (e.g. after a cudaDeviceReset, which reloads the
+ * library's device code), so the first call after a reset must also come
+ * before any capture.  All calls share the array and each call
  * clears its state first, so calls that overlap on the GPU (other streams,
  * other host threads) race and must not be made.
  *

@@ -74,13 +74,10 @@ void wcc2d_default_options(wcc2d_options* opt);
  * degree 1 <= P <= 3 (order P + 1).  nx, ny >= 4 and at most 2^15 each;
  * bc is WCC_BC_PERIODIC or WCC_BC_TRANSMISSIVE.  opt may be NULL.
  * Allocates two stages, a host-layout staging buffer and the device-side
- * state on the current device (wcc2d_device_bytes reports the total).  The
- * half-step kernel's per-thread stack can exceed the context's default
- * limit; create raises cudaLimitStackSize of the calling process's current
- * context to what the kernel needs (never lowers it), a process-wide effect
- * that outlives the handle.  Errors: WCC_E_INVAL, WCC_E_CAPACITY (nx or ny
- * above 2^15), WCC_E_NOMEM, WCC_E_CUDA (no device, stream or stack
- * limit); *out is set to NULL on every error but a NULL out. */
+ * state on the current device (wcc2d_device_bytes reports the total); it
+ * changes no context-wide setting.  Errors: WCC_E_INVAL, WCC_E_CAPACITY (nx
+ * or ny above 2^15), WCC_E_NOMEM, WCC_E_CUDA (no device or stream); *out is
+ * set to NULL on every error but a NULL out. */
 int wcc2d_create(wcc2d_handle* out, int system, int64_t nx, int64_t ny, int P, const double domain[4], int bc,
                  const wcc2d_options* opt);
 

@@ -189,22 +189,6 @@ int wcc2d_create(wcc2d_handle* out, int system, int64_t nx, int64_t ny, int P, c
         }
         h->own_stream = true;
     }
-    // The half-step kernel's spill stack can exceed the context's default
-    // per-thread stack limit; raise the limit (of this process's context) to
-    // what the kernel needs before its first launch.
-    {
-        size_t need = 0, have = 0;
-        const cudaError_t qe = h->mixed ? halfstep2d_mx_local_bytes(system, P, &need)
-                                        : halfstep2d_local_bytes(system, P, h->fp32 != 0, &need);
-        if (qe != cudaSuccess ||
-            cudaDeviceGetLimit(&have, cudaLimitStackSize) != cudaSuccess ||
-            (need > have && cudaDeviceSetLimit(cudaLimitStackSize, (need + 255) / 256 * 256) != cudaSuccess)) {
-            cudaGetLastError();
-            if (h->own_stream) cudaStreamDestroy(h->stream);
-            delete h;
-            return fail2(nullptr, WCC_E_CUDA, "could not size the per-thread stack for the 2D kernel");
-        }
-    }
     const long long maxx = nx + 1, maxy = ny + 1;
     const long long align = h->fp32 ? 32 : 16;  // 128-byte aligned rows
     h->pitch = (maxx + align - 1) / align * align;

@@ -5,7 +5,4 @@ namespace wcc2d {
 cudaError_t launch_halfstep2d_euler_f32(int P, const Step2D& a, cudaStream_t stream) {
     return launch_halfstep2d_sys<EULER, float>(P, a, stream);
 }
-cudaError_t halfstep2d_local_bytes_euler_f32(int P, size_t* bytes) {
-    return halfstep2d_local_bytes_sys<EULER, float>(P, bytes);
-}
 }  // namespace wcc2d

@@ -5,7 +5,4 @@ namespace wcc2d {
 cudaError_t launch_halfstep2d_euler_f64(int P, const Step2D& a, cudaStream_t stream) {
     return launch_halfstep2d_sys<EULER, double>(P, a, stream);
 }
-cudaError_t halfstep2d_local_bytes_euler_f64(int P, size_t* bytes) {
-    return halfstep2d_local_bytes_sys<EULER, double>(P, bytes);
-}
 }  // namespace wcc2d

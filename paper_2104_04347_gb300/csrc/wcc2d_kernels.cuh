@@ -313,25 +313,6 @@ cudaError_t launch_halfstep2d_t(const Step2D& a, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
-// Per-thread local memory (spill stack) of the half-step kernel.
-template <int SYS, int P, class T>
-cudaError_t halfstep2d_local_bytes_t(size_t* bytes) {
-    cudaFuncAttributes attr;
-    cudaError_t e = cudaFuncGetAttributes(&attr, halfstep2d<SYS, P, T, strip_width<SYS, P, T>()>);
-    if (e == cudaSuccess) *bytes = attr.localSizeBytes;
-    return e;
-}
-
-template <int SYS, class T>
-cudaError_t halfstep2d_local_bytes_sys(int P, size_t* bytes) {
-    switch (P) {
-        case 1: return halfstep2d_local_bytes_t<SYS, 1, T>(bytes);
-        case 2: return halfstep2d_local_bytes_t<SYS, 2, T>(bytes);
-        case 3: return halfstep2d_local_bytes_t<SYS, 3, T>(bytes);
-        default: return cudaErrorInvalidValue;
-    }
-}
-
 template <int SYS, class T>
 cudaError_t launch_halfstep2d_sys(int P, const Step2D& a, cudaStream_t stream) {
     switch (P) {
@@ -632,13 +613,11 @@ cudaError_t launch_stage_rate2d_mx(int system, int P, const float* planes, long 
                                    int ny, const Law2D& law, double dx, double dy, DevState2D* st, cudaStream_t stream);
 cudaError_t launch_convert2d_mx(int P, bool to_planes, double* aos, float* planes, int nx, int ny, int nv,
                                 long long pitch, long long plane, cudaStream_t stream);
-cudaError_t halfstep2d_mx_local_bytes(int system, int P, size_t* bytes);
 }  // namespace wcc2d
 
 namespace wcc2d {
 // Instantiated in wcc2d_scalar.cu, wcc2d_euler_f64.cu, wcc2d_euler_f32.cu.
 cudaError_t launch_halfstep2d(int system, int P, bool fp32, const Step2D& a, cudaStream_t stream);
-cudaError_t halfstep2d_local_bytes(int system, int P, bool fp32, size_t* bytes);
 cudaError_t launch_stage_rate2d(int system, bool fp32, const void* planes, long long pitch, long long plane, int nx,
                                 int ny, int nq_, const Law2D& law, double dx, double dy, DevState2D* st,
                                 cudaStream_t stream);

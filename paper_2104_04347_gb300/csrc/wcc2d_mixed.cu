@@ -35,23 +35,6 @@ cudaError_t rate_mx_sys(int P, const float* planes, long long pitch, long long p
     }
 }
 
-template <int SYS, int P>
-cudaError_t local_mx_t(size_t* bytes) {
-    cudaFuncAttributes attr;
-    cudaError_t e = cudaFuncGetAttributes(&attr, halfstep2d_mx<SYS, P, strip_width_mx<SYS, P>()>);
-    if (e == cudaSuccess) *bytes = attr.localSizeBytes;
-    return e;
-}
-
-template <int SYS>
-cudaError_t local_mx_sys(int P, size_t* bytes) {
-    switch (P) {
-        case 1: return local_mx_t<SYS, 1>(bytes);
-        case 2: return local_mx_t<SYS, 2>(bytes);
-        case 3: return local_mx_t<SYS, 3>(bytes);
-        default: return cudaErrorInvalidValue;
-    }
-}
 }  // namespace
 
 cudaError_t launch_halfstep2d_mx(int system, int P, const Step2D& a, cudaStream_t stream) {
@@ -94,15 +77,6 @@ cudaError_t launch_convert2d_mx(int P, bool to_planes, double* aos, float* plane
             return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
-}
-
-cudaError_t halfstep2d_mx_local_bytes(int system, int P, size_t* bytes) {
-    switch (system) {
-        case ADVECTION: return local_mx_sys<ADVECTION>(P, bytes);
-        case BURGERS: return local_mx_sys<BURGERS>(P, bytes);
-        case EULER: return local_mx_sys<EULER>(P, bytes);
-        default: return cudaErrorInvalidValue;
-    }
 }
 
 }  // namespace wcc2d

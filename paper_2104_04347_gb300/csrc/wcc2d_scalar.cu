@@ -6,23 +6,6 @@ namespace wcc2d {
 
 cudaError_t launch_halfstep2d_euler_f64(int P, const Step2D& a, cudaStream_t stream);
 cudaError_t launch_halfstep2d_euler_f32(int P, const Step2D& a, cudaStream_t stream);
-cudaError_t halfstep2d_local_bytes_euler_f64(int P, size_t* bytes);
-cudaError_t halfstep2d_local_bytes_euler_f32(int P, size_t* bytes);
-
-cudaError_t halfstep2d_local_bytes(int system, int P, bool fp32, size_t* bytes) {
-    switch (system) {
-        case ADVECTION:
-            return fp32 ? halfstep2d_local_bytes_sys<ADVECTION, float>(P, bytes)
-                        : halfstep2d_local_bytes_sys<ADVECTION, double>(P, bytes);
-        case BURGERS:
-            return fp32 ? halfstep2d_local_bytes_sys<BURGERS, float>(P, bytes)
-                        : halfstep2d_local_bytes_sys<BURGERS, double>(P, bytes);
-        case EULER:
-            return fp32 ? halfstep2d_local_bytes_euler_f32(P, bytes) : halfstep2d_local_bytes_euler_f64(P, bytes);
-        default:
-            return cudaErrorInvalidValue;
-    }
-}
 
 cudaError_t launch_halfstep2d(int system, int P, bool fp32, const Step2D& a, cudaStream_t stream) {
     switch (system) {

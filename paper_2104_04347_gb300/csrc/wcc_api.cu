@@ -169,6 +169,12 @@ struct wcc_ctx {
     cudaGraphExec_t gexec = nullptr;
     int g_cur = -1, g_parity = -1, g_chunk = 0;
     double g_cfl = 0.0;
+    // two half-steps per launch (tb_depth = 2)
+    cudaGraphExec_t gexec_tb = nullptr;
+    int gt_cur = -1, gt_parity = -1, gt_pairs = 0;
+    double gt_cfl = 0.0;
+    double tb_limit = 0.0;  // wcc_stability_limit(P)
+    long long tb_pairs = 0, tb_fallbacks = 0;
 
     long long launches = 0;
     std::string err;
@@ -197,6 +203,14 @@ long long stage_cells(const wcc_ctx* h, int parity) {
 }
 
 long long next_cells(const wcc_ctx* h, int parity) { return stage_cells(h, parity ^ 1); }
+
+cudaError_t launch_pair_kernel(wcc_ctx* h, const StepArgs& a) {
+    switch (h->system) {
+        case WCC_ADVECTION: return launch_halfstep_pair<ADVECTION>(h->P, h->opt.precision, a, h->stream);
+        case WCC_BURGERS: return launch_halfstep_pair<BURGERS>(h->P, h->opt.precision, a, h->stream);
+        default: return launch_halfstep_pair<EULER>(h->P, h->opt.precision, a, h->stream);
+    }
+}
 
 cudaError_t launch_step_kernel(wcc_ctx* h, const StepArgs& a) {
     switch (h->system) {
@@ -238,6 +252,8 @@ StepArgs make_args(wcc_ctx* h, int cur, int parity, double cfl, double dt_fixed)
     split_double(h->opt.adv_speed, a.adv_hi, a.adv_lo);
     a.eps_f = (float)h->opt.eps;
     a.alpha_f = (float)h->opt.alpha;
+    a.n_mid = stage_cells(h, parity ^ 1);
+    a.tb_nu_max = std::min(cfl * (1.0 + h->opt.tb_cfl_growth), h->tb_limit);
     return a;
 }
 
@@ -269,6 +285,10 @@ int ensure_history(wcc_ctx* h, long long need) {
     if (h->gexec) {  // captured launches hold the old pointer
         cudaGraphExecDestroy(h->gexec);
         h->gexec = nullptr;
+    }
+    if (h->gexec_tb) {
+        cudaGraphExecDestroy(h->gexec_tb);
+        h->gexec_tb = nullptr;
     }
     return WCC_OK;
 }
@@ -319,8 +339,62 @@ int build_graph(wcc_ctx* h, int chunk, double cfl) {
     return WCC_OK;
 }
 
+// Two half-steps in one launch from the current buffer (parity unchanged).
+// Arguments of a two-half-step launch: the final stage has the parity, and
+// so the cell count, of the input stage.
+StepArgs make_pair_args(wcc_ctx* h, int cur, double cfl) {
+    StepArgs a = make_args(h, cur, h->parity, cfl, 0.0);
+    a.n_new = a.n_old;
+    return a;
+}
+
+int enqueue_pair(wcc_ctx* h, double cfl) {
+    StepArgs a = make_pair_args(h, h->cur, cfl);
+    cudaError_t e = launch_pair_kernel(h, a);
+    if (e != cudaSuccess) return cuda_fail(h, e, "two-half-step launch");
+    h->launches += 1;
+    h->cur ^= 1;
+    h->steps += 2;
+    return WCC_OK;
+}
+
+// Capture `pairs` (even) two-half-step launches from the current buffer and
+// parity into one graph; after it the buffer and parity are unchanged.
+int build_graph_pairs(wcc_ctx* h, int pairs, double cfl) {
+    if (h->gexec_tb) {
+        cudaGraphExecDestroy(h->gexec_tb);
+        h->gexec_tb = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    WCC_CHECK(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+    int cur = h->cur;
+    for (int s = 0; s < pairs; ++s) {
+        StepArgs a = make_pair_args(h, cur, cfl);
+        cudaError_t e = launch_pair_kernel(h, a);
+        if (e != cudaSuccess) {
+            cudaStreamEndCapture(h->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(h, e, "two-half-step launch during capture");
+        }
+        cur ^= 1;
+    }
+    WCC_CHECK(h, cudaStreamEndCapture(h->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&h->gexec_tb, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        h->gexec_tb = nullptr;
+        return cuda_fail(h, e, "cudaGraphInstantiate");
+    }
+    h->gt_cur = h->cur;
+    h->gt_parity = h->parity;
+    h->gt_cfl = cfl;
+    h->gt_pairs = pairs;
+    return WCC_OK;
+}
+
 void release(wcc_ctx* h) {
     if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->gexec_tb) cudaGraphExecDestroy(h->gexec_tb);
     for (int i = 0; i < 2; ++i) {
         if (h->s64[i]) cudaFree(h->s64[i]);
         if (h->s32[i]) cudaFree(h->s32[i]);
@@ -329,6 +403,80 @@ void release(wcc_ctx* h) {
     if (h->st) cudaFree(h->st);
     if (h->hist) cudaFree(h->hist);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+}
+
+
+// nsteps single CFL half-steps: graphs of graph_chunk, then direct launches.
+int step_single(wcc_ctx* h, long long nsteps, double cfl) {
+    int rc;
+    long long left = nsteps;
+    const int chunk = h->opt.graph_chunk;
+    if (chunk >= 2 && h->stream != nullptr && left >= chunk) {
+        if (!h->gexec || h->g_cur != h->cur || h->g_parity != h->parity || h->g_cfl != cfl ||
+            h->g_chunk != chunk) {
+            rc = build_graph(h, chunk, cfl);
+            if (rc != WCC_OK) return rc;
+        }
+        while (left >= chunk) {
+            WCC_CHECK(h, cudaGraphLaunch(h->gexec, h->stream));
+            h->launches += chunk;
+            h->steps += chunk;
+            left -= chunk;
+        }
+    }
+    for (; left > 0; --left) {
+        rc = enqueue_one(h, cfl, 0.0);
+        if (rc != WCC_OK) return rc;
+    }
+    return WCC_OK;
+}
+
+// nsteps CFL half-steps as two-half-step launches (an odd last one single),
+// checked after the launches: a pair refused by its CFL check (ERR_CFL; it
+// and the launches queued after it changed nothing) is re-done as two single
+// half-steps from the last stage reached, and the pairs resume.
+int step_pairs(wcc_ctx* h, long long nsteps, double cfl) {
+    long long pairs = nsteps / 2;
+    const int graph_pairs = (h->opt.graph_chunk / 2) & ~1;  // even: the graph keeps cur
+    while (pairs > 0) {
+        const int cur0 = h->cur;
+        const long long steps0 = h->steps;
+        long long left = pairs;
+        int rc;
+        if (graph_pairs >= 2 && h->stream != nullptr && left >= graph_pairs) {
+            if (!h->gexec_tb || h->gt_cur != h->cur || h->gt_parity != h->parity || h->gt_cfl != cfl ||
+                h->gt_pairs != graph_pairs) {
+                if ((rc = build_graph_pairs(h, graph_pairs, cfl)) != WCC_OK) return rc;
+            }
+            while (left >= graph_pairs) {
+                WCC_CHECK(h, cudaGraphLaunch(h->gexec_tb, h->stream));
+                h->launches += graph_pairs;
+                h->steps += 2 * graph_pairs;
+                left -= graph_pairs;
+            }
+        }
+        for (; left > 0; --left)
+            if ((rc = enqueue_pair(h, cfl)) != WCC_OK) return rc;
+        DevState st;
+        if ((rc = read_state(h, &st)) != WCC_OK) return rc;
+        if (!(st.err & ERR_CFL)) {
+            h->tb_pairs += pairs;
+            break;
+        }
+        // refused: the device state is at the last stage reached
+        const long long done_pairs = (st.step - steps0) / 2;
+        h->tb_pairs += done_pairs;
+        h->tb_fallbacks += 1;
+        h->cur = cur0 ^ (int)(done_pairs & 1);
+        h->steps = st.step;
+        const unsigned e = st.err & ~ERR_CFL;
+        WCC_CHECK(h, cudaMemcpy(&h->st->err, &e, sizeof e, cudaMemcpyHostToDevice));
+        for (int k = 0; k < 2; ++k)
+            if ((rc = enqueue_one(h, cfl, 0.0)) != WCC_OK) return rc;
+        pairs -= done_pairs + 1;
+    }
+    if (nsteps & 1) return enqueue_one(h, cfl, 0.0);
+    return WCC_OK;
 }
 
 }  // namespace
@@ -345,7 +493,9 @@ void wcc_default_options(wcc_options* opt) {
     opt->gamma = 1.4;
     opt->adv_speed = 1.0;
     opt->graph_chunk = 32;
+    opt->tb_depth = 1;
     opt->cuda_stream = nullptr;
+    opt->tb_cfl_growth = 0.1;
 }
 
 int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domain[2], int bc,
@@ -366,6 +516,15 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     if (!(o.eps >= 0.0) || !(o.alpha > 0.0) || !(o.gamma > 1.0))
         return fail(nullptr, WCC_E_INVAL, "need eps >= 0, alpha > 0, gamma > 1");
     if (o.graph_chunk < 0) return fail(nullptr, WCC_E_INVAL, "graph_chunk must be >= 0");
+    if (o.tb_depth == 0) o.tb_depth = 1;
+    if (o.tb_depth != 1 && o.tb_depth != 2) return fail(nullptr, WCC_E_INVAL, "tb_depth must be 1 or 2");
+    if (o.tb_depth == 2 && o.precision == WCC_FP64)
+        return fail(nullptr, WCC_E_INVAL, "tb_depth = 2 needs WCC_FP32_MIXED or WCC_FP32");
+    if (!(o.tb_cfl_growth >= -1.0) || !(o.tb_cfl_growth < 1e6))
+        return fail(nullptr, WCC_E_INVAL, "tb_cfl_growth must be a number >= -1");
+    double tb_limit = 0.0;
+    if (o.tb_depth == 2 && wcc_stability_limit(P, &tb_limit) != WCC_OK)
+        return fail(nullptr, WCC_E_INVAL, "no stability limit for this P");
 
     int ndev = 0;
     cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -383,6 +542,7 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     h->xr = domain[1];
     h->dx = (domain[1] - domain[0]) / (double)N;
     h->opt = o;
+    h->tb_limit = tb_limit;
     if (h->opt.graph_chunk & 1) h->opt.graph_chunk += 1;
     cudaGetDevice(&h->device);
 
@@ -458,6 +618,7 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     h->cur = 0;
     h->parity = 0;
     h->steps = 0;
+    h->tb_pairs = h->tb_fallbacks = 0;
     const bool mixed = h->opt.precision != WCC_FP64;
     WCC_CHECK(h, cudaMemsetAsync(h->st, 0, sizeof(DevState), h->stream));
     StepArgs a = make_args(h, 0, 0, 0.0, 0.0);
@@ -503,26 +664,19 @@ int wcc_step(wcc_handle h, int64_t nsteps, double cfl) {
     if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
     int rc = ensure_history(h, h->steps + nsteps);
     if (rc != WCC_OK) return rc;
-    long long left = nsteps;
-    const int chunk = h->opt.graph_chunk;
-    if (chunk >= 2 && h->stream != nullptr && left >= chunk) {
-        if (!h->gexec || h->g_cur != h->cur || h->g_parity != h->parity || h->g_cfl != cfl ||
-            h->g_chunk != chunk) {
-            rc = build_graph(h, chunk, cfl);
-            if (rc != WCC_OK) return rc;
-        }
-        while (left >= chunk) {
-            WCC_CHECK(h, cudaGraphLaunch(h->gexec, h->stream));
-            h->launches += chunk;
-            h->steps += chunk;
-            left -= chunk;
-        }
-    }
-    for (; left > 0; --left) {
-        rc = enqueue_one(h, cfl, 0.0);
-        if (rc != WCC_OK) return rc;
-    }
-    return WCC_OK;
+    if (h->opt.tb_depth == 2) return step_pairs(h, nsteps, cfl);
+    return step_single(h, nsteps, cfl);
+}
+
+int wcc_tb_stats(wcc_handle h, int64_t* pairs, int64_t* fallbacks, double* nu2_max) {
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
+    DevState s;
+    int rc = read_state(h, &s);
+    if (pairs) *pairs = h->tb_pairs;
+    if (fallbacks) *fallbacks = h->tb_fallbacks;
+    if (nu2_max) *nu2_max = s.tb_nu2_max;
+    return rc;
 }
 
 int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts) {

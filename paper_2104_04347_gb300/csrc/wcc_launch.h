@@ -12,6 +12,12 @@ namespace wcc {
 template <int SYS>
 cudaError_t launch_halfstep(int P, int precision, const StepArgs& args, cudaStream_t stream);
 
+// Two half-steps in one launch (FP32 variants, P <= 4; halfstep_mixed2_tb2):
+// args.in32 -> args.out32 with args.n_mid cells in between;
+// grid = ceil(n_new / kTileTB) CTAs.
+template <int SYS>
+cudaError_t launch_halfstep_pair(int P, int precision, const StepArgs& args, cudaStream_t stream);
+
 // Largest characteristic speed of the stage whose centre point values start
 // at u0planes (variable v at u0planes + v * var_stride); result in
 // st->amax_bits[slot], which must be zero beforehand.

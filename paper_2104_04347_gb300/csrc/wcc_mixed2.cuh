@@ -314,142 +314,163 @@ constexpr int mixed2_smem_float2() {
     return nvars(SYS) * (5 + P) * (kThreadsMixed + 1);
 }
 
-// One tile of the FP32-mixed half-step, two cells per thread: parents
-// io.first_new + s - parity for slots s = 0..2 kThreadsMixed - 1, new cells
-// io.first_new + c for c = 0..kTileMixed - 1.  rec: mixed2_smem_float2 float2
-// of shared memory.  Returns the larger of the thread's two cell speeds
-// (cells outside the stage count as 0) and error bits; the caller
-// synchronises the block before rec is written again.
-template <int SYS, int P, bool COMP, bool PARK = (P >= 3)>
-__device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, const StepArgs& args, float2* rec,
-                                            float& speed, unsigned& err) {
-    using A = FF<COMP>;
+// The tile is built from four steps that the single half-step runs in a row
+// (mixed_tile2) and the two-half-step kernel twice (halfstep_mixed2_tb2):
+//   mixed_load_parents    the parents' stored values from a stage in global memory,
+//   mixed_parent_records  phase 1: each parent's record into rec,
+//   mixed_new_cells       phase 2: the new cells from neighbouring records,
+//   mixed_store           the new cells into a stage in global memory.
+// Parents are slots s = 0..2 kThreadsMixed - 1 (lane x: s = t, lane y:
+// s = t + kThreadsMixed); new cell c is built from slots c and c + 1.
+
+// Values of parent slots t and t + kThreadsMixed (stage index
+// io.first_new + s - parity, through the boundary rule): the cell average
+// ub (float-float) and the Taylor coefficients c[v][1..P] (c[v][0] is left
+// for mixed_parent_records).
+template <int SYS, int P, bool COMP>
+__device__ __forceinline__ void mixed_load_parents(const TileIO& io, ff2 (&ub)[nvars(SYS)],
+                                                   f2 (&c)[nvars(SYS)][P + 1]) {
     constexpr int NV = nvars(SYS);
     constexpr int K = P + 1;
     constexpr int NP = P + 2;
+    const int t = threadIdx.x;
+    const long long base = io.first_new + t - (io.parity ? 1 : 0);
+    const long long pa = parent_index(base, io.n_old, io.bc);
+    const long long pb = parent_index(base + kThreadsMixed, io.n_old, io.bc);
+    sfor<0, NV>([&](auto V) {
+        constexpr int v = decltype(V)::value;
+        const float* p0 = io.in32 + (long long)(v * NP + 0) * io.pitch;
+        const float* p1 = io.in32 + (long long)(v * NP + 1) * io.pitch;
+        ub[v].hi = f2(__ldg(p0 + pa), __ldg(p0 + pb));
+        ub[v].lo = COMP ? f2(__ldg(p1 + pa), __ldg(p1 + pb)) : f2(0.f);
+        sfor<1, K>([&](auto Ki) {
+            constexpr int k = decltype(Ki)::value;
+            const float* pk = io.in32 + (long long)(v * NP + k + 1) * io.pitch;
+            c[v][k] = f2(__ldg(pk + pa), __ldg(pk + pb));
+        });
+    });
+}
+
+// Phase 1: the records of this thread's two parents (cell averages ub,
+// coefficients c[v][1..P]; c[v][0] is overwritten) into rec.  The caller
+// synchronises the block before reading rec.
+template <int SYS, int P, bool COMP, bool PARK = (P >= 3)>
+__device__ __forceinline__ void mixed_parent_records(const ff2 (&ub_in)[nvars(SYS)], f2 (&c)[nvars(SYS)][P + 1],
+                                                     const ff2 lam2, const StepArgs& args, float2* rec) {
+    using A = FF<COMP>;
+    constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
     constexpr int RV = 5 + P;
     constexpr int W = kThreadsMixed + 1;  // row width of rec in float2
     const int t = threadIdx.x;
-    const long long first_new = io.first_new;
-    const ff2 lam2{f2(lam.hi), f2(COMP ? lam.lo : 0.f)};
-
-    // ---- phase 1: parent records of slots t (lane x) and t + kThreadsMixed (lane y)
+    // record row `row` of variable v for this thread's slots; slot
+    // kThreadsMixed (lane y of thread 0) is also the right parent of new
+    // cell kThreadsMixed - 1 (lane x of the last thread), whose y lane
+    // repeats the value so that the unused lane sees real data
+    auto put = [&](int v, int row, f2 x) {
+        float2* r = rec + v * RV * W + row * W;
+        r[t] = x.v;
+        if (t == 0) r[kThreadsMixed] = make_float2(x.y(), x.y());
+    };
+    auto get = [&](int v, int row) { return f2(rec[v * RV * W + row * W + t]); };
+    // With PARK (the default for P >= 3), ubar and lam f(u_0) wait in
+    // their record rows (0-1 and 2-3) while the Cauchy-Kovalewski table
+    // holds the registers; for lower P alone they fit in registers, which
+    // is faster.
+    constexpr bool kPark = PARK;
+    ff2 ub_r[NV], lf_r[NV];
     {
-        const long long base = first_new + t - (io.parity ? 1 : 0);
-        const long long pa = parent_index(base, io.n_old, io.bc);
-        const long long pb = parent_index(base + kThreadsMixed, io.n_old, io.bc);
-        // record row `row` of variable v for this thread's slots; slot
-        // kThreadsMixed (lane y of thread 0) is also the right parent of new
-        // cell kThreadsMixed - 1 (lane x of the last thread), whose y lane
-        // repeats the value so that the unused lane sees real data
-        auto put = [&](int v, int row, f2 x) {
-            float2* r = rec + v * RV * W + row * W;
-            r[t] = x.v;
-            if (t == 0) r[kThreadsMixed] = make_float2(x.y(), x.y());
-        };
-        auto get = [&](int v, int row) { return f2(rec[v * RV * W + row * W + t]); };
-        // With PARK (the default for P >= 3), ubar and lam f(u_0) wait in
-        // their record rows (0-1 and 2-3) while the Cauchy-Kovalewski table
-        // holds the registers; for lower P alone they fit in registers, which
-        // is faster.
-        constexpr bool kPark = PARK;
-        f2 c[NV][K];
-        ff2 ub_r[NV], lf_r[NV];
-        {
-            ff2 u0[NV];
-            sfor<0, NV>([&](auto V) {
-                constexpr int v = decltype(V)::value;
-                const float* p0 = io.in32 + (long long)(v * NP + 0) * io.pitch;
-                const float* p1 = io.in32 + (long long)(v * NP + 1) * io.pitch;
-                ff2 ub;
-                ub.hi = f2(__ldg(p0 + pa), __ldg(p0 + pb));
-                ub.lo = COMP ? f2(__ldg(p1 + pa), __ldg(p1 + pb)) : f2(0.f);
-                sfor<1, K>([&](auto Ki) {
-                    constexpr int k = decltype(Ki)::value;
-                    const float* pk = io.in32 + (long long)(v * NP + k + 1) * io.pitch;
-                    c[v][k] = f2(__ldg(pk + pa), __ldg(pk + pb));
-                });
-                u0[v] = A::add(ub, -average_minus_centre<P>(c[v]));
-                c[v][0] = u0[v].hi;
-                if constexpr (kPark) {
-                    put(v, 0, ub.hi);
-                    if constexpr (COMP) put(v, 1, ub.lo);
-                } else {
-                    ub_r[v] = ub;
-                }
-            });
-            ff2 f0[NV];
-            flux_ff2<SYS, COMP>(u0, args, f0);
-            sfor<0, NV>([&](auto V) {
-                constexpr int v = decltype(V)::value;
-                const ff2 lf = A::mul(f0[v], lam2);
-                if constexpr (kPark) {
-                    put(v, 2, lf.hi);
-                    if constexpr (COMP) put(v, 3, lf.lo);
-                } else {
-                    lf_r[v] = lf;
-                }
-            });
-        }
-        f2 X[NV][K][K], F0[NV][K];
-        ck_table<SYS, P, f2>(c, lam2.hi, args, X, F0);
-        // Record of the parent (Eqs. Cal1DFlux, SubEq:1DCellAVGR/L,
-        // SubEq:Cal_1D_Derivatives_4): its cell average ubar and
-        //   A   = ubar / 2 + g,  g = lam fbar + dodd / 2, the part of ubar that
-        //         goes to the new cell on its right (float-float; the new cell
-        //         on its left gets B = ubar - A, so the scheme stays
-        //         conservative to float-float rounding),
-        //   dev = v_0 - ubar, the centre value at the new time level minus the
-        //         cell average,
-        //   and the higher vertex coefficients sum_m X[k][m], k >= 1.
-        // g is lam f(u_0) in float-float plus the FP32 rest
-        // h = lam (fbar - f(u_0)) + dodd / 2.
+        ff2 u0[NV];
         sfor<0, NV>([&](auto V) {
             constexpr int v = decltype(V)::value;
-            f2 fhigh(0.f);
-            sfor<1, K>([&](auto Bi) {
-                constexpr int b = decltype(Bi)::value;
-                fhigh = fma(f2((float)(1.0 / (b + 1.0))), F0[v][b], fhigh);
-            });
-            f2 dodd(0.f);
-            sfor<1, K>([&](auto Ki) {
-                constexpr int k = decltype(Ki)::value;
-                if constexpr (k & 1) dodd = fma(f2((float)(1.0 / ((k + 1.0) * cpow2(k)))), c[v][k], dodd);
-            });
-            const f2 h = fma(lam2.hi, fhigh, f2(0.5f) * dodd);
-            ff2 ub, lf;
+            const ff2 ub = ub_in[v];
+            u0[v] = A::add(ub, -average_minus_centre<P>(c[v]));
+            c[v][0] = u0[v].hi;
             if constexpr (kPark) {
-                ub = ff2{get(v, 0), COMP ? get(v, 1) : f2(0.f)};
-                lf = ff2{get(v, 2), COMP ? get(v, 3) : f2(0.f)};
-            } else {
-                ub = ub_r[v];
-                lf = lf_r[v];
                 put(v, 0, ub.hi);
                 if constexpr (COMP) put(v, 1, ub.lo);
+            } else {
+                ub_r[v] = ub;
             }
-            const ff2 Ac = A::add(ff2_scale(ub, 0.5f), A::add(lf, h));
-            put(v, 2, Ac.hi);
-            if constexpr (COMP) put(v, 3, Ac.lo);
-            f2 vt0(0.f);
-            sfor<1, K>([&](auto Mi) { vt0 += X[v][0][decltype(Mi)::value]; });
-            put(v, 4, vt0 - average_minus_centre<P>(c[v]));
-            sfor<1, K>([&](auto Ki) {
-                constexpr int k = decltype(Ki)::value;
-                f2 s = X[v][k][0];
-                sfor<1, K - k>([&](auto Mi) { s += X[v][k][decltype(Mi)::value]; });
-                put(v, 4 + k, s);
-            });
+        });
+        ff2 f0[NV];
+        flux_ff2<SYS, COMP>(u0, args, f0);
+        sfor<0, NV>([&](auto V) {
+            constexpr int v = decltype(V)::value;
+            const ff2 lf = A::mul(f0[v], lam2);
+            if constexpr (kPark) {
+                put(v, 2, lf.hi);
+                if constexpr (COMP) put(v, 3, lf.lo);
+            } else {
+                lf_r[v] = lf;
+            }
         });
     }
-    __syncthreads();
+    f2 X[NV][K][K], F0[NV][K];
+    ck_table<SYS, P, f2>(c, lam2.hi, args, X, F0);
+    // Record of the parent (Eqs. Cal1DFlux, SubEq:1DCellAVGR/L,
+    // SubEq:Cal_1D_Derivatives_4): its cell average ubar and
+    //   A   = ubar / 2 + g,  g = lam fbar + dodd / 2, the part of ubar that
+    //         goes to the new cell on its right (float-float; the new cell
+    //         on its left gets B = ubar - A, so the scheme stays
+    //         conservative to float-float rounding),
+    //   dev = v_0 - ubar, the centre value at the new time level minus the
+    //         cell average,
+    //   and the higher vertex coefficients sum_m X[k][m], k >= 1.
+    // g is lam f(u_0) in float-float plus the FP32 rest
+    // h = lam (fbar - f(u_0)) + dodd / 2.
+    sfor<0, NV>([&](auto V) {
+        constexpr int v = decltype(V)::value;
+        f2 fhigh(0.f);
+        sfor<1, K>([&](auto Bi) {
+            constexpr int b = decltype(Bi)::value;
+            fhigh = fma(f2((float)(1.0 / (b + 1.0))), F0[v][b], fhigh);
+        });
+        f2 dodd(0.f);
+        sfor<1, K>([&](auto Ki) {
+            constexpr int k = decltype(Ki)::value;
+            if constexpr (k & 1) dodd = fma(f2((float)(1.0 / ((k + 1.0) * cpow2(k)))), c[v][k], dodd);
+        });
+        const f2 h = fma(lam2.hi, fhigh, f2(0.5f) * dodd);
+        ff2 ub, lf;
+        if constexpr (kPark) {
+            ub = ff2{get(v, 0), COMP ? get(v, 1) : f2(0.f)};
+            lf = ff2{get(v, 2), COMP ? get(v, 3) : f2(0.f)};
+        } else {
+            ub = ub_r[v];
+            lf = lf_r[v];
+            put(v, 0, ub.hi);
+            if constexpr (COMP) put(v, 1, ub.lo);
+        }
+        const ff2 Ac = A::add(ff2_scale(ub, 0.5f), A::add(lf, h));
+        put(v, 2, Ac.hi);
+        if constexpr (COMP) put(v, 3, Ac.lo);
+        f2 vt0(0.f);
+        sfor<1, K>([&](auto Mi) { vt0 += X[v][0][decltype(Mi)::value]; });
+        put(v, 4, vt0 - average_minus_centre<P>(c[v]));
+        sfor<1, K>([&](auto Ki) {
+            constexpr int k = decltype(Ki)::value;
+            f2 s = X[v][k][0];
+            sfor<1, K - k>([&](auto Mi) { s += X[v][k][decltype(Mi)::value]; });
+            put(v, 4 + k, s);
+        });
+    });
+}
 
-    // ---- phase 2: new cells t (lane x) and t + kThreadsMixed (lane y)
-    const long long ia = first_new + t;
-    const long long ib = first_new + kThreadsMixed + t;
-    const bool va = ia < io.n_new;
-    const bool vb = (t < kThreadsMixed - 1) && ib < io.n_new;
-    ff2 ubn[NV];
-    f2 d[NV][K], dl[NV], dr[NV];
+// Phase 2: new cells t (lane x) and t + kThreadsMixed (lane y) from the
+// records of slots (t, t + 1) and (t + kThreadsMixed, t + kThreadsMixed + 1):
+// the cell average ubn (float-float), the point value minus the average
+// d[v][0] and the coefficients d[v][1..P] of the limited polynomial.
+template <int SYS, int P, bool COMP>
+__device__ __forceinline__ void mixed_new_cells(const float2* rec, const StepArgs& args, ff2 (&ubn)[nvars(SYS)],
+                                                f2 (&d)[nvars(SYS)][P + 1], unsigned& err) {
+    using A = FF<COMP>;
+    constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
+    constexpr int RV = 5 + P;
+    constexpr int W = kThreadsMixed + 1;
+    const int t = threadIdx.x;
+    f2 dl[NV], dr[NV];
     sfor<0, NV>([&](auto V) {
         constexpr int v = decltype(V)::value;
         const float2* r = rec + v * RV * W;
@@ -503,7 +524,31 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
             });
         }
     }
+}
 
+// Largest characteristic speed at the centre values ubn + d[v][0] of the
+// thread's two new cells, counting a lane only if it is valid.
+template <int SYS>
+__device__ __forceinline__ float mixed_cell_speed(const ff2 (&ubn)[nvars(SYS)], const f2 (&d0)[nvars(SYS)],
+                                                  bool va, bool vb, const StepArgs& args, unsigned& err) {
+    f2 u0n[nvars(SYS)];
+    sfor<0, nvars(SYS)>([&](auto V) { u0n[decltype(V)::value] = ubn[decltype(V)::value].hi + d0[decltype(V)::value]; });
+    const f2 sp = wave_speed<SYS, f2>(u0n, args, err);
+    return fmaxf(va ? sp.x() : 0.f, vb ? sp.y() : 0.f);
+}
+
+// New cells io.first_new + t (lane x, if va) and io.first_new + t +
+// kThreadsMixed (lane y, if vb) into the stage io.out32; returns the larger
+// of their speeds.
+template <int SYS, int P>
+__device__ __forceinline__ float mixed_store(const TileIO& io, const ff2 (&ubn)[nvars(SYS)],
+                                             const f2 (&d)[nvars(SYS)][P + 1], bool va, bool vb,
+                                             const StepArgs& args, unsigned& err) {
+    constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
+    constexpr int NP = P + 2;
+    const long long ia = io.first_new + threadIdx.x;
+    const long long ib = ia + kThreadsMixed;
     f2 u0n[NV];
     f2 check(0.f);  // NaN / Inf in any stored value reaches this sum
     sfor<0, NV>([&](auto V) {
@@ -530,7 +575,36 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
     });
     if ((va && not_finite(check.x())) || (vb && not_finite(check.y()))) err |= ERR_NONFINITE;
     const f2 sp = wave_speed<SYS, f2>(u0n, args, err);
-    speed = fmaxf(va ? sp.x() : 0.f, vb ? sp.y() : 0.f);
+    return fmaxf(va ? sp.x() : 0.f, vb ? sp.y() : 0.f);
+}
+
+// One tile of the FP32-mixed half-step, two cells per thread: parents
+// io.first_new + s - parity for slots s = 0..2 kThreadsMixed - 1, new cells
+// io.first_new + c for c = 0..kTileMixed - 1.  rec: mixed2_smem_float2 float2
+// of shared memory.  Returns the larger of the thread's two cell speeds
+// (cells outside the stage count as 0) and error bits; the caller
+// synchronises the block before rec is written again.
+template <int SYS, int P, bool COMP, bool PARK = (P >= 3)>
+__device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, const StepArgs& args, float2* rec,
+                                            float& speed, unsigned& err) {
+    constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
+    const int t = threadIdx.x;
+    const ff2 lam2{f2(lam.hi), f2(COMP ? lam.lo : 0.f)};
+    {
+        ff2 ub[NV];
+        f2 c[NV][K];
+        mixed_load_parents<SYS, P, COMP>(io, ub, c);
+        mixed_parent_records<SYS, P, COMP, PARK>(ub, c, lam2, args, rec);
+    }
+    __syncthreads();
+    ff2 ubn[NV];
+    f2 d[NV][K];
+    mixed_new_cells<SYS, P, COMP>(rec, args, ubn, d, err);
+    const long long ia = io.first_new + t;
+    const bool va = ia < io.n_new;
+    const bool vb = (t < kThreadsMixed - 1) && ia + kThreadsMixed < io.n_new;
+    speed = mixed_store<SYS, P>(io, ubn, d, va, vb, args, err);
 }
 
 template <int SYS, int P, bool COMP = true>
@@ -558,6 +632,210 @@ __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_m
         }
     }
     finish_halfstep<float, kThreadsMixed>(speed, err, z.dt, args);
+}
+
+// ------------------------------------------------------ two half-steps per launch
+
+// Final cells of a two-half-step tile: 2 kThreadsMixed parents give
+// 2 kThreadsMixed - 1 intermediate cells and 2 kThreadsMixed - 2 final ones.
+constexpr int kTileTB = 2 * kThreadsMixed - 2;
+
+// Bookkeeping of a two-half-step launch after its last CTA finished (one
+// thread): the pair is taken when the realised CFL number of its second
+// half-step, dt a_mid / dx with a_mid the bound of the intermediate stage,
+// is at most args.tb_nu_max; then dt is recorded twice, t advances by two
+// steps and the next launch's dt comes from the final stage's bound, as in
+// finalize_state.  Otherwise ERR_CFL is set and the state (t, step, the
+// bounds of the input stage and the prepared dt) is left as it was before
+// the launch, so that the caller can take the two half-steps one by one
+// from the input stage, which the launch did not overwrite.
+__device__ __forceinline__ void finalize_pair(DevState* st, double dt, const StepArgs& args) {
+    const int parity = args.parity;
+    const float fmid = __uint_as_float(st->amax_f32[parity ^ 1]);
+    const float ffin = __uint_as_float(st->amax_f32_tb);
+    st->amax_f32[parity ^ 1] = 0u;
+    st->amax_f32_tb = 0u;
+    st->blocks_done = 0u;
+    const double nu2 = dt * (double)fmid / args.dx;
+    if (!(nu2 <= args.tb_nu_max)) {
+        st->err |= ERR_CFL;
+        __threadfence();
+        return;
+    }
+    if (nu2 > st->tb_nu2_max) st->tb_nu2_max = nu2;
+    st->amax_bits[parity ^ 1] = (unsigned long long)__double_as_longlong((double)fmid);
+    st->amax_bits[parity] = (unsigned long long)__double_as_longlong((double)ffin);
+    const long long k = st->step;
+    if (k < args.hist_cap) args.hist[k] = dt;
+    if (k + 1 < args.hist_cap) args.hist[k + 1] = dt;
+    st->step = k + 2;
+    st->t = (st->t + dt) + dt;
+    if (not_finite(dt)) st->err |= ERR_NONFINITE;
+    if (args.cfl_mode) {
+        const double ndt = args.cfl * args.dx / (double)ffin;
+        st->next_dt = ndt;
+        st->next_lam = ndt / args.dx;
+        split_to_floats(st->next_lam, st->next_lam_hi, st->next_lam_lo);
+        st->next_cfl = args.cfl;
+    } else {
+        st->next_cfl = 0.0;
+    }
+    __threadfence();
+}
+
+// Block maxima of the intermediate and final speeds, one atomic each per
+// CTA, then the CTA count; the last CTA runs finalize_pair.  Synchronises
+// the block.
+__device__ __forceinline__ void finish_pair(float mid, float fin, unsigned err, double dt, const StepArgs& args) {
+    __shared__ float s_mid[kThreadsMixed / 32], s_fin[kThreadsMixed / 32];
+    __shared__ unsigned s_err[kThreadsMixed / 32];
+    if (mid != mid) {
+        mid = INFINITY;
+        err |= ERR_NONFINITE;
+    }
+    if (fin != fin) {
+        fin = INFINITY;
+        err |= ERR_NONFINITE;
+    }
+    mid = warp_max<float>(mid);
+    fin = warp_max<float>(fin);
+    err = __reduce_or_sync(0xffffffffu, err);
+    if ((threadIdx.x & 31) == 0) {
+        s_mid[threadIdx.x >> 5] = mid;
+        s_fin[threadIdx.x >> 5] = fin;
+        s_err[threadIdx.x >> 5] = err;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = s_mid[0], f = s_fin[0];
+        unsigned e = s_err[0];
+#pragma unroll
+        for (int w = 1; w < kThreadsMixed / 32; ++w) {
+            m = fmaxf(m, s_mid[w]);
+            f = fmaxf(f, s_fin[w]);
+            e |= s_err[w];
+        }
+        DevState* st = args.st;
+        if (m > 0.f) atomicMax(&st->amax_f32[args.parity ^ 1], __float_as_uint(m));
+        if (f > 0.f) atomicMax(&st->amax_f32_tb, __float_as_uint(f));
+        if (e) atomicOr(&st->err, e);
+        __threadfence();
+        const unsigned done = atomicAdd(&st->blocks_done, 1u);
+        if (done == gridDim.x - 1) {
+            __threadfence();
+            finalize_pair(st, dt, args);
+        }
+    }
+}
+
+// Two staggered half-steps in one pass over HBM (temporal blocking, FP32
+// variants): stage n (parity p, args.in32) -> n + 1/2 -> n + 1 (parity p,
+// args.out32), both with the dt of stage n's bound.  CTA b owns final cells
+// f0 = b kTileTB .. f0 + kTileTB - 1; it loads the parents o0 = f0 - 1 ..
+// o0 + 2 kThreadsMixed - 1, builds the intermediate cells m0 = o0 + p ..
+// m0 + 2 kThreadsMixed - 2 in registers (each thread's two intermediate
+// cells are the parents it needs next, slot for slot), and from them the
+// final cells.  Neighbouring CTAs build one intermediate cell twice.  At a
+// transmissive boundary the intermediate cells outside the stage take the
+// adjacent cell's values (the ghost rule of Sec. 2.1's staggered mesh), at a
+// periodic one they are the wrapped cells, built from wrapped parents.  The
+// intermediate stage's bound decides whether the pair is taken
+// (finalize_pair); a launch that finds ERR_CFL set does nothing.
+template <int SYS, int P, bool COMP = true>
+__global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_mixed2_tb2(const StepArgs args) {
+    constexpr int NV = nvars(SYS);
+    constexpr int K = P + 1;
+    __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
+    if (args.st->err & ERR_CFL) return;  // an earlier pair was refused: the caller steps singly from there
+    const int t = threadIdx.x;
+    const StepSize z = step_size(args);
+    const ff2 lam2{f2(z.lam_hi), f2(COMP ? z.lam_lo : 0.f)};
+    const int p = args.parity;
+    const long long f0 = (long long)blockIdx.x * kTileTB;
+    const long long o0 = f0 - 1;
+    const long long m0 = o0 + p;
+    unsigned err = 0u;
+    float mid_speed = 0.f;
+
+    ff2 ub[NV];
+    f2 c[NV][K];
+    {
+        const TileIO io1{args.in32, nullptr, args.pitch, args.n_old, args.n_mid, m0, p, args.bc};
+        mixed_load_parents<SYS, P, COMP>(io1, ub, c);
+        mixed_parent_records<SYS, P, COMP>(ub, c, lam2, args, rec);
+    }
+    __syncthreads();
+    {
+        f2 d[NV][K];
+        mixed_new_cells<SYS, P, COMP>(rec, args, ub, d, err);
+        // intermediate cells m0 + t (lane x) and m0 + t + kThreadsMixed (lane
+        // y; slot 2 kThreadsMixed - 1 is not a cell of the tile)
+        const long long ia = m0 + t, ib = ia + kThreadsMixed;
+        const bool va = ia >= 0 && ia < args.n_mid;
+        const bool vb = t < kThreadsMixed - 1 && ib >= 0 && ib < args.n_mid;
+        f2 d0[NV];
+        sfor<0, NV>([&](auto V) { d0[decltype(V)::value] = d[decltype(V)::value][0]; });
+        mid_speed = mixed_cell_speed<SYS>(ub, d0, va, vb, args, err);
+        sfor<0, NV>([&](auto V) {
+            constexpr int v = decltype(V)::value;
+            sfor<1, K>([&](auto Ki) { c[v][decltype(Ki)::value] = d[v][decltype(Ki)::value]; });
+        });
+        __syncthreads();  // every record of the first half-step has been read
+        if (args.bc == BC_TRANSMISSIVE && (m0 < 0 || m0 + 2 * kThreadsMixed - 1 > args.n_mid)) {
+            // edge tiles: slots outside [0, n_mid) copy the edge cell
+            constexpr int Q = K + 1;  // hi, lo, c_1..c_P per variable
+            float* sc = reinterpret_cast<float*>(rec);
+            auto save = [&](int slot, int lane) {
+                sfor<0, NV>([&](auto V) {
+                    constexpr int v = decltype(V)::value;
+                    sc[(v * Q + 0) * 2 * kThreadsMixed + slot] = lane ? ub[v].hi.y() : ub[v].hi.x();
+                    sc[(v * Q + 1) * 2 * kThreadsMixed + slot] = lane ? ub[v].lo.y() : ub[v].lo.x();
+                    sfor<1, K>([&](auto Ki) {
+                        constexpr int k = decltype(Ki)::value;
+                        sc[(v * Q + 1 + k) * 2 * kThreadsMixed + slot] = lane ? c[v][k].y() : c[v][k].x();
+                    });
+                });
+            };
+            save(t, 0);
+            save(t + kThreadsMixed, 1);
+            __syncthreads();
+            auto fetch = [&](long long idx, int lane) {
+                const long long cl = idx < 0 ? 0 : (idx >= args.n_mid ? args.n_mid - 1 : idx);
+                if (cl == idx) return;
+                const int slot = (int)(cl - m0);
+                sfor<0, NV>([&](auto V) {
+                    constexpr int v = decltype(V)::value;
+                    const float hi = sc[(v * Q + 0) * 2 * kThreadsMixed + slot];
+                    const float lo = sc[(v * Q + 1) * 2 * kThreadsMixed + slot];
+                    if (lane) {
+                        ub[v].hi.v.y = hi;
+                        ub[v].lo.v.y = lo;
+                    } else {
+                        ub[v].hi.v.x = hi;
+                        ub[v].lo.v.x = lo;
+                    }
+                    sfor<1, K>([&](auto Ki) {
+                        constexpr int k = decltype(Ki)::value;
+                        const float x = sc[(v * Q + 1 + k) * 2 * kThreadsMixed + slot];
+                        if (lane) c[v][k].v.y = x; else c[v][k].v.x = x;
+                    });
+                });
+            };
+            fetch(m0 + t, 0);
+            fetch(m0 + t + kThreadsMixed, 1);
+            __syncthreads();
+        }
+    }
+    mixed_parent_records<SYS, P, COMP>(ub, c, lam2, args, rec);
+    __syncthreads();
+    ff2 ubn[NV];
+    f2 d[NV][K];
+    mixed_new_cells<SYS, P, COMP>(rec, args, ubn, d, err);
+    const TileIO io2{nullptr, args.out32, args.pitch, args.n_mid, args.n_new, f0, p ^ 1, args.bc};
+    const bool va = f0 + t < args.n_new;
+    const bool vb = t < kThreadsMixed - 2 && f0 + t + kThreadsMixed < args.n_new;
+    const float fin_speed = mixed_store<SYS, P>(io2, ubn, d, va, vb, args, err);
+    finish_pair(mid_speed, fin_speed, err, z.dt, args);
 }
 
 // Set-up of an FP32-mixed stage in one pass: the host-layout DOFs (already in

@@ -28,7 +28,9 @@ enum { PREC_FP64 = 0, PREC_FP32_MIXED = 1, PREC_FP32 = 2 };
 constexpr int kThreads = 128;
 constexpr int kTile = kThreads - 1;
 
-enum : unsigned { ERR_NONFINITE = 1u, ERR_POSITIVITY = 2u };
+// ERR_CFL: the second half-step of a two-half-step launch would exceed its
+// CFL bound (the pair is not taken; see halfstep_mixed2_tb2).
+enum : unsigned { ERR_NONFINITE = 1u, ERR_POSITIVITY = 2u, ERR_CFL = 4u };
 
 // Device-resident time-marching state (one per solver).
 struct DevState {
@@ -50,6 +52,12 @@ struct DevState {
     double next_dt;
     double next_lam;
     float next_lam_hi, next_lam_lo;
+    // two half-steps per launch: the bound of the pair's final stage (FP32
+    // bits, accumulated like amax_f32) and the largest CFL number a pair's
+    // second half-step has taken since the state was loaded
+    unsigned int amax_f32_tb;
+    unsigned int pad_tb_;
+    double tb_nu2_max;
 };
 
 // Arguments of one half-step launch.  Plane (v, k) of a stage holds the
@@ -85,6 +93,11 @@ struct StepArgs {
     // FP32 copies for the FP32-mixed kernels (hi/lo: float-float split)
     float gamma_f, g1_hi, g1_lo, adv_hi, adv_lo, eps_f, alpha_f;
     float lam_fixed_hi, lam_fixed_lo;
+    // two half-steps per launch (halfstep_mixed2_tb2): cells of the
+    // intermediate stage, and the largest CFL number its second half-step
+    // may take with the pair's dt
+    long long n_mid;
+    double tb_nu_max;
 };
 
 // dt and lam of this launch (the same values in every thread).

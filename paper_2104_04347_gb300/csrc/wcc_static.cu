@@ -8,6 +8,7 @@
 // caller already owns, and keeps the kernels' scratch -- the CFL accumulators,
 // counters, error bits and the dt history -- in a fixed array in the
 // library's device image instead of in cudaMalloc'd memory.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -35,19 +36,54 @@ static __device__ __align__(256) unsigned char g_static_scratch[sizeof(StaticScr
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_ptr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once
-// per device, with that device current).
+// Unique id of the calling thread's current CUDA context (driver entry
+// points cuCtxGetCurrent / cuCtxGetId, reached through the runtime without
+// linking the driver library), or 0 when none is current or the driver
+// lacks them.  A device reset destroys the context, and the next one gets a
+// new id.
+unsigned long long current_context_id() {
+    using GetCurrent = CUresult (*)(CUcontext*);
+    using GetId = CUresult (*)(CUcontext, unsigned long long*);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static bool looked_up = false;
+    if (!looked_up) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+        looked_up = true;
+    }
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// Device address of the scratch array on the current device, looked up with
+// that device current at the first call on it, and again whenever the
+// device's context has changed since (after a cudaDeviceReset the module is
+// loaded anew and the array may move).
 int scratch_address(void** out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return WCC_E_CUDA;
     if (dev < 0 || dev >= kMaxDevices) return WCC_E_CAPACITY;
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_ptr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_ptr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress((void**)&ptr, g_static_scratch);
         if (e != cudaSuccess || !ptr) return WCC_E_CUDA;
         g_scratch_ptr[dev] = ptr;
+        g_scratch_ctx[dev] = current_context_id();
     }
     *out = g_scratch_ptr[dev];
     return WCC_OK;
@@ -82,7 +118,8 @@ extern "C" int wcc_advance_static(int system, int P, int bc, int64_t N, const do
                                   int64_t pitch, int64_t nsteps, double cfl, double* dts_out) {
     if (system < WCC_ADVECTION || system > WCC_EULER || P < 1 || P > 4) return WCC_E_INVAL;
     if (bc != WCC_BC_PERIODIC && bc != WCC_BC_TRANSMISSIVE) return WCC_E_INVAL;
-    if (N < 4 || !domain || !(domain[1] > domain[0]) || (parity != 0 && parity != 1)) return WCC_E_INVAL;
+    if (N < 4 || N > (1ll << 31) || !domain || !(domain[1] > domain[0]) || (parity != 0 && parity != 1))
+        return WCC_E_INVAL;
     if (!stage_a || !stage_b || stage_a == stage_b) return WCC_E_INVAL;
     if (nsteps < 0 || !(cfl > 0.0) || !(cfl < 1e6)) return WCC_E_INVAL;
     if (nsteps > WCC_STATIC_MAX_HALFSTEPS) return WCC_E_CAPACITY;

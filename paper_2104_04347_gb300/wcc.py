@@ -42,8 +42,9 @@ class Options(ctypes.Structure):
         ("gamma", ctypes.c_double),
         ("adv_speed", ctypes.c_double),
         ("graph_chunk", ctypes.c_int),
-        ("reserved", ctypes.c_int),
+        ("tb_depth", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
+        ("tb_cfl_growth", ctypes.c_double),
     ]
 
 
@@ -77,6 +78,7 @@ _SIGS = {
     "wcc_set_initial": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "wcc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
     "wcc_step_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp]),
+    "wcc_tb_stats": (ctypes.c_int, [ctypes.c_void_p, _i64p, _i64p, _dp]),
     "wcc_step_until": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_int64)]),
     "wcc_get_dofs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
@@ -86,6 +88,8 @@ _SIGS = {
     "wcc_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "wcc_launch_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "wcc_measure_fp_peak": (ctypes.c_int, [ctypes.c_int, _dp]),
+    "wcc_stability_limit": (ctypes.c_int, [ctypes.c_int, _dp]),
+    "wcc_default_cfl": (ctypes.c_int, [ctypes.c_int, _dp]),
     "wcc_advance_static": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, _dp,
                                           ctypes.POINTER(Options), ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                           ctypes.c_int64, ctypes.c_int64, ctypes.c_double, _dp]),
@@ -168,6 +172,24 @@ def measure_fp_peak(precision: int) -> float:
     return v.value
 
 
+def stability_limit(P: int) -> float:
+    """Linear stability limit of degree P (the library's von Neumann scan)."""
+    v = ctypes.c_double()
+    rc = load().wcc_stability_limit(int(P), ctypes.byref(v))
+    if rc != 0:
+        raise WCCError(rc, f"no stability limit for P = {P}")
+    return v.value
+
+
+def default_cfl(P: int) -> float:
+    """The library's default CFL number of degree P."""
+    v = ctypes.c_double()
+    rc = load().wcc_default_cfl(int(P), ctypes.byref(v))
+    if rc != 0:
+        raise WCCError(rc, f"no default CFL number for P = {P}")
+    return v.value
+
+
 def _ptr(a: np.ndarray) -> ctypes.c_void_p:
     return ctypes.c_void_p(a.ctypes.data)
 
@@ -181,7 +203,8 @@ class Solver:
 
     def __init__(self, system: int, N: int, P: int, domain, bc: int, *, precision: int = FP64,
                  limiter: bool = True, alpha: float = 2.0, eps: float = 1e-40, gamma: float = 1.4,
-                 adv_speed: float = 1.0, graph_chunk: int = 32, stream: int | None = None):
+                 adv_speed: float = 1.0, graph_chunk: int = 32, stream: int | None = None, tb_depth: int = 1,
+                 tb_cfl_growth: float = 0.1):
         self.lib = load()
         o = default_options()
         o.precision = precision
@@ -192,6 +215,8 @@ class Solver:
         o.adv_speed = adv_speed
         o.graph_chunk = graph_chunk
         o.cuda_stream = stream
+        o.tb_depth = tb_depth
+        o.tb_cfl_growth = tb_cfl_growth
         h = ctypes.c_void_p()
         dom = (ctypes.c_double * 2)(float(domain[0]), float(domain[1]))
         rc = self.lib.wcc_create(ctypes.byref(h), system, int(N), int(P), dom, bc, ctypes.byref(o))
@@ -242,6 +267,13 @@ class Solver:
     def step_dt(self, dts) -> None:
         d = np.ascontiguousarray(dts, dtype=np.float64)
         self._check(self.lib.wcc_step_dt(self.h, d.size, d.ctypes.data_as(_dp)))
+
+    def tb_stats(self):
+        """(pairs taken, pairs refused and re-done singly, largest second
+        half-step CFL number) of the two-half-step launches."""
+        pairs, fb, nu = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+        self._check(self.lib.wcc_tb_stats(self.h, ctypes.byref(pairs), ctypes.byref(fb), ctypes.byref(nu)))
+        return pairs.value, fb.value, nu.value
 
     def step_until(self, t_end: float, cfl: float) -> int:
         """Advance to exactly t_end on an integer stage; returns the half-steps taken."""

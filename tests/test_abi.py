@@ -82,3 +82,19 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.wcc2d_step(None, 1, 0.3) == -1
     assert lib.wcc2d_synchronize(None) == -1
     assert lib.wcc2d_destroy(None) == 0
+
+
+@pytest.mark.parametrize("kw,needle", [
+    (dict(precision=wcc.FP64, tb_depth=2), "tb_depth = 2 needs"),
+    (dict(precision=wcc.FP32_MIXED, tb_depth=3), "tb_depth must be"),
+    (dict(precision=wcc.FP32_MIXED, tb_depth=2, tb_cfl_growth=-2.0), "tb_cfl_growth"),
+])
+def test_create_rejects_bad_temporal_blocking(kw, needle):
+    with pytest.raises(wcc.WCCError) as ei:
+        wcc.Solver(2, 64, 3, (0.0, 1.0), 1, **kw)
+    assert ei.value.code == -1 and needle in str(ei.value)
+
+
+def test_default_temporal_blocking_options():
+    o = wcc.default_options()
+    assert o.tb_depth == 1 and o.tb_cfl_growth == 0.1
