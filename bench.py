@@ -67,8 +67,11 @@ def parse():
     ap.add_argument("--n2d", type=int, default=2048, help="cells per axis of the 2D workload")
     ap.add_argument("--workloads2d", action="store_true",
                     help="the paper's 2D Riemann problems at 1200^2 to t_end instead")
+    ap.add_argument("--advection", action="store_true",
+                    help="the linear-advection workload (N = 200, P = 2, to t = 2): time and error")
     ap.add_argument("--burgers", action="store_true",
                     help="the Burgers workload: N = 2^10..2^20, P = 1..4, FP64 and FP32-mixed")
+    ap.add_argument("--burgers-log2n", default="10,14,18,20", help="log2 N of the Burgers workload, comma-separated")
     ap.add_argument("--high-order", action="store_true",
                     help="FP64 Euler half-steps at P = 3..6 (seeded Riemann data) instead")
     return ap.parse_args()
@@ -444,6 +447,25 @@ def tb_bench(pr, stream, steps, warmup, barrier, dev, cells_per_step, cells_per_
             "dt_rule": "one dt per pair from the first stage's bound; second half-step's CFL number checked"}
 
 
+def tuned_bench(pr, stream, steps, warmup, barrier, dev, cells_per_step):
+    """The headline workload with the launch configuration wcc_autotune picks
+    on it (cells per CTA, one or two half-steps per launch)."""
+    from paper_2104_04347_gb300 import wcc
+
+    with wcc.Solver(pr.system, pr.N, P, (pr.x_l, pr.x_r), pr.bc, precision=wcc.FP32_MIXED,
+                    graph_chunk=HALFSTEPS_PER_STEP, stream=stream.cuda_stream) as s:
+        s.set_initial(pr.q0)
+        t0 = time.perf_counter()
+        cpb, tb = s.autotune(CFL)
+        tune_s = time.perf_counter() - t0
+        total_ms, step_ms, launches = time_solver(s, stream, steps, warmup, barrier)
+    value = job_throughput(cells_per_step * steps, total_ms * 1e-3, dev)
+    return {"value": value, "unit": "cell-updates/s", "cells_per_block": cpb, "tb_depth": tb,
+            "ms_per_halfstep": statistics.median(step_ms) / HALFSTEPS_PER_STEP, "steps": steps,
+            "gpu_launches": launches, "tuning_seconds": tune_s,
+            "candidates": "cells_per_block 255 / 510 with one half-step per launch, two half-steps per launch"}
+
+
 def run_wcc(args, rank, world):
     import torch
 
@@ -512,6 +534,8 @@ def run_wcc(args, rank, world):
     if args.tb:
         results["mixed_tb2"] = tb_bench(pr, stream, max(2, min(args.steps, 10)), args.warmup, barrier, dev,
                                         cells_per_step, cells_per_launch, pk)
+        results["mixed_tuned"] = tuned_bench(pr, stream, max(2, min(args.steps, 10)), args.warmup, barrier, dev,
+                                             cells_per_step)
     if args.batch:
         results["batch"] = batch_bench(stream, max(2, min(args.steps, 5)), args.warmup,
                                        results["mixed"]["value"] / world, barrier)
@@ -889,23 +913,32 @@ def high_order_bench(args):
 
 
 # Floating-point operations per cell-update of the oracle's half-step as the
-# oracle writes it (derivative form, binomial Leibniz sums, each parent's
-# Cauchy-Kovalewski table counted once), limiter on: the output of
-# `python oracle/count_flops.py 1 P 1` (Burgers) and `2 P 1` (Euler).
+# oracle writes it (derivative form, binomial Leibniz sums, divisions by
+# constants, each parent's Cauchy-Kovalewski table counted once), limiter on:
+# the output of `python oracle/count_flops.py 1 P 1` (Burgers) and `2 P 1`
+# (Euler).  Reported beside the kernels' own counts, not used as a roofline.
 ORACLE_FLOPS = {(1, 1): 93.0, (1, 2): 191.0, (1, 3): 314.0, (1, 4): 502.0,
                 (2, 1): 517.0, (2, 2): 847.0, (2, 3): 1252.0, (2, 4): 1852.0, (2, 5): 2725.0, (2, 6): 3934.0}
+# FP64 operations per cell-update the Burgers FP64 kernel executes
+# (halfstep_fp64<BURGERS, P>, limiter on): DADD + DMUL + 2 DFMA thread
+# instructions of one launch at N = 2^20 (ncu, profiles/burgers_halfstep.md)
+# over the launch's cells, e.g. P = 3: (24167170 + 41019267 + 2 x 60018446) / 2^20.
+BURGERS_FP64_FLOPS = {1: 67.17, 2: 127.37, 3: 176.64, 4: 252.11}
 BURGERS_CFL = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2}
 
 
 def burgers_bench(args):
     """The Burgers workload (u_t + (u^2/2)_x = 0, periodic [0, 2 pi], seeded
-    u0 = 0.5 + 8 Fourier modes, limiter on) at N = 2^10, 2^14, 2^18, 2^20,
-    P = 1..4 (CFL 0.4 / 0.3 / 0.25 / 0.2), FP64 and FP32-mixed.  Per case:
+    u0 = 0.5 + 8 Fourier modes, limiter on) at N = 2^10, 2^14, 2^18, 2^20
+    (--burgers-log2n), P = 1..4 (CFL 0.4 / 0.3 / 0.25 / 0.2), FP64,
+    FP32-mixed, and FP32-mixed with two half-steps per launch.  Per case:
     cell-updates/s over graphs of 32 half-steps with CUDA events (inputs
     resident; from the initial data: the kernels' work does not depend on
     the state), the HBM fraction at the algorithmic bytes (one read and one
-    write of the state: 16 (P + 1) B in FP64, 2 (8 + 4 P) B in FP32-mixed)
-    and, for FP64, the fraction of the FP64 peak at the oracle's flop count;
+    write of the state per launch: 16 (P + 1) B in FP64, 2 (8 + 4 P) B in
+    FP32-mixed, half of that per cell-update with two half-steps per launch)
+    and, for FP64, the fraction of the FP64 peak at the kernel's executed
+    FP64 operations (BURGERS_FP64_FLOPS);
     time to 2 t_s (past the shock) for N <= 2^18; and the oracle on the host
     cores on a bounded sample (N = 2^14, CFL half-steps for about
     cpu_seconds / 8 per degree)."""
@@ -918,15 +951,17 @@ def burgers_bench(args):
     clocks = ClockSampler()
     clocks.start()
     rows = []
+    sizes = [int(x) for x in args.burgers_log2n.split(",")]
     for P in (1, 2, 3, 4):
         cfl = BURGERS_CFL[P]
-        for log2n in (10, 14, 18, 20):
+        for log2n in sizes:
             N = 1 << log2n
             pr = inputs.burgers_fourier(N, P)
             t_s = inputs.shock_time(inputs.burgers_fourier_data())
-            for prec, name in ((wcc.FP64, "fp64"), (wcc.FP32_MIXED, "fp32-mixed")):
+            for prec, name, tb in ((wcc.FP64, "fp64", 1), (wcc.FP32_MIXED, "fp32-mixed", 1),
+                                   (wcc.FP32_MIXED, "fp32-mixed-tb2", 2)):
                 with wcc.Solver(pr.system, N, P, (pr.x_l, pr.x_r), pr.bc, precision=prec,
-                                stream=stream.cuda_stream) as s:
+                                stream=stream.cuda_stream, tb_depth=tb) as s:
                     s.set_initial(pr.q0)
                     for _ in range(args.warmup):
                         s.step(HALFSTEPS_PER_STEP, cfl)
@@ -947,14 +982,15 @@ def burgers_bench(args):
                         k = s.step_until(2.0 * t_s, cfl)
                         tts = {"t_end": 2.0 * t_s, "halfsteps": k, "seconds": time.perf_counter() - t0}
                 rate = N / (ms * 1e-3)
-                bpc = 16 * (P + 1) if prec == wcc.FP64 else 2 * (8 + 4 * P)
+                bpc = 16 * (P + 1) if prec == wcc.FP64 else 2 * (8 + 4 * P) / tb
                 row = {"workload": f"burgers1d-fourier8-N2^{log2n}-P{P}-periodic-cfl{cfl}", "N": N, "P": P,
                        "precision": name, "ms_per_halfstep": ms, "cell_updates_per_s": rate,
                        "bytes_per_cell_update": bpc, "hbm_gbs": bpc * rate / 1e9,
                        "hbm_frac": bpc * rate / 1e9 / pk["hbm_gbs"], "time_to_2ts": tts}
                 if prec == wcc.FP64:
-                    tf = ORACLE_FLOPS[(1, P)] * rate / 1e12
-                    row.update({"oracle_flops_per_cell_update": ORACLE_FLOPS[(1, P)], "fp64_tflops": tf,
+                    tf = BURGERS_FP64_FLOPS[P] * rate / 1e12
+                    row.update({"fp64_flops_per_cell_update": BURGERS_FP64_FLOPS[P],
+                                "oracle_flops_per_cell_update": ORACLE_FLOPS[(1, P)], "fp64_tflops": tf,
                                 "fp64_frac": tf / FP64_PEAK_TFLOPS})
                 rows.append(row)
                 print(json.dumps(row), flush=True)
@@ -975,7 +1011,7 @@ def burgers_bench(args):
     print(json.dumps({"clocks": clk, "peak_hbm_gbs": pk["hbm_gbs"], "peak_source": pk_kind,
                       "oracle_cell_updates_per_s": cpu, "oracle_cores": oracle.get_threads(),
                       "oracle_sample": "N = 2^14, CFL half-steps from the initial data"}), flush=True)
-    print("| P | N | precision | ms / half-step | cell-updates/s | of HBM | of FP64 peak (oracle flops) | "
+    print("| P | N | precision | ms / half-step | cell-updates/s | of HBM | of FP64 peak (kernel flops) | "
           "time to 2 t_s | oracle (host) |")
     print("|---|---|---|---|---|---|---|---|---|")
     for r in rows:
@@ -984,6 +1020,41 @@ def burgers_bench(args):
         print(f"| {r['P']} | 2^{int(math.log2(r['N']))} | {r['precision']} | {r['ms_per_halfstep']:.4f} | "
               f"{r['cell_updates_per_s'] / 1e9:.2f} G | {r['hbm_frac']:.3f} | {fr} | {tt} | "
               f"{cpu[r['P']] / 1e6:.2f} M |")
+
+
+def advection_config(args):
+    """The linear-advection workload: u0 = sin(pi x) on periodic [0, 2],
+    N = 200, P = 2, limiter off, to t = 2 (one period; the exact solution is
+    the initial data) at nu = 0.25 (the half-step reading of CFL 0.5), FP64.
+    Reports the time to solution through wcc_step_dt (host clock around the
+    synchronous run, second pass), L1 of the point values against the exact
+    translate, and the oracle's time and L1 on the host cores."""
+    import oracle
+    from paper_2104_04347_gb300 import inputs, wcc
+
+    pr = inputs.advection_sine(200, 2, 0.0, 2.0)
+    dts = oracle.constant_speed_dts(2.0, 0.25 * pr.dx)
+    x = inputs.centres(200, 0.0, 2.0, inputs.PERIODIC)
+    exact = np.sin(np.pi * x)
+    with wcc.Solver(pr.system, 200, 2, (0.0, 2.0), pr.bc, limiter=False) as s:
+        for _ in range(2):
+            s.set_initial(pr.q0)
+            t0 = time.perf_counter()
+            s.step_dt(dts)
+            q = s.get_dofs()
+            secs = time.perf_counter() - t0
+    oracle.set_threads(1)
+    sol = oracle.Solver(oracle.make_law(oracle.ADVECTION, 2, limiter=False), pr.q0, pr.dx)
+    t0 = time.perf_counter()
+    sol.step_dt(dts)
+    osecs = time.perf_counter() - t0
+    row = {"workload": "advection1d-sine-N200-P2-periodic-nu0.25-t2", "halfsteps": len(dts),
+           "gpu_seconds": secs, "gpu_cell_updates_per_s": 200 * len(dts) / secs,
+           "l1_vs_exact": float(np.mean(np.abs(q[:, 0, 0] - exact))),
+           "max_vs_oracle": float(np.max(np.abs(q - sol.q))),
+           "oracle_seconds": osecs, "oracle_cell_updates_per_s": 200 * len(dts) / osecs, "oracle_cores": 1,
+           "note": "200 cells: the GPU run is bound by launch latency, one launch per half-step"}
+    print(json.dumps(row), flush=True)
 
 
 def paper_workloads_2d(n=1200):
@@ -1038,6 +1109,9 @@ def main():
         return
     if args.burgers:
         burgers_bench(args)
+        return
+    if args.advection:
+        advection_config(args)
         return
     if args.two_d:
         two_d_bench(args)

@@ -75,8 +75,14 @@ enum {
  *   value is used for P = 1, where the paper does not state it),
  *   eps = 1e-40 (Eq. 1D2ndOrderWeights), gamma = 1.4, adv_speed = 1,
  *   graph_chunk = 32 (half-steps per captured CUDA graph; 0 disables graphs),
- *   tb_depth = 1, tb_cfl_growth = 0.1 (see below),
+ *   tb_depth = 1, tb_cfl_growth = 0.1 (see below), cells_per_block = 0,
  *   cuda_stream = NULL (the handle creates its own non-blocking stream).
+ *
+ * cells_per_block: new cells per CTA of the one-half-step kernel.  0 takes
+ * the compiled default of the degree; FP32-mixed also offers 255 and 510
+ * (one or two 255-cell tiles per CTA; the default is 510 for P <= 2 and 255
+ * above); plain FP32 only its default; FP64 only 127.  Other values are
+ * WCC_E_INVAL.  wcc_autotune picks it, with tb_depth, by timing.
  *
  * tb_depth (temporal blocking): half-steps per pass over the state in
  * device memory, 1 or 2 (0 reads as 1).  With 2 (FP32 variants only,
@@ -101,6 +107,8 @@ typedef struct {
     int tb_depth;
     void* cuda_stream; /* cudaStream_t to run on, or NULL */
     double tb_cfl_growth;
+    int cells_per_block;
+    int reserved;
 } wcc_options;
 
 typedef struct wcc_ctx* wcc_handle;
@@ -138,6 +146,20 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count);
  * cfl > 0.  Asynchronous on the handle's stream (with tb_depth = 2: the
  * half-steps go in pairs and the call waits for them, see wcc_options). */
 int wcc_step(wcc_handle h, int64_t nsteps, double cfl);
+
+/* Autotuner of the single-grid launch: times every compiled launch
+ * configuration of the handle -- for FP32-mixed cells_per_block 255 and 510
+ * with one half-step per launch, and two half-steps per launch -- on the
+ * handle's own current stage at CFL number cfl (a warm-up graph, then three
+ * graphs of graph_chunk half-steps each, CUDA events on the handle's
+ * stream), keeps the fastest in the handle's options and reports it in
+ * *cells_per_block and *tb_depth (either may be NULL).  The stage, its time
+ * and step count and the dt history are restored afterwards (the launch
+ * count is not).  FP64 and plain FP32 handles have one configuration each,
+ * which is returned untimed.  Allocates a copy of the stage while it runs.
+ * Synchronous.  Errors: WCC_E_STATE before wcc_set_initial, WCC_E_INVAL
+ * (cfl), WCC_E_NOMEM, WCC_E_CUDA. */
+int wcc_autotune(wcc_handle h, double cfl, int* cells_per_block, int* tb_depth);
 
 /* Two-half-step launches (tb_depth = 2) since wcc_set_initial: *pairs (may
  * be NULL) receives the pairs taken, *fallbacks the pairs refused by the CFL

@@ -13,6 +13,7 @@
 #include "../../include/wcc.h"
 #include "wcc_launch.h"
 #include "wcc_convert.cuh"
+#include "wcc_mixed2.cuh"
 #include "wcc_ff.cuh"
 #include "wcc_scheme.cuh"
 #include "wcc_trace.h"
@@ -254,6 +255,8 @@ StepArgs make_args(wcc_ctx* h, int cur, int parity, double cfl, double dt_fixed)
     a.alpha_f = (float)h->opt.alpha;
     a.n_mid = stage_cells(h, parity ^ 1);
     a.tb_nu_max = std::min(cfl * (1.0 + h->opt.tb_cfl_growth), h->tb_limit);
+    a.tiles_per_cta = (h->opt.precision == WCC_FP64 || h->opt.cells_per_block == 0)
+                          ? 0 : h->opt.cells_per_block / kTileMixed;
     return a;
 }
 
@@ -496,6 +499,8 @@ void wcc_default_options(wcc_options* opt) {
     opt->tb_depth = 1;
     opt->cuda_stream = nullptr;
     opt->tb_cfl_growth = 0.1;
+    opt->cells_per_block = 0;
+    opt->reserved = 0;
 }
 
 int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domain[2], int bc,
@@ -522,6 +527,14 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
         return fail(nullptr, WCC_E_INVAL, "tb_depth = 2 needs WCC_FP32_MIXED or WCC_FP32");
     if (!(o.tb_cfl_growth >= -1.0) || !(o.tb_cfl_growth < 1e6))
         return fail(nullptr, WCC_E_INVAL, "tb_cfl_growth must be a number >= -1");
+    {
+        const int c = o.cells_per_block;
+        const bool ok = c == 0 ||
+                        (o.precision == WCC_FP64 && c == kTile) ||
+                        (o.precision == WCC_FP32_MIXED && (c == kTileMixed || c == 2 * kTileMixed)) ||
+                        (o.precision == WCC_FP32 && c == kTileMixed * mixed_default_tiles(P));
+        if (!ok) return fail(nullptr, WCC_E_INVAL, "cells_per_block is not a compiled tile size for this precision");
+    }
     double tb_limit = 0.0;
     if (o.tb_depth == 2 && wcc_stability_limit(P, &tb_limit) != WCC_OK)
         return fail(nullptr, WCC_E_INVAL, "no stability limit for this P");
@@ -677,6 +690,109 @@ int wcc_tb_stats(wcc_handle h, int64_t* pairs, int64_t* fallbacks, double* nu2_m
     if (fallbacks) *fallbacks = h->tb_fallbacks;
     if (nu2_max) *nu2_max = s.tb_nu2_max;
     return rc;
+}
+
+int wcc_autotune(wcc_handle h, double cfl, int* cells_per_block, int* tb_depth) {
+    WccTraceRange trace_("wcc_autotune");
+    if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
+    if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
+    if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
+    struct Cand {
+        int cpb, tb;
+    };
+    Cand cands[3];
+    int nc = 0;
+    if (h->opt.precision == WCC_FP32_MIXED) {
+        cands[nc++] = {kTileMixed, 1};
+        cands[nc++] = {2 * kTileMixed, 1};
+        cands[nc++] = {0, 2};
+    }
+    const wcc_options saved = h->opt;
+    if (nc == 0) {  // one compiled configuration
+        if (cells_per_block) *cells_per_block = saved.cells_per_block;
+        if (tb_depth) *tb_depth = saved.tb_depth;
+        return WCC_OK;
+    }
+    const int chunk = h->opt.graph_chunk >= 2 ? h->opt.graph_chunk : 32;
+    int rc = ensure_history(h, h->steps + 4 * chunk + 2);
+    if (rc != WCC_OK) return rc;
+    // the state to return to: the current stage, the device state, the
+    // host-side position and the pair counters
+    DevState st0;
+    if ((rc = read_state(h, &st0)) != WCC_OK) return rc;
+    if (h->tb_limit == 0.0 && wcc_stability_limit(h->P, &h->tb_limit) != WCC_OK)
+        return fail(h, WCC_E_INVAL, "no stability limit for this P");
+    const int cur0 = h->cur, parity0 = h->parity;
+    const long long steps0 = h->steps, pairs0 = h->tb_pairs, fb0 = h->tb_fallbacks;
+    const size_t bytes = (size_t)((long long)h->nv * (h->K + 1) * h->pitch) * sizeof(float);
+    float* copy = nullptr;
+    if (cudaMalloc(&copy, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, WCC_E_NOMEM, "cudaMalloc of the autotuner's stage copy failed");
+    }
+    auto restore = [&]() -> int {
+        WCC_CHECK(h, cudaMemcpyAsync(h->s32[cur0], copy, bytes, cudaMemcpyDeviceToDevice, h->stream));
+        WCC_CHECK(h, cudaMemcpyAsync(h->st, &st0, sizeof(DevState), cudaMemcpyHostToDevice, h->stream));
+        WCC_CHECK(h, cudaStreamSynchronize(h->stream));
+        h->cur = cur0;
+        h->parity = parity0;
+        h->steps = steps0;
+        h->tb_pairs = pairs0;
+        h->tb_fallbacks = fb0;
+        return WCC_OK;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    float best_ms = 0.f;
+    int best = -1;
+    rc = cudaMemcpyAsync(copy, h->s32[cur0], bytes, cudaMemcpyDeviceToDevice, h->stream) == cudaSuccess &&
+                 cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess
+             ? WCC_OK
+             : cuda_fail(h, cudaGetLastError(), "autotuner set-up");
+    for (int i = 0; i < nc && rc == WCC_OK; ++i) {
+        h->opt.cells_per_block = cands[i].cpb;
+        h->opt.tb_depth = cands[i].tb;
+        if (h->gexec) {
+            cudaGraphExecDestroy(h->gexec);
+            h->gexec = nullptr;
+        }
+        if ((rc = restore()) != WCC_OK) break;
+        if ((rc = wcc_step(h, chunk, cfl)) != WCC_OK) break;  // warm-up (and graph capture)
+        DevState warm;
+        if ((rc = read_state(h, &warm)) != WCC_OK) break;
+        cudaEventRecord(e0, h->stream);
+        for (int r = 0; r < 3 && rc == WCC_OK; ++r) rc = wcc_step(h, chunk, cfl);
+        cudaEventRecord(e1, h->stream);
+        if (rc != WCC_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = cuda_fail(h, cudaGetLastError(), "autotuner timing");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (best < 0 || ms < best_ms) {
+            best_ms = ms;
+            best = i;
+        }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    h->opt = saved;
+    if (best >= 0 && rc == WCC_OK) {
+        h->opt.cells_per_block = cands[best].cpb;
+        h->opt.tb_depth = cands[best].tb;
+    }
+    if (h->gexec) {
+        cudaGraphExecDestroy(h->gexec);
+        h->gexec = nullptr;
+    }
+    const int rrc = restore();
+    cudaFree(copy);
+    if (rc != WCC_OK) return rc;
+    if (rrc != WCC_OK) return rrc;
+    if (cells_per_block) *cells_per_block = h->opt.cells_per_block;
+    if (tb_depth) *tb_depth = h->opt.tb_depth;
+    return WCC_OK;
 }
 
 int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts) {

@@ -281,6 +281,8 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
         return bfail(nullptr, WCC_E_INVAL, "need eps >= 0, alpha > 0, gamma > 1, graph_chunk >= 0");
     if (o.tb_depth != 0 && o.tb_depth != 1)
         return bfail(nullptr, WCC_E_INVAL, "batches advance one half-step per launch (tb_depth 1)");
+    if (o.cells_per_block != 0 && o.cells_per_block != kTileMixed)
+        return bfail(nullptr, WCC_E_INVAL, "batches use tiles of 255 new cells (cells_per_block 0 or 255)");
     int degrees[2] = {0, 0}, nd = 0;
     for (int64_t i = 0; i < count; ++i) {
         if (P[i] < 1 || P[i] > 4) return bfail(nullptr, WCC_E_INVAL, "every P must be in 1..4");

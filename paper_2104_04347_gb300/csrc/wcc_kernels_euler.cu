@@ -1,3 +1,4 @@
-// Kernels for the euler system.
+// FP64 half-step kernels, the stage bound and the dispatcher of the euler system.
 #define WCC_SYSTEM ::wcc::EULER
+#define WCC_KERNELS_PART 0
 #include "wcc_kernels.inc"

@@ -1,0 +1,4 @@
+// FP32-variant half-step kernels and the FP32 stage set-up of the euler system.
+#define WCC_SYSTEM ::wcc::EULER
+#define WCC_KERNELS_PART 1
+#include "wcc_kernels.inc"

@@ -11,6 +11,11 @@ namespace wcc {
 // One fused half-step over a whole stage: grid = ceil(n_new / kTile) CTAs.
 template <int SYS>
 cudaError_t launch_halfstep(int P, int precision, const StepArgs& args, cudaStream_t stream);
+// its FP64 and FP32-variant parts (compiled in separate translation units)
+template <int SYS>
+cudaError_t launch_halfstep_fp64(int P, const StepArgs& args, cudaStream_t stream);
+template <int SYS>
+cudaError_t launch_halfstep_mixed(int P, int precision, const StepArgs& args, cudaStream_t stream);
 
 // Two half-steps in one launch (FP32 variants, P <= 4; halfstep_mixed2_tb2):
 // args.in32 -> args.out32 with args.n_mid cells in between;

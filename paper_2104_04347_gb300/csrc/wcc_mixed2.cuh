@@ -50,9 +50,11 @@ constexpr int kTileMixed = 2 * kThreadsMixed - 1;
 // Consecutive tiles per CTA of the single-grid kernel: 2 for P <= 2 (one
 // CTA reduction for two tiles; measured faster), 1 for P >= 3 (measured
 // slower with 2).
+__host__ __device__ constexpr int mixed_default_tiles(int P) { return P <= 2 ? 2 : 1; }
+
 template <int P>
 constexpr int mixed_tiles_per_cta() {
-    return P <= 2 ? 2 : 1;
+    return mixed_default_tiles(P);
 }
 
 template <int P>
@@ -607,10 +609,11 @@ __device__ __forceinline__ void mixed_tile2(const TileIO& io, const ff lam, cons
     speed = mixed_store<SYS, P>(io, ubn, d, va, vb, args, err);
 }
 
-template <int SYS, int P, bool COMP = true>
+// One half-step over a stage; each CTA handles TPC consecutive tiles
+// (kTileMixed new cells each), one CTA reduction for all of them.
+template <int SYS, int P, bool COMP = true, int TPC = mixed_tiles_per_cta<P>()>
 __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_mixed2(const StepArgs args) {
     __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
-    constexpr int TPC = mixed_tiles_per_cta<P>();
     const StepSize z = step_size(args);
     float speed = 0.f;
     unsigned err = 0u;

@@ -98,6 +98,10 @@ struct StepArgs {
     // may take with the pair's dt
     long long n_mid;
     double tb_nu_max;
+    // FP32 variants: tiles of the single-half-step kernel per CTA (0: the
+    // degree's default)
+    int tiles_per_cta;
+    int pad2_;
 };
 
 // dt and lam of this launch (the same values in every thread).

@@ -45,6 +45,8 @@ class Options(ctypes.Structure):
         ("tb_depth", ctypes.c_int),
         ("cuda_stream", ctypes.c_void_p),
         ("tb_cfl_growth", ctypes.c_double),
+        ("cells_per_block", ctypes.c_int),
+        ("reserved", ctypes.c_int),
     ]
 
 
@@ -79,6 +81,8 @@ _SIGS = {
     "wcc_step": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, ctypes.c_double]),
     "wcc_step_dt": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp]),
     "wcc_tb_stats": (ctypes.c_int, [ctypes.c_void_p, _i64p, _i64p, _dp]),
+    "wcc_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_int),
+                                    ctypes.POINTER(ctypes.c_int)]),
     "wcc_step_until": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.c_double,
                                       ctypes.POINTER(ctypes.c_int64)]),
     "wcc_get_dofs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
@@ -204,7 +208,7 @@ class Solver:
     def __init__(self, system: int, N: int, P: int, domain, bc: int, *, precision: int = FP64,
                  limiter: bool = True, alpha: float = 2.0, eps: float = 1e-40, gamma: float = 1.4,
                  adv_speed: float = 1.0, graph_chunk: int = 32, stream: int | None = None, tb_depth: int = 1,
-                 tb_cfl_growth: float = 0.1):
+                 tb_cfl_growth: float = 0.1, cells_per_block: int = 0):
         self.lib = load()
         o = default_options()
         o.precision = precision
@@ -217,6 +221,7 @@ class Solver:
         o.cuda_stream = stream
         o.tb_depth = tb_depth
         o.tb_cfl_growth = tb_cfl_growth
+        o.cells_per_block = cells_per_block
         h = ctypes.c_void_p()
         dom = (ctypes.c_double * 2)(float(domain[0]), float(domain[1]))
         rc = self.lib.wcc_create(ctypes.byref(h), system, int(N), int(P), dom, bc, ctypes.byref(o))
@@ -267,6 +272,13 @@ class Solver:
     def step_dt(self, dts) -> None:
         d = np.ascontiguousarray(dts, dtype=np.float64)
         self._check(self.lib.wcc_step_dt(self.h, d.size, d.ctypes.data_as(_dp)))
+
+    def autotune(self, cfl: float):
+        """Time the compiled launch configurations on the current stage, keep
+        the fastest; returns (cells_per_block, tb_depth)."""
+        cpb, tb = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.wcc_autotune(self.h, float(cfl), ctypes.byref(cpb), ctypes.byref(tb)))
+        return cpb.value, tb.value
 
     def tb_stats(self):
         """(pairs taken, pairs refused and re-done singly, largest second

@@ -98,3 +98,12 @@ def test_create_rejects_bad_temporal_blocking(kw, needle):
 def test_default_temporal_blocking_options():
     o = wcc.default_options()
     assert o.tb_depth == 1 and o.tb_cfl_growth == 0.1
+
+
+@pytest.mark.parametrize("precision,cpb", [(wcc.FP64, 255), (wcc.FP32_MIXED, 127), (wcc.FP32_MIXED, 300),
+                                           (wcc.FP32, 510)])
+def test_create_rejects_tile_sizes_that_are_not_compiled(precision, cpb):
+    # P = 3: FP64 tiles are 127 cells, FP32-mixed 255 or 510, plain FP32 255
+    with pytest.raises(wcc.WCCError) as ei:
+        wcc.Solver(2, 64, 3, (0.0, 1.0), 1, precision=precision, cells_per_block=cpb)
+    assert ei.value.code == -1 and "cells_per_block" in str(ei.value)
