@@ -588,7 +588,8 @@ def run_wcc(args, rank, world):
 
 def precision_sweep(max_log2n=16):
     """Smooth Euler density wave rho = 1 + 0.2 sin 2 pi x, u = 1, p = 1,
-    periodic [0, 1], to t = 1, P = 1..4, N = 2^8 .. 2^max_log2n: every
+    periodic [0, 1], to t = 1, P = 1..4 at N = 2^8 .. 2^max_log2n and
+    P = 5, 6 at N = 2^4 .. 2^11: every
     precision on the same half-step sizes; L1 of the density point values
     against the exact solution and against the FP64 path (and the oracle for
     N <= 2^10), and the measured order.  Prints one JSON line per case and a
@@ -599,13 +600,16 @@ def precision_sweep(max_log2n=16):
     from paper_2104_04347_gb300 import inputs, wcc
 
     oracle.set_threads(os.cpu_count() or 1)
-    nu = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2}
+    nu = {1: 0.4, 2: 0.3, 3: 0.25, 4: 0.2, 5: 0.16, 6: 0.14}
     amax = 1.0 + math.sqrt(1.4 / 0.8)
     names = {wcc.FP64: "fp64", wcc.FP32_MIXED: "fp32-mixed", wcc.FP32: "fp32"}
     rows = []
-    for P in (1, 2, 3, 4):
+    for P in (1, 2, 3, 4, 5, 6):
         prev = {}
-        for log2n in range(8, max_log2n + 1):
+        # P = 5, 6 reach the FP64 rounding floor by 2^10 cells; finer meshes
+        # only take longer
+        top = max_log2n if P <= 4 else min(max_log2n, 11)
+        for log2n in range(8 if P <= 4 else 4, top + 1):
             N = 1 << log2n
             pr = inputs.euler_density_wave(N, P)
             dts = oracle.constant_speed_dts(1.0, nu[P] * pr.dx / amax)

@@ -116,9 +116,8 @@ typedef struct wcc_ctx* wcc_handle;
 void wcc_default_options(wcc_options* opt);
 
 /* Create a solver for `system` on [domain[0], domain[1]] with N cells of
- * width dx and polynomial degree P (order P+1, Sec. 2.1): 1 <= P <= 6 with
- * WCC_FP64, 1 <= P <= 4 with WCC_FP32_MIXED and WCC_FP32 (WCC_E_INVAL
- * otherwise).  The paper prints CFL numbers up to P = 3; the von Neumann
+ * width dx and polynomial degree P (order P+1, Sec. 2.1): 1 <= P <= 6 in
+ * every precision (WCC_E_INVAL otherwise).  The paper prints CFL numbers up to P = 3; the von Neumann
  * limits of the linear scheme (Sec. 2.3) are 0.282, 0.212 and 0.185 at
  * P = 4, 5, 6, and the CFL number must stay below them.
  * 4 <= N <= 2^31; bc is WCC_BC_PERIODIC or WCC_BC_TRANSMISSIVE.  opt may
@@ -225,7 +224,13 @@ typedef struct wcc_batch_ctx* wcc_batch;
 
 /* count instances; N[count], P[count] (1..4, at most two distinct values),
  * domains[2*count] (x_L, x_R per instance), bcs[count]; opt may be NULL but
- * opt->precision must be WCC_FP32_MIXED when given. */
+ * opt->precision must be WCC_FP32_MIXED when given.  opt->tb_depth 2 (two
+ * half-steps per launch, one dt per instance and pair, as for a single
+ * problem) is taken for the degree mixes {2}, {3} and {2, 3} only; a pair is
+ * refused for the whole batch when any instance's second half-step would
+ * exceed its bound (opt->tb_cfl_growth, capped at the degree's linear
+ * stability limit) and the batch then takes the two half-steps singly.
+ * opt->cells_per_block must be 0 or 255 (the batch kernel's tile). */
 int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N, const int* P,
                      const double* domains, const int* bcs, const wcc_options* opt);
 int wcc_batch_dof_count(wcc_batch b, int64_t* count);
@@ -242,10 +247,20 @@ int wcc_batch_get_dt_history(wcc_batch b, int64_t instance, double* dts, int64_t
 /* Persistent grid of the step kernel in CTAs (0: all resident CTAs). */
 int wcc_batch_set_grid(wcc_batch b, int ctas);
 /* Time the candidate grids (1..max resident CTAs per SM, and one CTA per
- * tile) over a few half-steps of this batch with this CFL number, keep the
- * fastest, and restore the batch state; *ctas (may be NULL) receives it.
- * Allocates a temporary copy of the current stage.  Synchronous. */
+ * tile), each with one half-step per launch and, where the degree mix has
+ * the kernel (degrees {2}, {3}, {2, 3}), two; keep the fastest pair of grid
+ * and pass depth, and restore the batch state.  Timed over eight half-steps
+ * of this batch with this CFL number.  *ctas (may be NULL) receives the grid;
+ * wcc_batch_get_tuning reports both.  Allocates a temporary copy of the
+ * current stage.  Synchronous. */
 int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas);
+/* The launch configuration in use: *ctas the persistent grid of the step
+ * kernel, *tb_depth half-steps per launch (1 or 2).  Either may be NULL. */
+int wcc_batch_get_tuning(wcc_batch b, int* ctas, int* tb_depth);
+/* Two-half-step launches of a batch: *pairs taken, *fallbacks refused (a
+ * refused pair leaves every instance untouched and is re-done as two single
+ * half-steps).  Either may be NULL.  Synchronises the batch's stream. */
+int wcc_batch_tb_stats(wcc_batch b, int64_t* pairs, int64_t* fallbacks);
 int wcc_batch_synchronize(wcc_batch b);
 int wcc_batch_launch_count(wcc_batch b, int64_t* launches);
 int wcc_batch_device_bytes(wcc_batch b, int64_t* bytes);

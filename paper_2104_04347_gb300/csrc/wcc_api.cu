@@ -128,6 +128,8 @@ cudaError_t launch_planes_to_aos_mixed(int K, unsigned grid, cudaStream_t s, con
         case 3: planes_to_aos_mixed<3><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
         case 4: planes_to_aos_mixed<4><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
         case 5: planes_to_aos_mixed<5><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
+        case 6: planes_to_aos_mixed<6><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
+        case 7: planes_to_aos_mixed<7><<<grid, kConvThreads, 0, s>>>(planes, n, nv, pitch, aos); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -517,7 +519,6 @@ int wcc_create(wcc_handle* out, int system, int64_t N, int P, const double domai
     if (opt) o = *opt;
     if (o.precision != WCC_FP64 && o.precision != WCC_FP32_MIXED && o.precision != WCC_FP32)
         return fail(nullptr, WCC_E_INVAL, "precision must be WCC_FP64, WCC_FP32_MIXED or WCC_FP32");
-    if (o.precision != WCC_FP64 && P > 4) return fail(nullptr, WCC_E_INVAL, "P > 4 needs WCC_FP64");
     if (!(o.eps >= 0.0) || !(o.alpha > 0.0) || !(o.gamma > 1.0))
         return fail(nullptr, WCC_E_INVAL, "need eps >= 0, alpha > 0, gamma > 1");
     if (o.graph_chunk < 0) return fail(nullptr, WCC_E_INVAL, "graph_chunk must be >= 0");

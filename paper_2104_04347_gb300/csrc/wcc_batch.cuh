@@ -41,6 +41,11 @@ struct BatchArgs {
     long long total_tiles;
     int ninst;
     int parity;
+    // two half-steps per launch: the second half-step's largest CFL number
+    // per group, the states before the launch, the batch's refusal flag
+    double nu_max[2];
+    DevState* tb_backup;
+    unsigned* tb_refused;
 };
 
 
@@ -73,6 +78,50 @@ __global__ void __launch_bounds__(kThreadsMixed, (mixed_min_ctas<PA>() < mixed_m
             mixed_tile2<SYS, PB, true, true>(io, ff_make(z.lam_hi, z.lam_lo), ph, rec, speed, err);
         reduce_and_finish<float, kThreadsMixed>(speed, err, z.dt, st, ntiles, b.hist + (long long)i * b.hist_cap, b.hist_cap,
                                  b.parity, 1, b.phys.cfl, I.dx);
+    }
+}
+
+// Two half-steps per launch for every instance (mixed_pair_tile): each
+// instance is cut into tiles of kTileTB final cells (tile list in
+// tile_start / tile_inst), a persistent grid walks the list, and each
+// instance's last tile does the instance's pair bookkeeping (finalize_pair),
+// first keeping the instance's state in tb_backup.  If any instance refuses
+// its pair, the batch's flag is set and the caller restores every instance
+// from tb_backup (the launch did not overwrite the input stages) and takes
+// that pair as two single half-steps; launches that find the flag set do
+// nothing.
+template <int SYS, int PA, int PB>
+__global__ void __launch_bounds__(kThreadsMixed, (mixed_min_ctas<PA>() < mixed_min_ctas<PB>() ? mixed_min_ctas<PA>()
+                                                                                            : mixed_min_ctas<PB>()))
+    batch_mixed_tb2(const BatchArgs b) {
+    constexpr int SA = mixed2_smem_float2<SYS, PA>();
+    constexpr int SB = mixed2_smem_float2<SYS, PB>();
+    __shared__ float2 rec[SA > SB ? SA : SB];
+    if (*(volatile unsigned*)b.tb_refused) return;
+    for (long long tile = blockIdx.x; tile < b.total_tiles; tile += gridDim.x) {
+        const int i = __ldg(b.tile_inst + tile);
+        const BatchInstance I = b.inst[i];
+        DevState* st = b.st + i;
+        const long long first = __ldg(b.tile_start + i);
+        const long long ntiles = __ldg(b.tile_start + i + 1) - first;
+        const StepSize z = cfl_step_size(st, b.phys.cfl_bits, b.phys.cfl, I.dx, b.parity);
+        const int g = I.group;
+        const PairIO io{b.in[g] + I.offset, b.out[g] + I.offset, b.pitch[g], I.cells[b.parity],
+                        I.cells[b.parity ^ 1], I.cells[b.parity], (tile - first) * kTileTB, b.parity, I.bc};
+        StepArgs ph = b.phys;  // per-instance boundary and mesh width
+        ph.bc = I.bc;
+        ph.dx = I.dx;
+        const ff2 lam2{f2(z.lam_hi), f2(z.lam_lo)};
+        float mid = 0.f, fin = 0.f;
+        unsigned err = 0u;
+        // both degrees share one register budget: both park (see mixed_parent_records)
+        if (g == 0)
+            mixed_pair_tile<SYS, PA, true, true>(io, lam2, ph, rec, mid, fin, err);
+        else
+            mixed_pair_tile<SYS, PB, true, true>(io, lam2, ph, rec, mid, fin, err);
+        const PairBook bk{st, b.hist + (long long)i * b.hist_cap, b.hist_cap, ntiles, I.dx, b.phys.cfl, b.nu_max[g],
+                          1, b.parity, b.tb_backup + i, b.tb_refused};
+        finish_pair(mid, fin, err, z.dt, bk);
     }
 }
 

@@ -60,6 +60,20 @@ struct wcc_batch_ctx {
     double g_cfl = 0.0;
     unsigned g_grid = 0;
 
+    // two half-steps per launch (tb_depth = 2): tiles of kTileTB final cells
+    long long* d_tiles_pair[2] = {nullptr, nullptr};
+    int* d_inst_pair[2] = {nullptr, nullptr};
+    long long tiles_pair[2] = {0, 0};
+    DevState* d_backup = nullptr;  // every instance's state before the latest pair launch
+    unsigned* d_refused = nullptr; // set when an instance refuses its pair
+    double tb_limit[2] = {0.0, 0.0};  // stability limit of each group's degree
+    cudaGraphExec_t gexec_tb = nullptr;
+    int gt_cur = -1, gt_parity = -1, gt_pairs = 0;
+    double gt_cfl = 0.0;
+    unsigned gt_grid = 0;
+    long long tb_pairs = 0, tb_fallbacks = 0;
+    bool pairs_compiled = false;  // the degree mix has a two-half-step kernel
+
     long long launches = 0;
     std::string err;
 };
@@ -111,7 +125,17 @@ BatchArgs make_bargs(wcc_batch_ctx* b, int cur, int parity, double cfl, int kind
         a.out[g] = b->planes[g][kind == BATCH_STEP ? cur ^ 1 : cur];
         a.pitch[g] = b->pitch[g];
     }
-    if (kind == BATCH_STEP) {
+    if (kind == BATCH_PAIR) {
+        for (int g = 0; g < 2; ++g) {
+            a.out[g] = b->planes[g][cur ^ 1];
+            a.nu_max[g] = std::min(cfl * (1.0 + b->opt.tb_cfl_growth), b->tb_limit[g]);
+        }
+        a.tile_start = b->d_tiles_pair[parity];
+        a.tile_inst = b->d_inst_pair[parity];
+        a.total_tiles = b->tiles_pair[parity];
+        a.tb_backup = b->d_backup;
+        a.tb_refused = b->d_refused;
+    } else if (kind == BATCH_STEP) {
         a.tile_start = b->d_tiles_step[parity];
         a.tile_inst = b->d_inst_step[parity];
         a.total_tiles = b->tiles_step[parity];
@@ -215,8 +239,56 @@ int build_graph(wcc_batch_ctx* b, int chunk, double cfl) {
     return WCC_OK;
 }
 
+int enqueue_pair(wcc_batch_ctx* b, int cur, int parity, double cfl, unsigned grid) {
+    BatchArgs a = make_bargs(b, cur, parity, cfl, BATCH_PAIR);
+    cudaError_t e = launch(b, BATCH_PAIR, a, nullptr, 0, grid);
+    if (e != cudaSuccess) return bfail(b, WCC_E_CUDA, std::string("batched two-half-step launch: ") + cudaGetErrorString(e));
+    return WCC_OK;
+}
+
+// `pairs` (even) two-half-step launches from the current buffer in one graph.
+int build_graph_pairs(wcc_batch_ctx* b, int pairs, double cfl) {
+    if (b->gexec_tb) {
+        cudaGraphExecDestroy(b->gexec_tb);
+        b->gexec_tb = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    WCC_BCHECK(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int cur = b->cur;
+    for (int s = 0; s < pairs; ++s) {
+        BatchArgs a = make_bargs(b, cur, b->parity, cfl, BATCH_PAIR);
+        cudaError_t e = launch(b, BATCH_PAIR, a, nullptr, 0, b->grid);
+        if (e != cudaSuccess) {
+            cudaStreamEndCapture(b->stream, &g);
+            if (g) cudaGraphDestroy(g);
+            return bfail(b, WCC_E_CUDA, std::string("launch during capture: ") + cudaGetErrorString(e));
+        }
+        cur ^= 1;
+    }
+    WCC_BCHECK(b, cudaStreamEndCapture(b->stream, &g));
+    cudaError_t e = cudaGraphInstantiate(&b->gexec_tb, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        b->gexec_tb = nullptr;
+        return bfail(b, WCC_E_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    b->gt_cur = b->cur;
+    b->gt_parity = b->parity;
+    b->gt_cfl = cfl;
+    b->gt_pairs = pairs;
+    b->gt_grid = b->grid;
+    return WCC_OK;
+}
+
 void release(wcc_batch_ctx* b) {
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
+    if (b->gexec_tb) cudaGraphExecDestroy(b->gexec_tb);
+    for (int s = 0; s < 2; ++s) {
+        if (b->d_tiles_pair[s]) cudaFree(b->d_tiles_pair[s]);
+        if (b->d_inst_pair[s]) cudaFree(b->d_inst_pair[s]);
+    }
+    if (b->d_backup) cudaFree(b->d_backup);
+    if (b->d_refused) cudaFree(b->d_refused);
     for (int g = 0; g < 2; ++g)
         for (int i = 0; i < 2; ++i)
             if (b->planes[g][i]) cudaFree(b->planes[g][i]);
@@ -233,9 +305,8 @@ void release(wcc_batch_ctx* b) {
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
-int do_step(wcc_batch_ctx* b, long long nsteps, double cfl) {
-    int rc = ensure_hist(b, b->steps + nsteps);
-    if (rc != WCC_OK) return rc;
+int do_step_single(wcc_batch_ctx* b, long long nsteps, double cfl) {
+    int rc;
     long long left = nsteps;
     const int chunk = b->opt.graph_chunk;
     if (chunk >= 2 && left >= chunk) {
@@ -262,6 +333,71 @@ int do_step(wcc_batch_ctx* b, long long nsteps, double cfl) {
     return WCC_OK;
 }
 
+// nsteps half-steps as two-half-step launches (an odd last one single),
+// checked after the launches: if an instance refused its pair, every
+// instance goes back to its state before that launch (the launch left the
+// input stages as they were; the launches queued after it did nothing), the
+// pair is taken as two single half-steps, and the pairs resume.
+int do_step_pairs(wcc_batch_ctx* b, long long nsteps, double cfl) {
+    long long pairs = nsteps / 2;
+    const int graph_pairs = (b->opt.graph_chunk / 2) & ~1;
+    while (pairs > 0) {
+        const int cur0 = b->cur;
+        const long long steps0 = b->steps;
+        long long left = pairs;
+        int rc;
+        if (graph_pairs >= 2 && left >= graph_pairs) {
+            if (!b->gexec_tb || b->gt_cur != b->cur || b->gt_parity != b->parity || b->gt_cfl != cfl ||
+                b->gt_pairs != graph_pairs || b->gt_grid != b->grid) {
+                if ((rc = build_graph_pairs(b, graph_pairs, cfl)) != WCC_OK) return rc;
+            }
+            while (left >= graph_pairs) {
+                WCC_BCHECK(b, cudaGraphLaunch(b->gexec_tb, b->stream));
+                b->launches += graph_pairs;
+                b->steps += 2 * graph_pairs;
+                left -= graph_pairs;
+            }
+        }
+        for (; left > 0; --left) {
+            if ((rc = enqueue_pair(b, b->cur, b->parity, cfl, b->grid)) != WCC_OK) return rc;
+            b->launches += 1;
+            b->cur ^= 1;
+            b->steps += 2;
+        }
+        unsigned refused = 0;
+        WCC_BCHECK(b, cudaMemcpyAsync(&refused, b->d_refused, sizeof refused, cudaMemcpyDeviceToHost, b->stream));
+        WCC_BCHECK(b, cudaStreamSynchronize(b->stream));
+        if (!refused) {
+            b->tb_pairs += pairs;
+            break;
+        }
+        // back to the states before the refused launch, flags cleared
+        WCC_BCHECK(b, cudaMemcpyAsync(b->d_st, b->d_backup, sizeof(DevState) * b->count, cudaMemcpyDeviceToDevice,
+                                      b->stream));
+        WCC_BCHECK(b, cudaMemsetAsync(b->d_refused, 0, sizeof(unsigned), b->stream));
+        std::vector<DevState> st;
+        if ((rc = read_states(b, st)) != WCC_OK) return rc;
+        for (auto& x : st) x.err &= ~ERR_CFL;
+        WCC_BCHECK(b, cudaMemcpy(b->d_st, st.data(), sizeof(DevState) * b->count, cudaMemcpyHostToDevice));
+        const long long done_pairs = (st[0].step - steps0) / 2;
+        b->tb_pairs += done_pairs;
+        b->tb_fallbacks += 1;
+        b->cur = cur0 ^ (int)(done_pairs & 1);
+        b->steps = st[0].step;
+        if ((rc = do_step_single(b, 2, cfl)) != WCC_OK) return rc;
+        pairs -= done_pairs + 1;
+    }
+    if (nsteps & 1) return do_step_single(b, 1, cfl);
+    return WCC_OK;
+}
+
+int do_step(wcc_batch_ctx* b, long long nsteps, double cfl) {
+    int rc = ensure_hist(b, b->steps + nsteps);
+    if (rc != WCC_OK) return rc;
+    if (b->opt.tb_depth == 2) return do_step_pairs(b, nsteps, cfl);
+    return do_step_single(b, nsteps, cfl);
+}
+
 }  // namespace
 
 extern "C" {
@@ -279,8 +415,10 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
     if (o.precision != WCC_FP32_MIXED) return bfail(nullptr, WCC_E_INVAL, "batches run in WCC_FP32_MIXED precision");
     if (!(o.eps >= 0.0) || !(o.alpha > 0.0) || !(o.gamma > 1.0) || o.graph_chunk < 0)
         return bfail(nullptr, WCC_E_INVAL, "need eps >= 0, alpha > 0, gamma > 1, graph_chunk >= 0");
-    if (o.tb_depth != 0 && o.tb_depth != 1)
-        return bfail(nullptr, WCC_E_INVAL, "batches advance one half-step per launch (tb_depth 1)");
+    if (o.tb_depth == 0) o.tb_depth = 1;
+    if (o.tb_depth != 1 && o.tb_depth != 2) return bfail(nullptr, WCC_E_INVAL, "tb_depth must be 1 or 2");
+    if (!(o.tb_cfl_growth >= -1.0) || !(o.tb_cfl_growth < 1e6))
+        return bfail(nullptr, WCC_E_INVAL, "tb_cfl_growth must be a number >= -1");
     if (o.cells_per_block != 0 && o.cells_per_block != kTileMixed)
         return bfail(nullptr, WCC_E_INVAL, "batches use tiles of 255 new cells (cells_per_block 0 or 255)");
     int degrees[2] = {0, 0}, nd = 0;
@@ -307,6 +445,17 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
     if (nd == 1) degrees[1] = degrees[0];
     b->PA = std::min(degrees[0], degrees[1]);
     b->PB = std::max(degrees[0], degrees[1]);
+    const int mix = b->PA * 10 + b->PB;
+    b->pairs_compiled = mix == 22 || mix == 33 || mix == 23;
+    if (o.tb_depth == 2 && !b->pairs_compiled) {
+        delete b;
+        return bfail(nullptr, WCC_E_INVAL, "two half-steps per launch in a batch: degrees 2 and 3 only");
+    }
+    if (b->pairs_compiled && (wcc_stability_limit(b->PA, &b->tb_limit[0]) != WCC_OK ||
+                              wcc_stability_limit(b->PB, &b->tb_limit[1]) != WCC_OK)) {
+        delete b;
+        return bfail(nullptr, WCC_E_INVAL, "no stability limit for the batch's degrees");
+    }
     b->N.assign(N, N + count);
     b->P.assign(P, P + count);
     b->bc.assign(bcs, bcs + count);
@@ -354,6 +503,14 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
         }
         b->tiles_step[s] = ts[s][count];
         b->tiles_cur[s] = tc[s][count];
+    }
+    // pair tiles: kTileTB final cells of the stage of the same parity
+    std::vector<long long> tp[2];
+    for (int s = 0; s < 2; ++s) {
+        tp[s].assign(count + 1, 0);
+        for (int64_t k = 0; k < count; ++k)
+            tp[s][k + 1] = tp[s][k] + (b->inst[k].cells[s] + kTileTB - 1) / kTileTB;
+        b->tiles_pair[s] = tp[s][count];
     }
 
     if (o.cuda_stream) {
@@ -408,6 +565,18 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
         dmalloc((void**)&b->d_inst_step[s], sizeof(int) * std::max<long long>(b->tiles_step[s], 1));
         dmalloc((void**)&b->d_inst_cur[s], sizeof(int) * std::max<long long>(b->tiles_cur[s], 1));
     }
+    std::vector<int> ip[2];
+    if (b->pairs_compiled) {
+        for (int s = 0; s < 2; ++s) {
+            dmalloc((void**)&b->d_tiles_pair[s], sizeof(long long) * (count + 1));
+            ip[s].resize(b->tiles_pair[s]);
+            for (int64_t k = 0; k < count; ++k)
+                for (long long t = tp[s][k]; t < tp[s][k + 1]; ++t) ip[s][t] = (int)k;
+            dmalloc((void**)&b->d_inst_pair[s], sizeof(int) * std::max<long long>(b->tiles_pair[s], 1));
+        }
+        dmalloc((void**)&b->d_backup, sizeof(DevState) * count);
+        dmalloc((void**)&b->d_refused, sizeof(unsigned));
+    }
     dmalloc((void**)&b->staging, sizeof(double) * (size_t)std::max(b->aos_total[0], b->aos_total[1]));
     if (!ok) {
         release(b);
@@ -420,6 +589,15 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
         cudaMemcpyAsync(b->d_tiles_cur[s], tc[s].data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice, b->stream);
         cudaMemcpyAsync(b->d_inst_step[s], is[s].data(), sizeof(int) * is[s].size(), cudaMemcpyHostToDevice, b->stream);
         cudaMemcpyAsync(b->d_inst_cur[s], ic[s].data(), sizeof(int) * ic[s].size(), cudaMemcpyHostToDevice, b->stream);
+    }
+    if (b->pairs_compiled) {
+        for (int s = 0; s < 2; ++s) {
+            cudaMemcpyAsync(b->d_tiles_pair[s], tp[s].data(), sizeof(long long) * (count + 1), cudaMemcpyHostToDevice,
+                            b->stream);
+            cudaMemcpyAsync(b->d_inst_pair[s], ip[s].data(), sizeof(int) * ip[s].size(), cudaMemcpyHostToDevice,
+                            b->stream);
+        }
+        cudaMemsetAsync(b->d_refused, 0, sizeof(unsigned), b->stream);
     }
     cudaStreamSynchronize(b->stream);  // the host vectors go out of scope
     cudaMemsetAsync(b->d_st, 0, sizeof(DevState) * count, b->stream);
@@ -456,6 +634,7 @@ int wcc_batch_set_initial(wcc_batch b, const double* dofs, int64_t count) {
     b->cur = 0;
     b->parity = 0;
     b->steps = 0;
+    b->tb_pairs = b->tb_fallbacks = 0;
     BatchArgs a = make_bargs(b, 0, 0, 1.0, BATCH_CONVERT);
     cudaError_t e = launch(b, BATCH_CONVERT, a, b->staging, 1, aux_grid(b, a.total_tiles));
     if (e != cudaSuccess) return bfail(b, WCC_E_CUDA, std::string("layout conversion: ") + cudaGetErrorString(e));
@@ -531,6 +710,16 @@ int wcc_batch_get_dt_history(wcc_batch b, int64_t instance, double* dts, int64_t
     return rc;
 }
 
+int wcc_batch_tb_stats(wcc_batch b, int64_t* pairs, int64_t* fallbacks) {
+    if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    DeviceScope ds_(b->device);
+    std::vector<DevState> st;
+    int rc = read_states(b, st);
+    if (pairs) *pairs = b->tb_pairs;
+    if (fallbacks) *fallbacks = b->tb_fallbacks;
+    return rc;
+}
+
 int wcc_batch_set_grid(wcc_batch b, int ctas) {
     if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
     DeviceScope ds_(b->device);
@@ -544,12 +733,21 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
     DeviceScope ds_(b->device);
     if (!b->initialised) return bfail(b, WCC_E_STATE, "wcc_batch_set_initial has not been called");
     if (!(cfl > 0.0)) return bfail(b, WCC_E_INVAL, "cfl must be positive");
-    // Candidates: persistent grids of 1..max resident CTAs per SM, and one
-    // CTA per tile.  Each is timed over a few half-steps on the batch itself;
-    // the state is restored afterwards.
-    std::vector<unsigned> cand;
-    for (int k = 1; k <= b->max_ctas_per_sm; ++k) cand.push_back((unsigned)(k * b->sms));
-    cand.push_back((unsigned)std::min<long long>(std::max(b->tiles_step[0], b->tiles_step[1]), 1ll << 30));
+    // Candidates: persistent grids of 1..max resident CTAs per SM and one
+    // CTA per tile, each with one half-step per launch and (where the degree
+    // mix has the kernel) two.  Each is timed over eight half-steps on the
+    // batch itself; the state is restored afterwards.
+    struct Cand {
+        unsigned grid;
+        int tb;
+    };
+    std::vector<Cand> cand;
+    for (int tb = 1; tb <= (b->pairs_compiled ? 2 : 1); ++tb) {
+        for (int k = 1; k <= b->max_ctas_per_sm; ++k) cand.push_back({(unsigned)(k * b->sms), tb});
+        const long long tiles = tb == 1 ? std::max(b->tiles_step[0], b->tiles_step[1])
+                                        : std::max(b->tiles_pair[0], b->tiles_pair[1]);
+        cand.push_back({(unsigned)std::min<long long>(tiles, 1ll << 30), tb});
+    }
     const int G = b->PB == b->PA ? 1 : 2;
     size_t plane_bytes[2] = {0, 0};
     for (int g = 0; g < G; ++g)
@@ -572,6 +770,7 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
         }
         if (to_save) cudaMemcpyAsync(sp + off, b->d_st, sizeof(DevState) * b->count, cudaMemcpyDeviceToDevice, b->stream);
         else cudaMemcpyAsync(b->d_st, sp + off, sizeof(DevState) * b->count, cudaMemcpyDeviceToDevice, b->stream);
+        if (!to_save && b->d_refused) cudaMemsetAsync(b->d_refused, 0, sizeof(unsigned), b->stream);
     };
     int rc = ensure_hist(b, steps0 + 16);
     if (rc != WCC_OK) {
@@ -584,13 +783,23 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
     cudaEventCreate(&e1);
     float best = 1e30f;
     unsigned best_grid = b->grid;
-    for (unsigned grid : cand) {
+    int best_tb = b->opt.tb_depth;
+    for (const Cand& c : cand) {
+        const unsigned grid = c.grid;
         int cur = cur0, par = par0;
-        for (int s = 0; s < 10 && rc == WCC_OK; ++s) {
-            if (s == 2) cudaEventRecord(e0, b->stream);
-            rc = enqueue_step(b, cur, par, cfl, grid);
-            cur ^= 1;
-            par ^= 1;
+        if (c.tb == 1) {
+            for (int s = 0; s < 10 && rc == WCC_OK; ++s) {
+                if (s == 2) cudaEventRecord(e0, b->stream);
+                rc = enqueue_step(b, cur, par, cfl, grid);
+                cur ^= 1;
+                par ^= 1;
+            }
+        } else {
+            for (int s = 0; s < 5 && rc == WCC_OK; ++s) {
+                if (s == 1) cudaEventRecord(e0, b->stream);
+                rc = enqueue_pair(b, cur, par, cfl, grid);
+                cur ^= 1;
+            }
         }
         cudaEventRecord(e1, b->stream);
         if (rc != WCC_OK || cudaEventSynchronize(e1) != cudaSuccess) {
@@ -602,6 +811,7 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
         if (ms < best) {
             best = ms;
             best_grid = grid;
+            best_tb = c.tb;
         }
         restore_copy(false);
     }
@@ -611,10 +821,18 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
     cudaFree(save);
     if (rc != WCC_OK) return rc;
     b->grid = best_grid;
+    b->opt.tb_depth = best_tb;
     b->cur = cur0;
     b->parity = par0;
     b->steps = steps0;
     if (ctas_out) *ctas_out = (int)best_grid;
+    return WCC_OK;
+}
+
+int wcc_batch_get_tuning(wcc_batch b, int* ctas, int* tb_depth) {
+    if (!b) return bfail(nullptr, WCC_E_INVAL, "NULL batch");
+    if (ctas) *ctas = (int)b->grid;
+    if (tb_depth) *tb_depth = b->opt.tb_depth;
     return WCC_OK;
 }
 

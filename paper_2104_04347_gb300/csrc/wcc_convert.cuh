@@ -33,14 +33,19 @@ struct ffc {
 };
 __host__ __device__ constexpr ffc ffc_of(double x) { return ffc{(float)x, (float)(x - (double)(float)x)}; }
 
-// 1/k!, k = 0..4
+// 1/k!, k = 0..6
 __host__ __device__ constexpr ffc inv_fact_c(int k) {
-    return k == 2 ? ffc_of(0.5) : k == 3 ? ffc_of(1.0 / 6.0) : k == 4 ? ffc_of(1.0 / 24.0) : ffc_of(1.0);
+    return k == 2 ? ffc_of(0.5) : k == 3 ? ffc_of(1.0 / 6.0) : k == 4 ? ffc_of(1.0 / 24.0)
+         : k == 5 ? ffc_of(1.0 / 120.0) : k == 6 ? ffc_of(1.0 / 720.0) : ffc_of(1.0);
 }
-// weight of u_kx in the cell average, 1/((k+1)! 2^k) (Eq. SubEq:1DCellAVG; even k >= 2)
-__host__ __device__ constexpr ffc avg_from_u_c(int k) { return k == 2 ? ffc_of(1.0 / 24.0) : ffc_of(1.0 / 1920.0); }
-// weight of e_k in the cell average, 1/((k+1) 2^k) (even k >= 2)
-__host__ __device__ constexpr ffc avg_from_e_c(int k) { return k == 2 ? ffc_of(1.0 / 12.0) : ffc_of(1.0 / 80.0); }
+// weight of u_kx in the cell average, 1/((k+1)! 2^k) (Eq. SubEq:1DCellAVG; even k = 2, 4, 6)
+__host__ __device__ constexpr ffc avg_from_u_c(int k) {
+    return k == 2 ? ffc_of(1.0 / 24.0) : k == 4 ? ffc_of(1.0 / 1920.0) : ffc_of(1.0 / 322560.0);
+}
+// weight of e_k in the cell average, 1/((k+1) 2^k) (even k = 2, 4, 6)
+__host__ __device__ constexpr ffc avg_from_e_c(int k) {
+    return k == 2 ? ffc_of(1.0 / 12.0) : k == 4 ? ffc_of(1.0 / 80.0) : ffc_of(1.0 / 448.0);
+}
 
 __device__ __forceinline__ ff ff_mul_c(ff a, ffc c) { return ff_mul(a, ff{c.hi, c.lo}); }
 
@@ -80,12 +85,16 @@ __device__ __forceinline__ ff split_double_bits(unsigned long long b) {
     return ff{hi, uint29_to_float(rest) * scale};
 }
 
-// The bit pattern of f * M exactly as a double, for an integer 1 <= M <= 24:
-// the 24-bit significand times M (< 2^29) renormalised with integer
+// floor(log2 m) for m >= 1
+__host__ __device__ constexpr int ilog2c(unsigned m) { return m <= 1 ? 0 : 1 + ilog2c(m >> 1); }
+
+// The bit pattern of f * M exactly as a double, for an integer 1 <= M <= 720:
+// the 24-bit significand times M (< 2^34) renormalised with integer
 // operations (its leading bit is 23 + floor(log2 M) or one above).
 template <unsigned M>
 __device__ __forceinline__ unsigned long long float_times_exact(float f) {
-    constexpr int L0 = 23 + (M >= 16 ? 4 : M >= 8 ? 3 : M >= 4 ? 2 : M >= 2 ? 1 : 0);
+    static_assert(M >= 1 && M <= 720, "the product must fit the double's significand");
+    constexpr int L0 = 23 + ilog2c(M);
     const unsigned u = __float_as_uint(f);
     if ((u << 1) == 0u) return (unsigned long long)u << 32;  // +-0
     const unsigned ex = (u >> 23) & 0xffu;
@@ -123,7 +132,8 @@ __device__ __forceinline__ void mixed_to_host(ff ubar, const float (&e)[K], unsi
 #pragma unroll
     for (int k = 1; k < K; ++k) {
         q[k] = k == 2 ? float_times_exact<2>(e[k]) : k == 3 ? float_times_exact<6>(e[k])
-               : k == 4 ? float_times_exact<24>(e[k]) : float_times_exact<1>(e[k]);
+               : k == 4 ? float_times_exact<24>(e[k]) : k == 5 ? float_times_exact<120>(e[k])
+               : k == 6 ? float_times_exact<720>(e[k]) : float_times_exact<1>(e[k]);
         if ((k & 1) == 0) u = ff_sub(u, ff_mul_c(ff{e[k], 0.f}, avg_from_e_c(k)));
     }
     q[0] = (unsigned long long)__double_as_longlong(

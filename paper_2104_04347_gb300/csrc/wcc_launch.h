@@ -16,6 +16,11 @@ template <int SYS>
 cudaError_t launch_halfstep_fp64(int P, const StepArgs& args, cudaStream_t stream);
 template <int SYS>
 cudaError_t launch_halfstep_mixed(int P, int precision, const StepArgs& args, cudaStream_t stream);
+// the FP32-variant kernels at P = 5, 6 (one- and two-half-step)
+template <int SYS>
+cudaError_t launch_halfstep_mixed_hi(int P, int precision, const StepArgs& args, cudaStream_t stream);
+template <int SYS>
+cudaError_t launch_halfstep_pair_hi(int P, int precision, const StepArgs& args, cudaStream_t stream);
 
 // Two half-steps in one launch (FP32 variants, P <= 4; halfstep_mixed2_tb2):
 // args.in32 -> args.out32 with args.n_mid cells in between;
@@ -39,14 +44,20 @@ cudaError_t launch_load_stage_mixed(int P, const double* aos, long long n, long 
                                     int keep_lo, const StepArgs& args, int slot, cudaStream_t stream);
 
 struct BatchArgs;
-enum { BATCH_STEP = 0, BATCH_SPEED = 1, BATCH_CONVERT = 2 };
+enum { BATCH_STEP = 0, BATCH_SPEED = 1, BATCH_CONVERT = 2, BATCH_PAIR = 3 };
 
 // Batched launches (wcc_batch.cuh) for groups of degree PA <= PB: one
-// half-step (BATCH_STEP), the stage bound after loading (BATCH_SPEED), or the
-// layout conversion (BATCH_CONVERT, to_planes = 1: host layout -> planes).
+// half-step (BATCH_STEP), two half-steps (BATCH_PAIR), the stage bound after
+// loading (BATCH_SPEED), or the layout conversion (BATCH_CONVERT,
+// to_planes = 1: host layout -> planes).
 template <int SYS>
 cudaError_t launch_batch(int PA, int PB, int kind, const BatchArgs& b, double* aos, int to_planes, unsigned grid,
                          cudaStream_t stream);
+
+// The batched two-half-step kernel (degree mixes (2, 2), (3, 3) and (2, 3);
+// cudaErrorInvalidValue for the others).
+template <int SYS>
+cudaError_t launch_batch_pair(int PA, int PB, const BatchArgs& b, unsigned grid, cudaStream_t stream);
 
 // Resident CTAs per SM of the batched half-step kernel.
 template <int SYS>

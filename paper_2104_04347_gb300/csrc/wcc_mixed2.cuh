@@ -46,7 +46,8 @@ constexpr int kTileMixed = 2 * kThreadsMixed - 1;
 // Resident CTAs per SM the FP32-mixed kernels are compiled for (register
 // budget 65536 / (kThreadsMixed * CTAs) per thread): the most that still
 // compiles without spills (measured on GB300, Euler): 7 for P <= 2, 6 for
-// P = 3, 5 for P = 4.  WCC_MIXED_MIN_CTAS overrides it for every P.
+// P = 3, 5 for P = 4; 4 (128 registers) for P = 5, 6.  WCC_MIXED_MIN_CTAS
+// overrides it for every P.
 // Consecutive tiles per CTA of the single-grid kernel: 2 for P <= 2 (one
 // CTA reduction for two tiles; measured faster), 1 for P >= 3 (measured
 // slower with 2).
@@ -62,7 +63,7 @@ constexpr int mixed_min_ctas() {
 #ifdef WCC_MIXED_MIN_CTAS
     return WCC_MIXED_MIN_CTAS;
 #else
-    return P <= 2 ? 7 : P == 3 ? 6 : 5;
+    return P <= 2 ? 7 : P == 3 ? 6 : P == 4 ? 5 : 4;
 #endif
 }
 
@@ -643,25 +644,47 @@ __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_m
 // 2 kThreadsMixed - 1 intermediate cells and 2 kThreadsMixed - 2 final ones.
 constexpr int kTileTB = 2 * kThreadsMixed - 2;
 
-// Bookkeeping of a two-half-step launch after its last CTA finished (one
-// thread): the pair is taken when the realised CFL number of its second
-// half-step, dt a_mid / dx with a_mid the bound of the intermediate stage,
-// is at most args.tb_nu_max; then dt is recorded twice, t advances by two
-// steps and the next launch's dt comes from the final stage's bound, as in
-// finalize_state.  Otherwise ERR_CFL is set and the state (t, step, the
+// Where one pair's bookkeeping goes: the device state of the problem (a
+// single grid, or one batch instance), its dt history, its mesh width, the
+// CFL numbers, and -- batches only -- the copy of the state taken before the
+// pair and the batch's refusal flag.
+struct PairBook {
+    DevState* st;
+    double* hist;
+    long long hist_cap;
+    long long ctas;     // CTAs (tiles) that count towards this state
+    double dx;
+    double cfl;
+    double nu_max;      // the second half-step's largest CFL number
+    int cfl_mode;
+    int parity;
+    DevState* backup;   // batches: the state before the pair, or nullptr
+    unsigned* refused;  // batches: set to 1 when this state refuses the pair, or nullptr
+};
+
+// Bookkeeping of a two-half-step launch after the last CTA of a problem
+// finished (one thread): the pair is taken when the realised CFL number of
+// its second half-step, dt a_mid / dx with a_mid the bound of the
+// intermediate stage, is at most nu_max; then dt is recorded twice, t
+// advances by two steps and the next launch's dt comes from the final
+// stage's bound, as in finalize_state.  Otherwise the refusal is flagged
+// (ERR_CFL in the state, and the batch's flag) and the state (t, step, the
 // bounds of the input stage and the prepared dt) is left as it was before
 // the launch, so that the caller can take the two half-steps one by one
 // from the input stage, which the launch did not overwrite.
-__device__ __forceinline__ void finalize_pair(DevState* st, double dt, const StepArgs& args) {
-    const int parity = args.parity;
+__device__ __forceinline__ void finalize_pair(const PairBook& bk, double dt) {
+    DevState* st = bk.st;
+    const int parity = bk.parity;
     const float fmid = __uint_as_float(st->amax_f32[parity ^ 1]);
     const float ffin = __uint_as_float(st->amax_f32_tb);
     st->amax_f32[parity ^ 1] = 0u;
     st->amax_f32_tb = 0u;
     st->blocks_done = 0u;
-    const double nu2 = dt * (double)fmid / args.dx;
-    if (!(nu2 <= args.tb_nu_max)) {
+    if (bk.backup) *bk.backup = *st;
+    const double nu2 = dt * (double)fmid / bk.dx;
+    if (!(nu2 <= bk.nu_max)) {
         st->err |= ERR_CFL;
+        if (bk.refused) atomicExch(bk.refused, 1u);
         __threadfence();
         return;
     }
@@ -669,17 +692,17 @@ __device__ __forceinline__ void finalize_pair(DevState* st, double dt, const Ste
     st->amax_bits[parity ^ 1] = (unsigned long long)__double_as_longlong((double)fmid);
     st->amax_bits[parity] = (unsigned long long)__double_as_longlong((double)ffin);
     const long long k = st->step;
-    if (k < args.hist_cap) args.hist[k] = dt;
-    if (k + 1 < args.hist_cap) args.hist[k + 1] = dt;
+    if (k < bk.hist_cap) bk.hist[k] = dt;
+    if (k + 1 < bk.hist_cap) bk.hist[k + 1] = dt;
     st->step = k + 2;
     st->t = (st->t + dt) + dt;
     if (not_finite(dt)) st->err |= ERR_NONFINITE;
-    if (args.cfl_mode) {
-        const double ndt = args.cfl * args.dx / (double)ffin;
+    if (bk.cfl_mode) {
+        const double ndt = bk.cfl * bk.dx / (double)ffin;
         st->next_dt = ndt;
-        st->next_lam = ndt / args.dx;
+        st->next_lam = ndt / bk.dx;
         split_to_floats(st->next_lam, st->next_lam_hi, st->next_lam_lo);
-        st->next_cfl = args.cfl;
+        st->next_cfl = bk.cfl;
     } else {
         st->next_cfl = 0.0;
     }
@@ -687,9 +710,9 @@ __device__ __forceinline__ void finalize_pair(DevState* st, double dt, const Ste
 }
 
 // Block maxima of the intermediate and final speeds, one atomic each per
-// CTA, then the CTA count; the last CTA runs finalize_pair.  Synchronises
-// the block.
-__device__ __forceinline__ void finish_pair(float mid, float fin, unsigned err, double dt, const StepArgs& args) {
+// CTA into the problem's state, then the CTA count; the CTA that completes
+// bk.ctas runs finalize_pair.  Synchronises the block.
+__device__ __forceinline__ void finish_pair(float mid, float fin, unsigned err, double dt, const PairBook& bk) {
     __shared__ float s_mid[kThreadsMixed / 32], s_fin[kThreadsMixed / 32];
     __shared__ unsigned s_err[kThreadsMixed / 32];
     if (mid != mid) {
@@ -718,54 +741,63 @@ __device__ __forceinline__ void finish_pair(float mid, float fin, unsigned err, 
             f = fmaxf(f, s_fin[w]);
             e |= s_err[w];
         }
-        DevState* st = args.st;
-        if (m > 0.f) atomicMax(&st->amax_f32[args.parity ^ 1], __float_as_uint(m));
+        DevState* st = bk.st;
+        if (m > 0.f) atomicMax(&st->amax_f32[bk.parity ^ 1], __float_as_uint(m));
         if (f > 0.f) atomicMax(&st->amax_f32_tb, __float_as_uint(f));
         if (e) atomicOr(&st->err, e);
         __threadfence();
         const unsigned done = atomicAdd(&st->blocks_done, 1u);
-        if (done == gridDim.x - 1) {
+        if (done == (unsigned)(bk.ctas - 1)) {
             __threadfence();
-            finalize_pair(st, dt, args);
+            finalize_pair(bk, dt);
         }
     }
 }
 
-// Two staggered half-steps in one pass over HBM (temporal blocking, FP32
-// variants): stage n (parity p, args.in32) -> n + 1/2 -> n + 1 (parity p,
-// args.out32), both with the dt of stage n's bound.  CTA b owns final cells
-// f0 = b kTileTB .. f0 + kTileTB - 1; it loads the parents o0 = f0 - 1 ..
-// o0 + 2 kThreadsMixed - 1, builds the intermediate cells m0 = o0 + p ..
-// m0 + 2 kThreadsMixed - 2 in registers (each thread's two intermediate
-// cells are the parents it needs next, slot for slot), and from them the
-// final cells.  Neighbouring CTAs build one intermediate cell twice.  At a
-// transmissive boundary the intermediate cells outside the stage take the
-// adjacent cell's values (the ghost rule of Sec. 2.1's staggered mesh), at a
-// periodic one they are the wrapped cells, built from wrapped parents.  The
-// intermediate stage's bound decides whether the pair is taken
-// (finalize_pair); a launch that finds ERR_CFL set does nothing.
-template <int SYS, int P, bool COMP = true>
-__global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_mixed2_tb2(const StepArgs args) {
+// Where one two-half-step tile reads and writes: the stage of parity
+// `parity` in in32 (n_old cells), the intermediate stage (n_mid cells, never
+// stored), the final stage in out32 (n_new = n_old cells); the tile's final
+// cells start at f0.
+struct PairIO {
+    const float* in32;
+    float* out32;
+    long long pitch;
+    long long n_old, n_mid, n_new;
+    long long f0;
+    int parity;
+    int bc;
+};
+
+// One tile of two staggered half-steps (temporal blocking, FP32 variants):
+// stage n (parity p) -> n + 1/2 -> n + 1 (parity p), both with the step lam2.
+// The tile owns final cells f0 .. f0 + kTileTB - 1; it loads the parents
+// o0 = f0 - 1 .. o0 + 2 kThreadsMixed - 1, builds the intermediate cells
+// m0 = o0 + p .. m0 + 2 kThreadsMixed - 2 in registers (each thread's two
+// intermediate cells are the parents it needs next, slot for slot), and from
+// them the final cells.  Neighbouring tiles build one intermediate cell
+// twice.  At a transmissive boundary the intermediate cells outside the stage
+// take the adjacent cell's values (the ghost rule of Sec. 2.1's staggered
+// mesh), at a periodic one they are the wrapped cells, built from wrapped
+// parents.  Returns the largest speeds of the thread's intermediate and final
+// cells (cells outside the stages count as 0) and error bits; synchronises
+// the block, and the caller synchronises it again before rec is written.
+template <int SYS, int P, bool COMP, bool PARK = (P >= 3)>
+__device__ __forceinline__ void mixed_pair_tile(const PairIO& io, const ff2 lam2, const StepArgs& args, float2* rec,
+                                                float& mid_speed, float& fin_speed, unsigned& err) {
     constexpr int NV = nvars(SYS);
     constexpr int K = P + 1;
-    __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
-    if (args.st->err & ERR_CFL) return;  // an earlier pair was refused: the caller steps singly from there
     const int t = threadIdx.x;
-    const StepSize z = step_size(args);
-    const ff2 lam2{f2(z.lam_hi), f2(COMP ? z.lam_lo : 0.f)};
-    const int p = args.parity;
-    const long long f0 = (long long)blockIdx.x * kTileTB;
+    const int p = io.parity;
+    const long long f0 = io.f0;
     const long long o0 = f0 - 1;
     const long long m0 = o0 + p;
-    unsigned err = 0u;
-    float mid_speed = 0.f;
 
     ff2 ub[NV];
     f2 c[NV][K];
     {
-        const TileIO io1{args.in32, nullptr, args.pitch, args.n_old, args.n_mid, m0, p, args.bc};
+        const TileIO io1{io.in32, nullptr, io.pitch, io.n_old, io.n_mid, m0, p, io.bc};
         mixed_load_parents<SYS, P, COMP>(io1, ub, c);
-        mixed_parent_records<SYS, P, COMP>(ub, c, lam2, args, rec);
+        mixed_parent_records<SYS, P, COMP, PARK>(ub, c, lam2, args, rec);
     }
     __syncthreads();
     {
@@ -774,8 +806,8 @@ __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_m
         // intermediate cells m0 + t (lane x) and m0 + t + kThreadsMixed (lane
         // y; slot 2 kThreadsMixed - 1 is not a cell of the tile)
         const long long ia = m0 + t, ib = ia + kThreadsMixed;
-        const bool va = ia >= 0 && ia < args.n_mid;
-        const bool vb = t < kThreadsMixed - 1 && ib >= 0 && ib < args.n_mid;
+        const bool va = ia >= 0 && ia < io.n_mid;
+        const bool vb = t < kThreadsMixed - 1 && ib >= 0 && ib < io.n_mid;
         f2 d0[NV];
         sfor<0, NV>([&](auto V) { d0[decltype(V)::value] = d[decltype(V)::value][0]; });
         mid_speed = mixed_cell_speed<SYS>(ub, d0, va, vb, args, err);
@@ -784,7 +816,7 @@ __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_m
             sfor<1, K>([&](auto Ki) { c[v][decltype(Ki)::value] = d[v][decltype(Ki)::value]; });
         });
         __syncthreads();  // every record of the first half-step has been read
-        if (args.bc == BC_TRANSMISSIVE && (m0 < 0 || m0 + 2 * kThreadsMixed - 1 > args.n_mid)) {
+        if (io.bc == BC_TRANSMISSIVE && (m0 < 0 || m0 + 2 * kThreadsMixed - 1 > io.n_mid)) {
             // edge tiles: slots outside [0, n_mid) copy the edge cell
             constexpr int Q = K + 1;  // hi, lo, c_1..c_P per variable
             float* sc = reinterpret_cast<float*>(rec);
@@ -803,7 +835,7 @@ __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_m
             save(t + kThreadsMixed, 1);
             __syncthreads();
             auto fetch = [&](long long idx, int lane) {
-                const long long cl = idx < 0 ? 0 : (idx >= args.n_mid ? args.n_mid - 1 : idx);
+                const long long cl = idx < 0 ? 0 : (idx >= io.n_mid ? io.n_mid - 1 : idx);
                 if (cl == idx) return;
                 const int slot = (int)(cl - m0);
                 sfor<0, NV>([&](auto V) {
@@ -829,16 +861,37 @@ __global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_m
             __syncthreads();
         }
     }
-    mixed_parent_records<SYS, P, COMP>(ub, c, lam2, args, rec);
+    mixed_parent_records<SYS, P, COMP, PARK>(ub, c, lam2, args, rec);
     __syncthreads();
     ff2 ubn[NV];
     f2 d[NV][K];
     mixed_new_cells<SYS, P, COMP>(rec, args, ubn, d, err);
-    const TileIO io2{nullptr, args.out32, args.pitch, args.n_mid, args.n_new, f0, p ^ 1, args.bc};
-    const bool va = f0 + t < args.n_new;
-    const bool vb = t < kThreadsMixed - 2 && f0 + t + kThreadsMixed < args.n_new;
-    const float fin_speed = mixed_store<SYS, P>(io2, ubn, d, va, vb, args, err);
-    finish_pair(mid_speed, fin_speed, err, z.dt, args);
+    const TileIO io2{nullptr, io.out32, io.pitch, io.n_mid, io.n_new, f0, p ^ 1, io.bc};
+    const bool va = f0 + t < io.n_new;
+    const bool vb = t < kThreadsMixed - 2 && f0 + t + kThreadsMixed < io.n_new;
+    fin_speed = mixed_store<SYS, P>(io2, ubn, d, va, vb, args, err);
+}
+
+// Two staggered half-steps in one pass over HBM (temporal blocking, FP32
+// variants) over a whole stage: args.in32 (parity args.parity) ->
+// args.out32, one tile (kTileTB final cells) per CTA, both half-steps with
+// the dt of the input stage's bound.  The intermediate stage's bound decides
+// whether the pair is taken (finalize_pair); a launch that finds ERR_CFL set
+// does nothing.
+template <int SYS, int P, bool COMP = true>
+__global__ void __launch_bounds__(kThreadsMixed, mixed_min_ctas<P>()) halfstep_mixed2_tb2(const StepArgs args) {
+    __shared__ float2 rec[mixed2_smem_float2<SYS, P>()];
+    if (args.st->err & ERR_CFL) return;  // an earlier pair was refused: the caller steps singly from there
+    const StepSize z = step_size(args);
+    const ff2 lam2{f2(z.lam_hi), f2(COMP ? z.lam_lo : 0.f)};
+    const PairIO io{args.in32, args.out32, args.pitch, args.n_old, args.n_mid, args.n_new,
+                    (long long)blockIdx.x * kTileTB, args.parity, args.bc};
+    float mid = 0.f, fin = 0.f;
+    unsigned err = 0u;
+    mixed_pair_tile<SYS, P, COMP>(io, lam2, args, rec, mid, fin, err);
+    const PairBook bk{args.st, args.hist, args.hist_cap, (long long)gridDim.x, args.dx, args.cfl, args.tb_nu_max,
+                      args.cfl_mode, args.parity, nullptr, nullptr};
+    finish_pair(mid, fin, err, z.dt, bk);
 }
 
 // Set-up of an FP32-mixed stage in one pass: the host-layout DOFs (already in

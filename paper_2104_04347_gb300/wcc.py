@@ -109,6 +109,9 @@ _SIGS = {
     "wcc_batch_get_dt_history": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int64, _dp, ctypes.c_int64, _i64p]),
     "wcc_batch_set_grid": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int]),
     "wcc_batch_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
+    "wcc_batch_get_tuning": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int),
+                                            ctypes.POINTER(ctypes.c_int)]),
+    "wcc_batch_tb_stats": (ctypes.c_int, [ctypes.c_void_p, _i64p, _i64p]),
     "wcc_batch_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
     "wcc_batch_launch_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "wcc_batch_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
@@ -338,7 +341,8 @@ class Batch:
     Host arrays are the concatenation of the instances' [cells, nv, P+1]."""
 
     def __init__(self, problems, *, limiter: bool = True, alpha: float = 2.0, eps: float = 1e-40,
-                 gamma: float = 1.4, adv_speed: float = 1.0, graph_chunk: int = 32, stream: int | None = None):
+                 gamma: float = 1.4, adv_speed: float = 1.0, graph_chunk: int = 32, stream: int | None = None,
+                 tb_depth: int = 1, tb_cfl_growth: float = 0.1):
         self.lib = load()
         self.problems = list(problems)
         n = len(self.problems)
@@ -349,6 +353,8 @@ class Batch:
         o.alpha, o.eps, o.gamma, o.adv_speed = alpha, eps, gamma, adv_speed
         o.graph_chunk = graph_chunk
         o.cuda_stream = stream
+        o.tb_depth = tb_depth
+        o.tb_cfl_growth = tb_cfl_growth
         Ns = (ctypes.c_int64 * n)(*[p.N for p in self.problems])
         Ps = (ctypes.c_int * n)(*[p.P for p in self.problems])
         doms = (ctypes.c_double * (2 * n))(*[v for p in self.problems for v in (p.x_l, p.x_r)])
@@ -441,6 +447,18 @@ class Batch:
         c = ctypes.c_int()
         self._check(self.lib.wcc_batch_autotune(self.h, float(cfl), ctypes.byref(c)))
         return c.value
+
+    def tuning(self):
+        """(persistent grid in CTAs, half-steps per launch)."""
+        c, d = ctypes.c_int(), ctypes.c_int()
+        self._check(self.lib.wcc_batch_get_tuning(self.h, ctypes.byref(c), ctypes.byref(d)))
+        return c.value, d.value
+
+    def tb_stats(self):
+        """(pairs taken, pairs refused and re-done as single half-steps)."""
+        p, f = ctypes.c_int64(), ctypes.c_int64()
+        self._check(self.lib.wcc_batch_tb_stats(self.h, ctypes.byref(p), ctypes.byref(f)))
+        return p.value, f.value
 
     def synchronize(self) -> None:
         self._check(self.lib.wcc_batch_synchronize(self.h))

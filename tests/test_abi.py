@@ -52,10 +52,18 @@ def test_create_rejects_bad_arguments(args, needle):
 
 
 @pytest.mark.parametrize("precision", [wcc.FP32_MIXED, wcc.FP32])
-def test_p_above_4_needs_fp64(precision):
+def test_every_precision_takes_p_up_to_6(precision):
+    # P = 7 is refused by every precision; P = 5, 6 pass the argument checks of
+    # the FP32 variants too (here, without a GPU, create then fails on the
+    # missing device, not on P)
     with pytest.raises(wcc.WCCError) as ei:
-        wcc.Solver(2, 64, 5, (0.0, 1.0), 1, precision=precision)
-    assert ei.value.code == -1 and "needs WCC_FP64" in str(ei.value)
+        wcc.Solver(2, 64, 7, (0.0, 1.0), 1, precision=precision)
+    assert ei.value.code == -1 and "P must" in str(ei.value)
+    for P in (5, 6):
+        try:
+            wcc.Solver(2, 64, P, (0.0, 1.0), 1, precision=precision).close()
+        except wcc.WCCError as e:
+            assert e.code != -1, str(e)
 
 
 @pytest.mark.parametrize("args,kw,code,needle", [
