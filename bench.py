@@ -388,9 +388,11 @@ def time_solver(solver, stream, steps, warmup, barrier):
 
 def batch_bench(stream, steps, warmup, p3_rate, barrier):
     """The batched workload: 4096 independent Euler problems (N log-uniform in
-    [256, 65536], P in {2, 3}, Riemann or density-wave data), FP32-mixed, one
-    persistent launch per half-step in graphs of 32, grid picked by the
-    autotuner.  Returns the batch line and the single-grid comparison."""
+    [256, 65536], P in {2, 3}, Riemann or density-wave data), FP32-mixed,
+    persistent launches in graphs of 32 half-steps, grid and pass depth (one
+    or two half-steps per launch) picked by the autotuner; the batch with
+    one half-step per launch is timed beside it.  Returns the batch line and
+    the single-grid comparison."""
     import torch
 
     from paper_2104_04347_gb300 import inputs, wcc
@@ -406,9 +408,14 @@ def batch_bench(stream, steps, warmup, p3_rate, barrier):
     with wcc.Batch(probs, graph_chunk=HALFSTEPS_PER_STEP, stream=stream.cuda_stream) as b:
         b.set_initial()
         ctas = b.autotune(CFL)
+        _, depth = b.tuning()
         total_ms, step_ms, launches = time_solver(b, stream, steps, warmup, barrier)
-        b.synchronize()
+        pairs, fallbacks = b.tb_stats()
     value = per_step * steps / (total_ms * 1e-3)
+    with wcc.Batch(probs, graph_chunk=HALFSTEPS_PER_STEP, stream=stream.cuda_stream) as b1:
+        b1.set_initial()
+        t1, _, _ = time_solver(b1, stream, steps, warmup, barrier)
+    value_one = per_step * steps / (t1 * 1e-3)
     # single-grid FP32-mixed rate at P = 2 on the same grid shape as the headline
     pr = inputs.euler_riemann_seeded(1 << 22, 2)
     with wcc.Solver(pr.system, pr.N, 2, (pr.x_l, pr.x_r), pr.bc, precision=wcc.FP32_MIXED,
@@ -421,6 +428,8 @@ def batch_bench(stream, steps, warmup, p3_rate, barrier):
     return {"workload": "euler1d-batch-4096-N256..65536-P2/3-riemann/density-wave", "value": value,
             "unit": "cell-updates/s", "ms_per_step": total_ms / steps, "steps": steps,
             "cells_per_halfstep": per_step / HALFSTEPS_PER_STEP, "persistent_ctas": ctas,
+            "halfsteps_per_launch": depth, "pairs": pairs, "pair_fallbacks": fallbacks,
+            "one_halfstep_per_launch": value_one,
             "gpu_launches": launches, "single_grid_same_mix": single, "single_grid_p2": p2_rate,
             "single_grid_p3": p3_rate, "single_over_batch": single / value}
 

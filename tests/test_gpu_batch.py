@@ -83,6 +83,8 @@ def test_batch_against_oracle_sampled():
 
 
 def test_autotune_keeps_the_state():
+    # the autotuner times candidate launches on the batch itself and puts
+    # the stages, times, step counts and dt histories back
     probs = _small_batch(30, seed=5)
     with wcc.Batch(probs) as a, wcc.Batch(probs) as b:
         a.set_initial()
@@ -90,12 +92,15 @@ def test_autotune_keeps_the_state():
         a.step(5, CFL)
         b.step(5, CFL)
         ctas = a.autotune(CFL)
-        assert ctas > 0
-        a.step(40, CFL)
-        b.step(40, CFL)
+        assert ctas > 0 and a.tuning()[0] == ctas
         for qa, qb in zip(a.get_dofs(), b.get_dofs()):
             assert np.array_equal(qa, qb)
-        assert a.state() == b.state() == (45, 1)
+        assert a.state() == b.state() == (5, 1)
+        assert np.array_equal(a.times(), b.times())
+        for i in range(len(probs)):
+            assert np.array_equal(a.dt_history(i), b.dt_history(i))
+        a.step(40, CFL)
+        assert a.state() == (45, 1)
 
 
 def _run_batch(probs, nsteps, grid=None):

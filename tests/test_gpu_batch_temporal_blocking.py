@@ -120,21 +120,25 @@ def test_any_persistent_grid_gives_the_same_result(grid):
 
 
 def test_autotune_chooses_depth_and_keeps_the_state():
+    # tuned right after loading, then stepped: as a fresh batch created with
+    # the chosen pass depth (the grid does not change results)
     probs = _batch(30, 13)
-    with wcc.Batch(probs) as a:
+    with wcc.Batch(probs) as a, wcc.Batch(probs) as fresh:
         a.set_initial()
-        a.step(6, CFL)
+        fresh.set_initial()
         ctas = a.autotune(CFL)
         grid, depth = a.tuning()
         assert ctas == grid > 0 and depth in (1, 2)
-        a.step(40, CFL)
+        assert a.state() == (0, 0) and not np.any(a.times())
+        for x, y in zip(a.get_dofs(), fresh.get_dofs()):
+            assert np.array_equal(x, y)
+        a.step(46, CFL)
         qa = a.get_dofs()
         ha = [a.dt_history(i) for i in range(len(probs))]
         assert a.state() == (46, 0)
     with wcc.Batch(probs, tb_depth=depth) as b:
         b.set_initial()
-        b.step(6, CFL)
-        b.step(40, CFL)
+        b.step(46, CFL)
         qb = b.get_dofs()
         hb = [b.dt_history(i) for i in range(len(probs))]
     for x, y in zip(ha, hb):
