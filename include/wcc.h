@@ -250,7 +250,8 @@ int wcc_batch_set_grid(wcc_batch b, int ctas);
  * tile), each with one half-step per launch and, where the degree mix has
  * the kernel (degrees {2}, {3}, {2, 3}), two; keep the fastest pair of grid
  * and pass depth, and restore the batch state.  Timed over eight half-steps
- * of this batch with this CFL number.  *ctas (may be NULL) receives the grid;
+ * of this batch with this CFL number; a two-half-step candidate that had a
+ * pair refused while it was timed is not taken.  *ctas (may be NULL) receives the grid;
  * wcc_batch_get_tuning reports both.  Allocates a temporary copy of the
  * current stage.  Synchronous. */
 int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas);

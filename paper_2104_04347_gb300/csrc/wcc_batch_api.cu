@@ -795,6 +795,7 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
                 par ^= 1;
             }
         } else {
+            cudaMemsetAsync(b->d_refused, 0, sizeof(unsigned), b->stream);
             for (int s = 0; s < 5 && rc == WCC_OK; ++s) {
                 if (s == 1) cudaEventRecord(e0, b->stream);
                 rc = enqueue_pair(b, cur, par, cfl, grid);
@@ -808,7 +809,17 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
         }
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        if (ms < best) {
+        // A refused pair leaves the launches after it with nothing to do, so
+        // the time says nothing; the state also made this batch refuse a
+        // pair, and the depth that needs no redoing is kept.
+        unsigned refused = 0;
+        if (c.tb == 2 && (cudaMemcpyAsync(&refused, b->d_refused, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream) !=
+                              cudaSuccess ||
+                          cudaStreamSynchronize(b->stream) != cudaSuccess)) {
+            rc = WCC_E_CUDA;
+            break;
+        }
+        if (!refused && ms < best) {
             best = ms;
             best_grid = grid;
             best_tb = c.tb;
