@@ -422,20 +422,27 @@ __global__ void __launch_bounds__(TW, 4) halfstep2d_mx(const Step2D a) {
             float* r = ring + (s & 1) * NF * TW;
 #pragma unroll
             for (int v = 0; v < NV; ++v) {
-                const ff fU = wcc::ff_add(F[v], par.fl[v][0]), fD = wcc::ff_add(F[v], par.fl[v][1]);
-                const ff gR = wcc::ff_add(G[v], par.fl[v][2]), gL = wcc::ff_add(G[v], par.fl[v][3]);
-                // quarter averages: ubar +- ox +- oy +- oxy with the signs of
-                // RU, LU, LD, RD (vertex roles 1..4); every term enters the
-                // four shares with opposite signs, so the parent's shares add
-                // up to its ubar to float-float rounding
+                // quarter averages: ubar/4 +- ox +- oy +- oxy with the signs of
+                // RU, LU, LD, RD (vertex roles 1..4), plus the edge fluxes
+                // hx f_U = tx, hx f_D = bx, hy g_R = ry, hy g_L = ly:
+                //   c0 = q4 + ox + oy + oxy + tx + ry,  c1 = q4 - ox + oy - oxy - tx + ly,
+                //   c2 = q4 - ox - oy + oxy - bx - ly,  c3 = q4 + ox - oy - oxy + bx - ry.
+                // The O(1) parts (q4 and the leading flux terms hx f(u_00),
+                // hy g(u_00)) are added exactly, the float parts (the odd
+                // terms and the flux corrections) join the low parts.  c3 is
+                // taken as ubar - c0 - c1 - c2, so the parent's shares add up
+                // to its ubar to float-float rounding.
                 const float ox = 0.25f * par.odd[v][0], oy = 0.25f * par.odd[v][1], oxy = 0.25f * par.odd[v][2];
-                const ff q4 = ffm(ub[v], 0.25f);
-                const ff tx = ffm(fU, hx), bx = ffm(fD, hx), ry = ffm(gR, hy), ly = ffm(gL, hy);
+                const float sxy = ox + oy, dxy = ox - oy;
+                const float q4h = 0.25f * ub[v].hi, q4l = 0.25f * ub[v].lo;
+                const ff hF = ffm_lazy(F[v], hx), hG = ffm_lazy(G[v], hy);
+                const float tl = fmaf(hx, par.fl[v][0], hF.lo), bl = fmaf(hx, par.fl[v][1], hF.lo);
+                const float rl = fmaf(hy, par.fl[v][2], hG.lo), ll = fmaf(hy, par.fl[v][3], hG.lo);
                 ff c[4];
-                c[0] = wcc::ff_add(wcc::ff_add(wcc::ff_add(wcc::ff_add(q4, ox), oy), oxy), wcc::ff_add(tx, ry));
-                c[1] = wcc::ff_add(wcc::ff_add(wcc::ff_add(wcc::ff_add(q4, -ox), oy), -oxy), wcc::ff_sub(ly, tx));
-                c[2] = wcc::ff_sub(wcc::ff_add(wcc::ff_add(wcc::ff_add(q4, -ox), -oy), oxy), wcc::ff_add(bx, ly));
-                c[3] = wcc::ff_add(wcc::ff_add(wcc::ff_add(wcc::ff_add(q4, ox), -oy), -oxy), wcc::ff_sub(bx, ry));
+                c[0] = ff_sum4(q4h, hF.hi, hG.hi, sxy + oxy, q4l + (tl + rl));
+                c[1] = ff_sum4(q4h, -hF.hi, hG.hi, -(dxy + oxy), q4l + (ll - tl));
+                c[2] = ff_sum4(q4h, -hF.hi, -hG.hi, oxy - sxy, q4l - (bl + ll));
+                c[3] = ff_rest3(ub[v], c[0], c[1], c[2]);
 #pragma unroll
                 for (int k = 0; k < 4; ++k) {
                     r[(v * 8 + k) * TW + t] = c[k].hi;

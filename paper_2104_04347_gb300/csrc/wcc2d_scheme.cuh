@@ -639,6 +639,41 @@ __device__ __forceinline__ ff ffm(ff a, float b) {  // a * b
     ff p = wcc::two_prod(a.hi, b);
     return wcc::fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
 }
+// a * b as an unnormalised pair (hi, lo): exact product of a.hi, plus a.lo * b
+__device__ __forceinline__ ff ffm_lazy(ff a, float b) {
+    const ff p = wcc::two_prod(a.hi, b);
+    return ff{p.hi, fmaf(a.lo, b, p.lo)};
+}
+// a + b + c + s + lo for O(1) floats a, b, c, a small float s and a low part
+// lo: every addition of a high part is exact (two_sum), its error joins the
+// low part, which is renormalised once at the end.
+__device__ __forceinline__ ff ff_sum4(float a, float b, float c, float s, float lo) {
+    const ff x = wcc::two_sum(a, b);
+    const ff y = wcc::two_sum(x.hi, c);
+    const ff z = wcc::two_sum(y.hi, s);
+    return wcc::fast_two_sum(z.hi, ((lo + x.lo) + y.lo) + z.lo);
+}
+// a - b - c - d in float-float, in the same way
+__device__ __forceinline__ ff ff_rest3(ff a, ff b, ff c, ff d) {
+    const ff x = wcc::two_sum(a.hi, -b.hi);
+    const ff y = wcc::two_sum(x.hi, -c.hi);
+    const ff z = wcc::two_sum(y.hi, -d.hi);
+    return wcc::fast_two_sum(z.hi, ((a.lo - b.lo) - (c.lo + d.lo)) + ((x.lo + y.lo) + z.lo));
+}
+// a + b + c + d in float-float, in the same way
+__device__ __forceinline__ ff ff_sum4(ff a, ff b, ff c, ff d) {
+    const ff x = wcc::two_sum(a.hi, b.hi);
+    const ff y = wcc::two_sum(x.hi, c.hi);
+    const ff z = wcc::two_sum(y.hi, d.hi);
+    return wcc::fast_two_sum(z.hi, ((a.lo + b.lo) + (c.lo + d.lo)) + ((x.lo + y.lo) + z.lo));
+}
+// (a + b) - (c + d) rounded to float
+__device__ __forceinline__ float ff_diff2(ff a, ff b, ff c, ff d) {
+    const ff x = wcc::two_sum(a.hi, b.hi);
+    const ff y = wcc::two_sum(x.hi, -c.hi);
+    const ff z = wcc::two_sum(y.hi, -d.hi);
+    return z.hi + (((a.lo + b.lo) - (c.lo + d.lo)) + ((x.lo + y.lo) + z.lo));
+}
 __device__ __forceinline__ ff ffdiv(ff a, ff b) {  // a / b for a normal b
     const float q1 = __fdividef(a.hi, b.hi);
     const ff r = wcc::ff_sub(a, wcc::ff_mul(b, ff{q1, 0.f}));
@@ -698,7 +733,7 @@ __device__ __forceinline__ void linear_cell_mx(const Rd& rd, float (&D)[nvars(SY
     constexpr int NV = nvars(SYS);
     unroll<NV>([&](auto vc) {
         constexpr int v = vc;
-        ubar[v] = wcc::ff_add(wcc::ff_add(rd.cf(0, v), rd.cf(1, v)), wcc::ff_add(rd.cf(2, v), rd.cf(3, v)));
+        ubar[v] = ff_sum4(rd.cf(0, v), rd.cf(1, v), rd.cf(2, v), rd.cf(3, v));
         unroll<P>([&](auto dd) {
             constexpr int d = P - dd;
             unroll<d + 1>([&](auto bc) {
@@ -709,8 +744,7 @@ __device__ __forceinline__ void linear_cell_mx(const Rd& rd, float (&D)[nvars(SY
                     constexpr int q0 = qidx(k, l);
                     float s;
                     if constexpr (q0 == 0)
-                        s = ffm(wcc::ff_sub(wcc::ff_add(rd.v00(1, v), rd.v00(2, v)), wcc::ff_add(rd.v00(0, v), rd.v00(3, v))),
-                                0.5f).hi;
+                        s = 0.5f * ff_diff2(rd.v00(1, v), rd.v00(2, v), rd.v00(0, v), rd.v00(3, v));
                     else
                         s = 0.5f * ((rd.V(1, v, q0) + rd.V(2, v, q0)) - (rd.V(0, v, q0) + rd.V(3, v, q0)));
                     unroll<r - 2>([&](auto s3c) {
@@ -732,8 +766,7 @@ __device__ __forceinline__ void linear_cell_mx(const Rd& rd, float (&D)[nvars(SY
                     constexpr int q0 = qidx(k, l);
                     float s;
                     if constexpr (q0 == 0)
-                        s = ffm(wcc::ff_sub(wcc::ff_add(rd.v00(3, v), rd.v00(2, v)), wcc::ff_add(rd.v00(0, v), rd.v00(1, v))),
-                                0.5f).hi;
+                        s = 0.5f * ff_diff2(rd.v00(3, v), rd.v00(2, v), rd.v00(0, v), rd.v00(1, v));
                     else
                         s = 0.5f * ((rd.V(3, v, q0) + rd.V(2, v, q0)) - (rd.V(0, v, q0) + rd.V(1, v, q0)));
                     unroll<r - 2>([&](auto t3c) {
