@@ -81,6 +81,7 @@ def parse():
 # solver handle, CUDA stream, pinned host buffers and host thread, so the
 # copies of one overlap the half-steps of the others.
 E2E_IN_FLIGHT = 3
+E2E_STEPS = 10  # timed steps per in-flight problem of the end-to-end leg
 
 
 def e2e_bench(wcc, pr, prec, cells_per_step, steps, dev, barrier):
@@ -111,7 +112,7 @@ def e2e_bench(wcc, pr, prec, cells_per_step, steps, dev, barrier):
             s.get_dofs_ptr(h_out.data_ptr(), count)
 
     for job in jobs:  # warm-up: graphs captured, pages touched
-        run(job, 1)
+        run(job, 2)
     barrier()
     t0 = time.perf_counter()
     run(jobs[0], steps)
@@ -390,9 +391,9 @@ def batch_bench(stream, steps, warmup, p3_rate, barrier):
     """The batched workload: 4096 independent Euler problems (N log-uniform in
     [256, 65536], P in {2, 3}, Riemann or density-wave data), FP32-mixed,
     persistent launches in graphs of 32 half-steps, grid and pass depth (one
-    or two half-steps per launch) picked by the autotuner; the batch with
-    one half-step per launch is timed beside it.  Returns the batch line and
-    the single-grid comparison."""
+    or two half-steps per launch) picked by the autotuner; the untuned batch
+    (one half-step per launch, all resident CTAs) is timed beside it.
+    Returns the batch line and the single-grid comparison."""
     import torch
 
     from paper_2104_04347_gb300 import inputs, wcc
@@ -429,7 +430,7 @@ def batch_bench(stream, steps, warmup, p3_rate, barrier):
             "unit": "cell-updates/s", "ms_per_step": total_ms / steps, "steps": steps,
             "cells_per_halfstep": per_step / HALFSTEPS_PER_STEP, "persistent_ctas": ctas,
             "halfsteps_per_launch": depth, "pairs": pairs, "pair_fallbacks": fallbacks,
-            "one_halfstep_per_launch": value_one,
+            "untuned_default_grid": value_one,
             "gpu_launches": launches, "single_grid_same_mix": single, "single_grid_p2": p2_rate,
             "single_grid_p3": p3_rate, "single_over_batch": single / value}
 
@@ -551,10 +552,10 @@ def run_wcc(args, rank, world):
     clk = clocks.stop()
 
     # ---- end to end through the public API with host buffers (headline precision)
-    # up to 10 steps per in-flight problem, so that filling and draining the
-    # pipeline of problems is a small part of the timed region
+    # 10 steps per in-flight problem whatever --steps is, so that filling and
+    # draining the pipeline of problems is a small part of the timed region
     e2e = e2e_bench(wcc, pr, wcc.FP64 if args.precision == "fp64" else wcc.FP32_MIXED, cells_per_step,
-                    max(4, min(args.steps, 10)), dev, barrier)
+                    E2E_STEPS, dev, barrier)
 
     fp64_peak_meas = wcc.measure_fp_peak(wcc.FP64)
     fp32_peak_meas = wcc.measure_fp_peak(wcc.FP32_MIXED)
@@ -753,19 +754,15 @@ BYTES_2D_PER_CELL = {"fp32_mixed": 2 * 44 * 4, "fp32": 2 * 40 * 4, "fp64": 2 * 4
 # kernel, 64-thread strips) thread instructions of one launch at n = 1024
 # divided by the 1024^2 cells (FMA = 2 flops; min/max, compares and
 # conversions not counted; the FP32 kernel's few FP64 instructions, 6 per
-# cell, are left out).  FP32-mixed was counted before its limiter took
-# float-float deviations from the average, which adds 16 float-float
-# subtractions and a repeated even correction per cell (an estimated 300
-# flops, 5 %) not in this figure.
-FLOPS_2D_PER_CELL = {"fp32_mixed": (2176000747 + 2 * 2024539194 + 315382295) / 1048576.0,
+# cell, are left out).  FP32-mixed: its current kernel (96-thread strips).
+FLOPS_2D_PER_CELL = {"fp32_mixed": (1534052286 + 2 * 2015778192 + 264860949) / 1048576.0,
                      "fp32": (474529627 + 2 * 2199850085 + 288415269) / 1048576.0,
                      "fp64": (412078081 + 2 * 2396458776 + 341564899) / 1048576.0}
 # DRAM bytes (read + write) of one launch per cell, same captures; scaled by
 # cells to the bench size.  The writes undercount the stored DOFs: part of
-# the output is still in L2 when the kernel ends.
-# FP32-mixed: none, its kernel has changed since the capture (the limiter
-# now takes float-float deviations from the average).
-TRAFFIC_2D_PER_CELL = {"fp32_mixed": None, "fp32": (178708480 + 119950336) / 1048576.0,
+# the output is still in L2 when the kernel ends.  FP32-mixed: one launch at
+# the bench size itself, 2048^2 (the fourth launch of the mixed kernel).
+TRAFFIC_2D_PER_CELL = {"fp32_mixed": (789145344 + 693487616) / 4194304.0, "fp32": (178708480 + 119950336) / 1048576.0,
                        "fp64": (358728448 + 294830336) / 1048576.0}
 
 
