@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--two-d", action="store_true",
                     help="the 2D Euler half-step (isentropic vortex, P = 3) instead")
     ap.add_argument("--n2d", type=int, default=2048, help="cells per axis of the 2D workload")
+    ap.add_argument("--rows2d", type=int, default=0,
+                    help="strip height of the 2D FP32-mixed line (0: picked by wcc2d_autotune)")
     ap.add_argument("--workloads2d", action="store_true",
                     help="the paper's 2D Riemann problems at 1200^2 to t_end instead")
     ap.add_argument("--advection", action="store_true",
@@ -761,8 +763,10 @@ FLOPS_2D_PER_CELL = {"fp32_mixed": (1534052286 + 2 * 2015778192 + 264860949) / 1
 # DRAM bytes (read + write) of one launch per cell, same captures; scaled by
 # cells to the bench size.  The writes undercount the stored DOFs: part of
 # the output is still in L2 when the kernel ends.  FP32-mixed: one launch at
-# the bench size itself, 2048^2 (the fourth launch of the mixed kernel).
-TRAFFIC_2D_PER_CELL = {"fp32_mixed": (789145344 + 693487616) / 4194304.0, "fp32": (178708480 + 119950336) / 1048576.0,
+# the bench size itself, 2048^2, per strip height (a strip re-reads one parent
+# row, so the bytes depend slightly on it); heights not captured report none.
+TRAFFIC_2D_MIXED_BY_ROWS = {16: (789145344 + 693487616) / 4194304.0, 19: (782315520 + 693396736) / 4194304.0}
+TRAFFIC_2D_PER_CELL = {"fp32_mixed": None, "fp32": (178708480 + 119950336) / 1048576.0,
                        "fp64": (358728448 + 294830336) / 1048576.0}
 
 
@@ -783,11 +787,18 @@ def two_d_bench(args):
     clocks = ClockSampler()
     clocks.start()
     results = {}
-    for prec, name, steps in ((wcc.FP32_MIXED, "fp32_mixed", args.steps), (wcc.FP32, "fp32", args.steps),
-                              (wcc.FP64, "fp64", max(2, min(args.steps, 3)))):
+    # the headline FP32-mixed line with the strip height picked by
+    # wcc2d_autotune; the default height (16) and the other precisions beside it
+    for prec, name, steps, tune in ((wcc.FP32_MIXED, "fp32_mixed", args.steps, True),
+                                    (wcc.FP32_MIXED, "fp32_mixed_rows16", args.steps, False),
+                                    (wcc.FP32, "fp32", args.steps, False),
+                                    (wcc.FP64, "fp64", max(2, min(args.steps, 3)), False)):
+        rows = args.rows2d if tune and args.rows2d else 16
         with wcc.Solver2D(pr.system, n, n, P, (pr.x_l, pr.x_r, pr.y_l, pr.y_r), pr.bc, precision=prec,
-                          rows_per_cta=16, stream=stream.cuda_stream) as s:
+                          rows_per_cta=rows, stream=stream.cuda_stream) as s:
             s.set_initial(pr.q0)
+            if tune and not args.rows2d:
+                rows = s.autotune(CFL_2D)
             for _ in range(args.warmup):
                 s.step(HALFSTEPS_2D, CFL_2D)
             s.synchronize()
@@ -804,16 +815,20 @@ def two_d_bench(args):
         per_launch_s = total_ms / 1e3 / (steps * HALFSTEPS_2D)
         cells = n * n
         r = {"value": cells / per_launch_s, "ms_per_halfstep": per_launch_s * 1e3, "steps": steps,
-             "gpu_launches": launches}
-        gbs = BYTES_2D_PER_CELL[name] * cells / per_launch_s / 1e9
+             "gpu_launches": launches, "rows_per_cta": rows}
+        kind = name if name in BYTES_2D_PER_CELL else "fp32_mixed"
+        gbs = BYTES_2D_PER_CELL[kind] * cells / per_launch_s / 1e9
         r["hbm"] = {"achieved_gbs": gbs, "peak_gbs": pk["hbm_gbs"], "frac": gbs / pk["hbm_gbs"],
-                    "bytes_per_cell": BYTES_2D_PER_CELL[name],
-                    "traffic": TRAFFIC_2D_PER_CELL[name] * cells if TRAFFIC_2D_PER_CELL[name] else None}
-        if FLOPS_2D_PER_CELL[name]:
-            tf = FLOPS_2D_PER_CELL[name] * cells / per_launch_s / 1e12
+                    "bytes_per_cell": BYTES_2D_PER_CELL[kind],
+                    "traffic": None}
+        per_cell = TRAFFIC_2D_MIXED_BY_ROWS.get(rows) if kind == "fp32_mixed" else TRAFFIC_2D_PER_CELL[kind]
+        if per_cell:
+            r["hbm"]["traffic"] = per_cell * cells
+        if FLOPS_2D_PER_CELL[kind]:
+            tf = FLOPS_2D_PER_CELL[kind] * cells / per_launch_s / 1e12
             peak = FP64_PEAK_TFLOPS if name == "fp64" else fp32_peak
             r["arith"] = {"achieved_tflops": tf, "peak_tflops": peak, "frac": tf / peak,
-                          "flops_per_cell": FLOPS_2D_PER_CELL[name]}
+                          "flops_per_cell": FLOPS_2D_PER_CELL[kind]}
         results[name] = r
     clk = clocks.stop()
     # CPU oracle on a bounded sample: the same vortex at 64 x 64, FP64, a few half-steps

@@ -118,6 +118,19 @@ int wcc2d_get_dt_history(wcc2d_handle h, double* dts, int64_t cap, int64_t* n);
 /* Wait for queued work; reports device-side errors. */
 int wcc2d_synchronize(wcc2d_handle h);
 
+/* Autotuner of the strip height: times rows_per_cta = 8 .. 24 (13
+ * candidates; the count of CTAs, and so how full the last wave of resident
+ * CTAs is, changes with it) on the handle's own current stage at CFL number
+ * cfl, one warm-up and four timed half-steps each (CUDA events on the
+ * handle's stream), keeps the fastest in the handle's options and reports it
+ * in *rows_per_cta (may be NULL).  The stage, its time and step count and the
+ * dt history are restored afterwards (the launch count is not); the results
+ * of later half-steps do not depend on the strip height.  Allocates a copy of
+ * the stage while it runs.  Synchronous.  Errors: WCC_E_STATE before
+ * wcc2d_set_initial, WCC_E_INVAL (cfl), WCC_E_NOMEM, WCC_E_CUDA, and the
+ * device-side errors of the timed half-steps (the state is restored). */
+int wcc2d_autotune(wcc2d_handle h, double cfl, int* rows_per_cta);
+
 /* Kernel launches issued by this handle since creation. */
 int wcc2d_launch_count(wcc2d_handle h, int64_t* n);
 

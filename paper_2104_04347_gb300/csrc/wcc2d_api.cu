@@ -470,6 +470,74 @@ int wcc2d_get_dt_history(wcc2d_handle h, double* dts, int64_t cap, int64_t* n) {
     return rc;
 }
 
+int wcc2d_autotune(wcc2d_handle h, double cfl, int* rows_per_cta) {
+    WccTraceRange trace_("wcc2d_autotune");
+    if (!h) return fail2(h, WCC_E_INVAL, "NULL handle");
+    DeviceScope ds_(h->device);
+    if (!h->loaded) return fail2(h, WCC_E_STATE, "wcc2d_set_initial has not succeeded");
+    if (!(cfl > 0) || !std::isfinite(cfl)) return fail2(h, WCC_E_INVAL, "bad cfl");
+    // Strip heights around the measured optimum: the number of CTAs, and so
+    // how full the last wave of resident CTAs is, changes with the height.
+    static const int kRows[] = {8, 10, 12, 13, 14, 15, 16, 17, 18, 19, 20, 22, 24};
+    constexpr int kWarm = 1, kTimed = 4;
+    const size_t stage_bytes = (size_t)(h->nv * (h->nq + (h->mixed ? 1 : 0))) * (size_t)h->plane * elem_size(h);
+    int rc = ensure_history(h, h->steps + kWarm + kTimed);
+    if (rc != WCC_OK) return rc;
+    void* save = nullptr;
+    if (cudaMalloc(&save, stage_bytes + sizeof(DevState2D)) != cudaSuccess) {
+        cudaGetLastError();
+        return fail2(h, WCC_E_NOMEM, "cudaMalloc of the stage copy failed");
+    }
+    char* sv = static_cast<char*>(save);
+    const int cur0 = h->cur, parity0 = h->parity, rows0 = h->opt.rows_per_cta;
+    const long long steps0 = h->steps;
+    cudaMemcpyAsync(sv, h->planes[cur0], stage_bytes, cudaMemcpyDeviceToDevice, h->stream);
+    cudaMemcpyAsync(sv + stage_bytes, h->st, sizeof(DevState2D), cudaMemcpyDeviceToDevice, h->stream);
+    auto restore = [&]() {
+        cudaMemcpyAsync(h->planes[cur0], sv, stage_bytes, cudaMemcpyDeviceToDevice, h->stream);
+        cudaMemcpyAsync(h->st, sv + stage_bytes, sizeof(DevState2D), cudaMemcpyDeviceToDevice, h->stream);
+        h->cur = cur0;
+        h->parity = parity0;
+        h->steps = steps0;
+    };
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_rows = rows0;
+    for (int rows : kRows) {
+        h->opt.rows_per_cta = rows;
+        for (int k = 0; k < kWarm + kTimed && rc == WCC_OK; ++k) {
+            if (k == kWarm) cudaEventRecord(e0, h->stream);
+            rc = launch_one(h, 0.0, cfl);
+        }
+        cudaEventRecord(e1, h->stream);
+        if (rc != WCC_OK) break;
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = fail2(h, WCC_E_CUDA, "autotune: a timed half-step failed");
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_rows = rows;
+        }
+        restore();
+    }
+    if (rc != WCC_OK) restore();
+    h->opt.rows_per_cta = rc == WCC_OK ? best_rows : rows0;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const cudaError_t se = cudaStreamSynchronize(h->stream);
+    cudaFree(save);
+    if (rc != WCC_OK) return rc;
+    if (se != cudaSuccess) return cuda_fail2(h, se, "autotune");
+    if (rows_per_cta) *rows_per_cta = best_rows;
+    DevState2D s;
+    return read_state(h, &s);
+}
+
 int wcc2d_synchronize(wcc2d_handle h) {
     if (!h) return fail2(h, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);

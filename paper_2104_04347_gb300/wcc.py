@@ -130,6 +130,7 @@ _SIGS = {
     "wcc2d_get_dofs": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64]),
     "wcc2d_get_state": (ctypes.c_int, [ctypes.c_void_p, _dp, _i64p, ctypes.POINTER(ctypes.c_int)]),
     "wcc2d_get_dt_history": (ctypes.c_int, [ctypes.c_void_p, _dp, ctypes.c_int64, _i64p]),
+    "wcc2d_autotune": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_double, ctypes.POINTER(ctypes.c_int)]),
     "wcc2d_synchronize": (ctypes.c_int, [ctypes.c_void_p]),
     "wcc2d_launch_count": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
     "wcc2d_device_bytes": (ctypes.c_int, [ctypes.c_void_p, _i64p]),
@@ -562,6 +563,12 @@ class Solver2D:
         out = np.empty(n.value)
         self._check(self.lib.wcc2d_get_dt_history(self.h, out.ctypes.data_as(_dp), out.size, ctypes.byref(n)))
         return out
+
+    def autotune(self, cfl: float) -> int:
+        """Time the strip heights on the current stage, keep the fastest, restore the state."""
+        r = ctypes.c_int()
+        self._check(self.lib.wcc2d_autotune(self.h, float(cfl), ctypes.byref(r)))
+        return r.value
 
     def synchronize(self) -> None:
         self._check(self.lib.wcc2d_synchronize(self.h))
