@@ -306,7 +306,7 @@ int wcc_measure_fp_peak(int precision, double* tflops);
  * buffers the caller owns, and calls no cudaMalloc, cudaFree or other
  * allocating routine.
  *
- * Arguments: system, P (1..4), bc, N (4..2^31), domain as in wcc_create; opt may be
+ * Arguments: system, P (1..6), bc, N (4..2^31), domain as in wcc_create; opt may be
  * NULL (opt->precision must be WCC_FP64; opt->cuda_stream is the stream,
  * NULL = legacy default stream).  parity is the stage parity of the input.
  * stage_a (input) and stage_b are device buffers of nv*(P+1) FP64 planes,

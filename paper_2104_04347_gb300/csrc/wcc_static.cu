@@ -116,7 +116,7 @@ cudaError_t speed_kernel(int system, const double* planes, long long var_stride,
 extern "C" int wcc_advance_static(int system, int P, int bc, int64_t N, const double domain[2],
                                   const wcc_options* opt, int parity, double* stage_a, double* stage_b,
                                   int64_t pitch, int64_t nsteps, double cfl, double* dts_out) {
-    if (system < WCC_ADVECTION || system > WCC_EULER || P < 1 || P > 4) return WCC_E_INVAL;
+    if (system < WCC_ADVECTION || system > WCC_EULER || P < 1 || P > 6) return WCC_E_INVAL;
     if (bc != WCC_BC_PERIODIC && bc != WCC_BC_TRANSMISSIVE) return WCC_E_INVAL;
     if (N < 4 || N > (1ll << 31) || !domain || !(domain[1] > domain[0]) || (parity != 0 && parity != 1))
         return WCC_E_INVAL;

@@ -59,6 +59,7 @@ CASES = [
     ("euler-riemann-transmissive", lambda: inputs.euler_riemann_seeded(1000, 3), 33, 31),
     ("burgers-periodic", lambda: inputs.burgers_fourier(1000, 2), 17, 16),
     ("euler-riemann-even", lambda: inputs.euler_riemann_seeded(1000, 3), 40, 40),
+    ("euler-density-wave-p6", lambda: inputs.euler_density_wave(500, 6), 9, 12),
 ]
 
 
@@ -67,7 +68,8 @@ def test_static_entry_matches_wcc_step_two_calls(name, make, n1, n2):
     torch = pytest.importorskip("torch")
     lib = wcc.load()
     pr = make()
-    N, P, cfl = pr.N, pr.P, 0.2
+    N, P = pr.N, pr.P
+    cfl = 0.2 if P <= 4 else 0.14  # below the linear stability limit of P = 6 (0.185)
     nv, K = pr.q0.shape[1], P + 1
     pitch = (N + 1 + 63) // 64 * 64
     bufs = [torch.tensor(_to_planes(pr.q0, pitch), dtype=torch.float64, device="cuda"),
@@ -104,6 +106,8 @@ def test_static_entry_rejects_sizes_beyond_its_limits():
     assert rc == E_INVAL
     rc, _ = _advance(lib, wcc.BURGERS, 3, wcc.PERIODIC, 64, (0.0, 1.0), 0, a, b, 64, 2, 0.2)
     assert rc == E_INVAL  # pitch < N + 1
+    rc, _ = _advance(lib, wcc.BURGERS, 7, wcc.PERIODIC, 64, (0.0, 1.0), 0, a, b, 128, 2, 0.2)
+    assert rc == E_INVAL  # P above 6
     # the context stays usable: a valid call after the rejected ones
     rc, _ = _advance(lib, wcc.BURGERS, 3, wcc.PERIODIC, 64, (0.0, 1.0), 0, a, b, 128, 0, 0.2)
     assert rc == 0
