@@ -141,6 +141,45 @@ __device__ __forceinline__ ff2 ff2_div(ff2 a, ff2 b) {
 // (a - b) rounded to a pair of floats, a and b close (Sterbenz on the hi parts)
 __device__ __forceinline__ f2 ff2_diff(ff2 a, ff2 b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
+// The same operations without the closing renormalisation, for results that
+// only feed further float-float arithmetic: (hi, lo) with lo a few ulp of hi
+// is as exact a representation of the value, and every operation above reads
+// both parts (a product takes hi * hi exactly and the lo cross terms).
+__device__ __forceinline__ ff2 ff2_add_u(ff2 a, ff2 b) {
+    const ff2 s = two_sum2(a.hi, b.hi);
+    return ff2{s.hi, s.lo + (a.lo + b.lo)};
+}
+__device__ __forceinline__ ff2 ff2_add_fp32_u(ff2 a, f2 b) {
+    const ff2 s = fast_two_sum2(a.hi, b);
+    return ff2{s.hi, s.lo + a.lo};
+}
+__device__ __forceinline__ ff2 ff2_mul_u(ff2 a, ff2 b) {
+    const f2 p = a.hi * b.hi;
+    const f2 e = fma(a.hi, b.hi, -p);
+    return ff2{p, fma(a.hi, b.lo, fma(a.lo, b.hi, e))};
+}
+__device__ __forceinline__ ff2 ff2_div_u(ff2 a, ff2 b) {
+    const f2 rb = rcp_approx(b.hi);
+    const f2 q1 = a.hi * rb;
+    const f2 p = b.hi * q1;
+    const f2 e = fma(b.hi, q1, -p);
+    const f2 rem = (a.hi - p) + (a.lo - fma(b.lo, q1, e));
+    return ff2{q1, rem * rb};
+}
+// a / 2 + b + c for b's FP32-accurate correction c (Fast2Sum on b + c as in
+// ff2_add_fp32), with one renormalisation at the end
+__device__ __forceinline__ ff2 ff2_half_plus(ff2 a, ff2 b, f2 c) {
+    const ff2 x = fast_two_sum2(b.hi, c);
+    const ff2 y = two_sum2(a.hi * f2(0.5f), x.hi);
+    return fast_two_sum2(y.hi, ((a.lo * f2(0.5f) + b.lo) + x.lo) + y.lo);
+}
+// a + (b - c) with one renormalisation at the end
+__device__ __forceinline__ ff2 ff2_add_diff(ff2 a, ff2 b, ff2 c) {
+    const ff2 x = two_sum2(b.hi, -c.hi);
+    const ff2 y = two_sum2(a.hi, x.hi);
+    return fast_two_sum2(y.hi, ((b.lo - c.lo) + a.lo) + (x.lo + y.lo));
+}
+
 // Arithmetic on cell-average quantities: float-float (COMP = true, the
 // FP32-mixed precision) or plain FP32 with the low parts kept at zero
 // (COMP = false, the uncompensated FP32 precision used to measure what the
@@ -153,6 +192,12 @@ struct FF {
     static __device__ __forceinline__ ff2 mul(ff2 a, ff2 b) { return ff2_mul(a, b); }
     static __device__ __forceinline__ ff2 div(ff2 a, ff2 b) { return ff2_div(a, b); }
     static __device__ __forceinline__ f2 diff(ff2 a, ff2 b) { return ff2_diff(a, b); }
+    static __device__ __forceinline__ ff2 add_u(ff2 a, ff2 b) { return ff2_add_u(a, b); }
+    static __device__ __forceinline__ ff2 add_u(ff2 a, f2 b) { return ff2_add_fp32_u(a, b); }
+    static __device__ __forceinline__ ff2 mul_u(ff2 a, ff2 b) { return ff2_mul_u(a, b); }
+    static __device__ __forceinline__ ff2 div_u(ff2 a, ff2 b) { return ff2_div_u(a, b); }
+    static __device__ __forceinline__ ff2 half_plus(ff2 a, ff2 b, f2 c) { return ff2_half_plus(a, b, c); }
+    static __device__ __forceinline__ ff2 add_diff(ff2 a, ff2 b, ff2 c) { return ff2_add_diff(a, b, c); }
 };
 
 template <>
@@ -164,6 +209,12 @@ struct FF<false> {
     static __device__ __forceinline__ ff2 mul(ff2 a, ff2 b) { return mk(a.hi * b.hi); }
     static __device__ __forceinline__ ff2 div(ff2 a, ff2 b) { return mk(fdiv_fast(a.hi, b.hi)); }
     static __device__ __forceinline__ f2 diff(ff2 a, ff2 b) { return a.hi - b.hi; }
+    static __device__ __forceinline__ ff2 add_u(ff2 a, ff2 b) { return add(a, b); }
+    static __device__ __forceinline__ ff2 add_u(ff2 a, f2 b) { return add(a, b); }
+    static __device__ __forceinline__ ff2 mul_u(ff2 a, ff2 b) { return mul(a, b); }
+    static __device__ __forceinline__ ff2 div_u(ff2 a, ff2 b) { return div(a, b); }
+    static __device__ __forceinline__ ff2 half_plus(ff2 a, ff2 b, f2 c) { return mk(a.hi * f2(0.5f) + (b.hi + c)); }
+    static __device__ __forceinline__ ff2 add_diff(ff2 a, ff2 b, ff2 c) { return mk(a.hi + (b.hi - c.hi)); }
 };
 
 // Cell average minus centre value of the Taylor polynomial with coefficients
@@ -183,16 +234,18 @@ template <int SYS, bool COMP>
 __device__ __forceinline__ void flux_ff2(const ff2 (&u)[nvars(SYS)], const StepArgs& args, ff2 (&f)[nvars(SYS)]) {
     using A = FF<COMP>;
     if constexpr (SYS == ADVECTION) {
-        f[0] = A::mul(u[0], ff2{f2(args.adv_hi), f2(COMP ? args.adv_lo : 0.f)});
+        f[0] = A::mul_u(u[0], ff2{f2(args.adv_hi), f2(COMP ? args.adv_lo : 0.f)});
     } else if constexpr (SYS == BURGERS) {
-        f[0] = ff2_scale(A::mul(u[0], u[0]), 0.5f);
+        f[0] = ff2_scale(A::mul_u(u[0], u[0]), 0.5f);
     } else {
-        const ff2 w = A::div(u[1], u[0]);
-        const ff2 q = A::mul(u[1], w);
-        const ff2 p = A::mul(A::add(u[2], ff2_scale(q, -0.5f)), ff2{f2(args.g1_hi), f2(COMP ? args.g1_lo : 0.f)});
+        // every result feeds float-float arithmetic again (lam f below):
+        // no renormalisation in between
+        const ff2 w = A::div_u(u[1], u[0]);
+        const ff2 q = A::mul_u(u[1], w);
+        const ff2 p = A::mul_u(A::add_u(u[2], ff2_scale(q, -0.5f)), ff2{f2(args.g1_hi), f2(COMP ? args.g1_lo : 0.f)});
         f[0] = u[1];
-        f[1] = A::add(q, p);
-        f[2] = A::mul(A::add(u[2], p), w);
+        f[1] = A::add_u(q, p);
+        f[2] = A::mul_u(A::add_u(u[2], p), w);
     }
 }
 
@@ -387,6 +440,8 @@ __device__ __forceinline__ void mixed_parent_records(const ff2 (&ub_in)[nvars(SY
         sfor<0, NV>([&](auto V) {
             constexpr int v = decltype(V)::value;
             const ff2 ub = ub_in[v];
+            // normalised: its high part is the float point value of the
+            // Cauchy-Kovalewski table
             u0[v] = A::add(ub, -average_minus_centre<P>(c[v]));
             c[v][0] = u0[v].hi;
             if constexpr (kPark) {
@@ -400,7 +455,7 @@ __device__ __forceinline__ void mixed_parent_records(const ff2 (&ub_in)[nvars(SY
         flux_ff2<SYS, COMP>(u0, args, f0);
         sfor<0, NV>([&](auto V) {
             constexpr int v = decltype(V)::value;
-            const ff2 lf = A::mul(f0[v], lam2);
+            const ff2 lf = A::mul_u(f0[v], lam2);
             if constexpr (kPark) {
                 put(v, 2, lf.hi);
                 if constexpr (COMP) put(v, 3, lf.lo);
@@ -445,7 +500,7 @@ __device__ __forceinline__ void mixed_parent_records(const ff2 (&ub_in)[nvars(SY
             put(v, 0, ub.hi);
             if constexpr (COMP) put(v, 1, ub.lo);
         }
-        const ff2 Ac = A::add(ff2_scale(ub, 0.5f), A::add(lf, h));
+        const ff2 Ac = A::half_plus(ub, lf, h);
         put(v, 2, Ac.hi);
         if constexpr (COMP) put(v, 3, Ac.lo);
         f2 vt0(0.f);
@@ -483,7 +538,7 @@ __device__ __forceinline__ void mixed_new_cells(const float2* rec, const StepArg
         const ff2 AL{f2(r[2 * W + t]), COMP ? f2(r[3 * W + t]) : zero};
         const ff2 AR{f2(r[2 * W + t + 1]), COMP ? f2(r[3 * W + t + 1]) : zero};
         const f2 eL(r[4 * W + t]), eR(r[4 * W + t + 1]);
-        ubn[v] = A::add(AL, A::sub(uR, AR));  // Eq. SubEq:1DIntegral: A_L + B_R
+        ubn[v] = A::add_diff(AL, uR, AR);  // Eq. SubEq:1DIntegral: A_L + B_R
         // vertex values v_L = ubar_L + dev_L, v_R = ubar_R + dev_R, taken
         // relative to the new average through differences of close numbers
         dl[v] = A::diff(ubn[v], uL) - eL;  // ubar_new - v_L
