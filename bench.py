@@ -164,7 +164,7 @@ FP64_FLOPS_PER_CELL_UPDATE = 885.04
 # tiles are still in L2 when the kernel ends, so the figure is a little below
 # the algorithmic one read + one write of the state.
 FP64_TRAFFIC_2_22 = 402869760 + 352474368
-MIXED_TRAFFIC_2_22 = 251710976 + 200019456
+MIXED_TRAFFIC_2_22 = 251713024 + 200436224
 # FP32 flops per cell-update of the same kernel, from the same capture's
 # executed paired instructions (sm__sass_thread_inst_executed_op_f{add2,ffma2,
 # fmul2}): 158.1 FADD2, 144.6 FFMA2 and 81.8 FMUL2 thread instructions per
