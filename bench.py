@@ -165,14 +165,15 @@ FP64_FLOPS_PER_CELL_UPDATE = 885.04
 # the algorithmic one read + one write of the state.
 FP64_TRAFFIC_2_22 = 402869760 + 352474368
 MIXED_TRAFFIC_2_22 = 251713024 + 200436224
-# FP32 flops per cell-update of the same kernel, from the same capture's
-# executed paired instructions (sm__sass_thread_inst_executed_op_f{add2,ffma2,
-# fmul2}): 158.1 FADD2, 144.6 FFMA2 and 81.8 FMUL2 thread instructions per
-# cell-update.  A thread carries two cells and a paired instruction does one
-# operation for each, so per cell-update that is 2 x 158.1 adds, 2 x 144.6
-# FMAs (2 flops each) and 2 x 81.8 multiplies.  Lane-wise min/max and compares
-# are not counted.
-MIXED_FP32_FLOPS_PER_CELL = 316.2 + 2 * 289.2 + 163.6
+# FP32 flops per cell-update of the same kernel, from one capture at
+# N = 2^21 of its executed paired instructions (sm__sass_thread_inst_executed_
+# op_f{add2,ffma2,fmul2}, thread instructions over the 2097152.5 cells):
+# 135.0 FADD2, 143.6 FFMA2 and 82.3 FMUL2 per cell-update, plus 8.5 scalar
+# FMUL.  A thread carries two cells and a paired instruction does one
+# operation for each, so per cell-update that is 2 x 135.0 adds, 2 x 143.6
+# FMAs (2 flops each), 2 x 82.3 multiplies and 8.5 multiplies.  Lane-wise
+# min/max and compares are not counted.
+MIXED_FP32_FLOPS_PER_CELL = 270.0 + 2 * 287.2 + 164.6 + 8.5
 # FP64 pipe peak of the GB300 (dense, nominal): 1.25 TFLOP/s.
 FP64_PEAK_TFLOPS = 1.25
 
