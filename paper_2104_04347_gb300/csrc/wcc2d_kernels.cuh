@@ -448,7 +448,7 @@ __global__ void __launch_bounds__(TW, 4) halfstep2d_mx(const Step2D a) {
                     r[(v * 8 + k) * TW + t] = c[k].hi;
                     r[(v * 8 + 4 + k) * TW + t] = c[k].lo;
                 }
-                const ff v00 = wcc::ff_add(u00[v], par.V[v][0]);
+                const ff v00 = ff_add_u(u00[v], par.V[v][0]);  // read as a pair only
                 r[(NV * 8 + 2 * v) * TW + t] = v00.hi;
                 r[(NV * 8 + 2 * v + 1) * TW + t] = v00.lo;
 #pragma unroll

@@ -635,10 +635,6 @@ __device__ __forceinline__ T cfl_rate(const T* centre, const Law2D& law, T idx, 
 // is float (as in the 1D FP32-mixed path).
 using wcc::ff;
 
-__device__ __forceinline__ ff ffm(ff a, float b) {  // a * b
-    ff p = wcc::two_prod(a.hi, b);
-    return wcc::fast_two_sum(p.hi, fmaf(a.lo, b, p.lo));
-}
 // a * b as an unnormalised pair (hi, lo): exact product of a.hi, plus a.lo * b
 __device__ __forceinline__ ff ffm_lazy(ff a, float b) {
     const ff p = wcc::two_prod(a.hi, b);
@@ -674,11 +670,32 @@ __device__ __forceinline__ float ff_diff2(ff a, ff b, ff c, ff d) {
     const ff z = wcc::two_sum(y.hi, -d.hi);
     return z.hi + (((a.lo + b.lo) - (c.lo + d.lo)) + ((x.lo + y.lo) + z.lo));
 }
-__device__ __forceinline__ ff ffdiv(ff a, ff b) {  // a / b for a normal b
-    const float q1 = __fdividef(a.hi, b.hi);
-    const ff r = wcc::ff_sub(a, wcc::ff_mul(b, ff{q1, 0.f}));
-    const float q2 = __fdividef(r.hi, b.hi);
-    return wcc::fast_two_sum(q1, q2);
+// Float-float operations without the closing renormalisation, for results
+// that only feed further float-float arithmetic ((hi, lo) with lo a few ulp
+// of hi is as exact a representation; every operation here reads both parts).
+__device__ __forceinline__ ff ff_add_u(ff a, ff b) {
+    const ff s = wcc::two_sum(a.hi, b.hi);
+    return ff{s.hi, s.lo + (a.lo + b.lo)};
+}
+__device__ __forceinline__ ff ff_add_u(ff a, float b) {
+    const ff s = wcc::two_sum(a.hi, b);
+    return ff{s.hi, s.lo + a.lo};
+}
+__device__ __forceinline__ ff ff_mul_u(ff a, ff b) {
+    const ff p = wcc::two_prod(a.hi, b.hi);
+    return ff{p.hi, fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, p.lo))};
+}
+__device__ __forceinline__ ff ff_scale(ff a, float pow2) { return ff{a.hi * pow2, a.lo * pow2}; }
+// a / b for a normal b: q1 = a.hi / b.hi, then the remainder a - b q1 (its
+// leading part a.hi - b.hi q1 is exact, Sterbenz) divided by b.hi; one
+// reciprocal estimate serves both quotients
+__device__ __forceinline__ ff ffdiv_u(ff a, ff b) {
+    const float rb = __fdividef(1.f, b.hi);
+    const float q1 = a.hi * rb;
+    const float p = b.hi * q1;
+    const float e = fmaf(b.hi, q1, -p);
+    const float rem = (a.hi - p) + (a.lo - fmaf(b.lo, q1, e));
+    return ff{q1, rem * rb};
 }
 
 // f(u) and g(u) at a point value u given in float-float (the (0,0,0) entries
@@ -686,25 +703,32 @@ __device__ __forceinline__ ff ffdiv(ff a, ff b) {  // a / b for a normal b
 template <int SYS>
 __device__ __forceinline__ void lead_flux_ff(const ff (&u)[nvars(SYS)], const Law2D& law, ff (&F)[nvars(SYS)],
                                              ff (&G)[nvars(SYS)]) {
+    // every result feeds float-float arithmetic again (the shares take
+    // hx f, hy g as exact products): no renormalisation in between; the
+    // constants (a_x, a_y, gamma - 1) enter as float-float pairs
+    auto pair = [](double c) {
+        const float h = (float)c;
+        return ff{h, (float)(c - (double)h)};
+    };
     if constexpr (SYS == ADVECTION) {
-        F[0] = ffm(u[0], (float)law.ax);
-        G[0] = ffm(u[0], (float)law.ay);
+        F[0] = ff_mul_u(u[0], pair(law.ax));
+        G[0] = ff_mul_u(u[0], pair(law.ay));
     } else if constexpr (SYS == BURGERS) {
-        F[0] = ffm(wcc::ff_mul(u[0], u[0]), 0.5f);
+        F[0] = ff_scale(ff_mul_u(u[0], u[0]), 0.5f);
         G[0] = F[0];
     } else {
-        const ff vx = ffdiv(u[1], u[0]), vy = ffdiv(u[2], u[0]);
-        const ff mu = wcc::ff_mul(u[1], vx), mv = wcc::ff_mul(u[1], vy), nv = wcc::ff_mul(u[2], vy);
-        const ff p = ffm(wcc::ff_sub(u[3], ffm(wcc::ff_add(mu, nv), 0.5f)), (float)(law.gamma - 1.0));
-        const ff Ep = wcc::ff_add(u[3], p);
+        const ff vx = ffdiv_u(u[1], u[0]), vy = ffdiv_u(u[2], u[0]);
+        const ff mu = ff_mul_u(u[1], vx), mv = ff_mul_u(u[1], vy), nv = ff_mul_u(u[2], vy);
+        const ff p = ff_mul_u(ff_add_u(u[3], ff_scale(ff_add_u(mu, nv), -0.5f)), pair(law.gamma - 1.0));
+        const ff Ep = ff_add_u(u[3], p);
         F[0] = u[1];
-        F[1] = wcc::ff_add(mu, p);
+        F[1] = ff_add_u(mu, p);
         F[2] = mv;
-        F[3] = wcc::ff_mul(Ep, vx);
+        F[3] = ff_mul_u(Ep, vx);
         G[0] = u[2];
         G[1] = mv;
-        G[2] = wcc::ff_add(nv, p);
-        G[3] = wcc::ff_mul(Ep, vy);
+        G[2] = ff_add_u(nv, p);
+        G[3] = ff_mul_u(Ep, vy);
     }
 }
 
