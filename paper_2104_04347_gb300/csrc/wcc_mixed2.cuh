@@ -564,7 +564,11 @@ __device__ __forceinline__ void mixed_new_cells(const float2* rec, const StepArg
             f2 cd[3][K], cdl[3], cdr[3];
             E.left(dl[0], dl[1], dl[2], cdl);
             E.left(dr[0], dr[1], dr[2], cdr);
-            sfor<0, K>([&](auto Ki) {
+            // the point value less the average is minus the even
+            // correction of the coefficients k >= 2 (the limiter keeps the
+            // average), a linear map that the projections commute with: it
+            // is formed on each side instead of being projected
+            sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
                 f2 w[3];
                 E.left(d[0][k], d[1][k], d[2][k], w);
@@ -574,11 +578,16 @@ __device__ __forceinline__ void mixed_new_cells(const float2* rec, const StepArg
             });
             sfor<0, 3>([&](auto Ii) {
                 constexpr int rr = decltype(Ii)::value;
+                cd[rr][0] = -average_minus_centre<P>(cd[rr]);
                 limit_deviation_f2<P>(cd[rr], cdl[rr], cdr[rr], args);
             });
-            sfor<0, K>([&](auto Ki) {
+            sfor<1, K>([&](auto Ki) {
                 constexpr int k = decltype(Ki)::value;
                 E.right(cd[0][k], cd[1][k], cd[2][k], d[0][k], d[1][k], d[2][k]);
+            });
+            sfor<0, 3>([&](auto Vi) {
+                constexpr int v = decltype(Vi)::value;
+                d[v][0] = -average_minus_centre<P>(d[v]);
             });
         }
     }
