@@ -51,6 +51,8 @@ def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--e2e-in-flight", type=int, default=E2E_IN_FLIGHT,
+                    help="problems in flight in the end-to-end leg (each on its own stream and host thread)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="wcc", choices=["wcc", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed"])
@@ -86,19 +88,19 @@ E2E_IN_FLIGHT = 3
 E2E_STEPS = 10  # timed steps per in-flight problem of the end-to-end leg
 
 
-def e2e_bench(wcc, pr, prec, cells_per_step, steps, dev, barrier):
+def e2e_bench(wcc, pr, prec, cells_per_step, steps, dev, barrier, in_flight=E2E_IN_FLIGHT):
     """Whole-job throughput through the public API with host buffers.
 
     Every step of every in-flight problem is wcc_set_initial from pinned host
     memory (copy engine H2D, then the layout conversion on the device), one
     graph of 32 half-steps and wcc_get_dofs back into pinned host memory (the
-    call synchronises).  E2E_IN_FLIGHT problems run on their own host threads
+    call synchronises).  in_flight problems run on their own host threads
     (the binding releases the GIL in every call); "serial_value" is the same
     loop with one problem."""
     import torch
     count = pr.q0.size
     jobs = []
-    for _ in range(E2E_IN_FLIGHT):
+    for _ in range(in_flight):
         st = torch.cuda.Stream()
         s = wcc.Solver(pr.system, pr.N, P, (pr.x_l, pr.x_r), pr.bc, precision=prec,
                        graph_chunk=HALFSTEPS_PER_STEP, stream=st.cuda_stream)
@@ -164,7 +166,7 @@ FP64_FLOPS_PER_CELL_UPDATE = 885.04
 # tiles are still in L2 when the kernel ends, so the figure is a little below
 # the algorithmic one read + one write of the state.
 FP64_TRAFFIC_2_22 = 402869760 + 352474368
-MIXED_TRAFFIC_2_22 = 251713024 + 200436224
+MIXED_TRAFFIC_2_22 = 251716864 + 200629504
 # FP32 flops per cell-update of the same kernel, from one capture at
 # N = 2^21 of its executed paired instructions (sm__sass_thread_inst_executed_
 # op_f{add2,ffma2,fmul2}, thread instructions over the 2097152.5 cells):
@@ -558,7 +560,7 @@ def run_wcc(args, rank, world):
     # 10 steps per in-flight problem whatever --steps is, so that filling and
     # draining the pipeline of problems is a small part of the timed region
     e2e = e2e_bench(wcc, pr, wcc.FP64 if args.precision == "fp64" else wcc.FP32_MIXED, cells_per_step,
-                    E2E_STEPS, dev, barrier)
+                    E2E_STEPS, dev, barrier, args.e2e_in_flight)
 
     fp64_peak_meas = wcc.measure_fp_peak(wcc.FP64)
     fp32_peak_meas = wcc.measure_fp_peak(wcc.FP32_MIXED)
