@@ -66,7 +66,8 @@ enum {
     WCC_E_CUDA = -4,       /* CUDA runtime error (no device, launch failure, ...) */
     WCC_E_NONFINITE = -5,  /* a new DOF or the CFL bound became NaN / Inf */
     WCC_E_POSITIVITY = -6, /* Euler: non-positive density or pressure at a cell centre */
-    WCC_E_CAPACITY = -7    /* a size above a documented maximum */
+    WCC_E_CAPACITY = -7,   /* a size above a documented maximum */
+    WCC_E_CFL = -8         /* a CFL number above the degree's linear stability limit */
 };
 
 /* Scheme and launch options.  wcc_default_options fills:
@@ -142,8 +143,10 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count);
 /* Advance nsteps half-steps with dt = cfl * dx / a_max, a_max the largest
  * characteristic speed (|a|, |u| or |u| + c) over the centre point values of
  * the stage being advanced, evaluated on the device (no host round trip).
- * cfl > 0.  Asynchronous on the handle's stream (with tb_depth = 2: the
- * half-steps go in pairs and the call waits for them, see wcc_options). */
+ * 0 < cfl <= wcc_stability_limit(P) (the von Neumann limit of the linear
+ * scheme, Sec. 2.3); a larger cfl is WCC_E_CFL and takes no step.
+ * Asynchronous on the handle's stream (with tb_depth = 2: the half-steps go
+ * in pairs and the call waits for them, see wcc_options). */
 int wcc_step(wcc_handle h, int64_t nsteps, double cfl);
 
 /* Autotuner of the single-grid launch: times every compiled launch
@@ -181,6 +184,7 @@ int wcc_step_dt(wcc_handle h, int64_t nsteps, const double* dts);
  * the time is taken in one step.  Must start on an integer stage
  * (WCC_E_STATE otherwise); t_end before the current time is WCC_E_INVAL.
  * *nsteps_taken (may be NULL) receives the number of half-steps taken.
+ * cfl as in wcc_step (WCC_E_CFL above the stability limit).
  * Synchronous; reports device-side errors. */
 int wcc_step_until(wcc_handle h, double t_end, double cfl, int64_t* nsteps_taken);
 
@@ -236,7 +240,9 @@ int wcc_batch_create(wcc_batch* out, int system, int64_t count, const int64_t* N
 int wcc_batch_dof_count(wcc_batch b, int64_t* count);
 /* Load integer stages of all instances (t = 0); synchronous. */
 int wcc_batch_set_initial(wcc_batch b, const double* dofs, int64_t count);
-/* nsteps half-steps of every instance, each with its own CFL dt; asynchronous. */
+/* nsteps half-steps of every instance, each with its own CFL dt;
+ * asynchronous.  cfl above the stability limit of either degree is
+ * WCC_E_CFL. */
 int wcc_batch_step(wcc_batch b, int64_t nsteps, double cfl);
 int wcc_batch_get_dofs(wcc_batch b, double* dofs, int64_t count);
 /* t[count]: the time of every instance (user order). */
@@ -309,6 +315,7 @@ int wcc_measure_fp_peak(int precision, double* tflops);
  * Arguments: system, P (1..6), bc, N (4..2^31), domain as in wcc_create; opt may be
  * NULL (opt->precision must be WCC_FP64; opt->cuda_stream is the stream,
  * NULL = legacy default stream).  parity is the stage parity of the input.
+ * cfl as in wcc_step (WCC_E_CFL above the degree's stability limit).
  * stage_a (input) and stage_b are device buffers of nv*(P+1) FP64 planes,
  * plane (v, k) at offset (v*(P+1) + k) * pitch elements, holding the Taylor
  * coefficients e_k = u_kx / k! of cell i at index i; pitch >= N + 1, both

@@ -669,14 +669,31 @@ int wcc_set_initial(wcc_handle h, const double* dofs, int64_t count) {
     return WCC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// A CFL number must be positive and at most the degree's linear stability
+// limit (Sec. 2.3, Table 1; wcc_stability_limit).
+int check_cfl(wcc_ctx* h, double cfl) {
+    if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
+    double lim = 0.0;
+    if (wcc_stability_limit(h->P, &lim) == WCC_OK && cfl > lim)
+        return fail(h, WCC_E_CFL, "cfl above the linear stability limit of the degree (wcc_stability_limit)");
+    return WCC_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int wcc_step(wcc_handle h, int64_t nsteps, double cfl) {
     WccTraceRange trace_("wcc_step");
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
     if (nsteps < 0) return fail(h, WCC_E_INVAL, "nsteps < 0");
-    if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
-    int rc = ensure_history(h, h->steps + nsteps);
+    int rc = check_cfl(h, cfl);
+    if (rc != WCC_OK) return rc;
+    rc = ensure_history(h, h->steps + nsteps);
     if (rc != WCC_OK) return rc;
     if (h->opt.tb_depth == 2) return step_pairs(h, nsteps, cfl);
     return step_single(h, nsteps, cfl);
@@ -698,7 +715,7 @@ int wcc_autotune(wcc_handle h, double cfl, int* cells_per_block, int* tb_depth) 
     if (!h) return fail(nullptr, WCC_E_INVAL, "NULL handle");
     DeviceScope ds_(h->device);
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
-    if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
+    if (int rc = check_cfl(h, cfl)) return rc;
     struct Cand {
         int cpb, tb;
     };
@@ -842,7 +859,7 @@ int wcc_step_until(wcc_handle h, double t_end, double cfl, int64_t* nsteps_taken
     DeviceScope ds_(h->device);
     if (nsteps_taken) *nsteps_taken = 0;
     if (!h->initialised) return fail(h, WCC_E_STATE, "wcc_set_initial has not been called");
-    if (!(cfl > 0.0) || !(cfl < 1e6)) return fail(h, WCC_E_INVAL, "cfl must be a positive number");
+    if (int rc = check_cfl(h, cfl)) return rc;
     if (!(std::fabs(t_end) < 1e300)) return fail(h, WCC_E_INVAL, "t_end must be finite");
     if (h->parity != 0) return fail(h, WCC_E_STATE, "wcc_step_until starts on an integer stage");
     DevState s;

@@ -391,6 +391,13 @@ int do_step_pairs(wcc_batch_ctx* b, long long nsteps, double cfl) {
     return WCC_OK;
 }
 
+// cfl above the linear stability limit (Sec. 2.3) of either degree
+bool cfl_above_limit(const wcc_batch_ctx* b, double cfl) {
+    double la = 0.0, lb = 0.0;
+    if (wcc_stability_limit(b->PA, &la) != WCC_OK || wcc_stability_limit(b->PB, &lb) != WCC_OK) return false;
+    return cfl > std::min(la, lb);
+}
+
 int do_step(wcc_batch_ctx* b, long long nsteps, double cfl) {
     int rc = ensure_hist(b, b->steps + nsteps);
     if (rc != WCC_OK) return rc;
@@ -656,6 +663,8 @@ int wcc_batch_step(wcc_batch b, int64_t nsteps, double cfl) {
     DeviceScope ds_(b->device);
     if (!b->initialised) return bfail(b, WCC_E_STATE, "wcc_batch_set_initial has not been called");
     if (nsteps < 0 || !(cfl > 0.0) || !(cfl < 1e6)) return bfail(b, WCC_E_INVAL, "need nsteps >= 0 and cfl > 0");
+    if (cfl_above_limit(b, cfl))
+        return bfail(b, WCC_E_CFL, "cfl above the linear stability limit of a degree (wcc_stability_limit)");
     return do_step(b, nsteps, cfl);
 }
 
@@ -733,6 +742,8 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
     DeviceScope ds_(b->device);
     if (!b->initialised) return bfail(b, WCC_E_STATE, "wcc_batch_set_initial has not been called");
     if (!(cfl > 0.0)) return bfail(b, WCC_E_INVAL, "cfl must be positive");
+    if (cfl_above_limit(b, cfl))
+        return bfail(b, WCC_E_CFL, "cfl above the linear stability limit of a degree (wcc_stability_limit)");
     // Candidates: persistent grids of 1..max resident CTAs per SM and one
     // CTA per tile, each with one half-step per launch and (where the degree
     // mix has the kernel) two.  Each is timed over eight half-steps on the

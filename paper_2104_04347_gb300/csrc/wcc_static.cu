@@ -122,6 +122,8 @@ extern "C" int wcc_advance_static(int system, int P, int bc, int64_t N, const do
         return WCC_E_INVAL;
     if (!stage_a || !stage_b || stage_a == stage_b) return WCC_E_INVAL;
     if (nsteps < 0 || !(cfl > 0.0) || !(cfl < 1e6)) return WCC_E_INVAL;
+    double nu_limit = 0.0;
+    if (wcc_stability_limit(P, &nu_limit) == WCC_OK && cfl > nu_limit) return WCC_E_CFL;
     if (nsteps > WCC_STATIC_MAX_HALFSTEPS) return WCC_E_CAPACITY;
     if (pitch < N + 1 || (((uintptr_t)stage_a | (uintptr_t)stage_b) & 7u)) return WCC_E_INVAL;
     wcc_options o;

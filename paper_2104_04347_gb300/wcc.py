@@ -23,7 +23,7 @@ FP64, FP32_MIXED, FP32 = 0, 1, 2
 
 ERRORS = {
     -1: "WCC_E_INVAL", -2: "WCC_E_STATE", -3: "WCC_E_NOMEM", -4: "WCC_E_CUDA",
-    -5: "WCC_E_NONFINITE", -6: "WCC_E_POSITIVITY", -7: "WCC_E_CAPACITY",
+    -5: "WCC_E_NONFINITE", -6: "WCC_E_POSITIVITY", -7: "WCC_E_CAPACITY", -8: "WCC_E_CFL",
 }
 
 
