@@ -38,8 +38,8 @@ def _batch(count, seed, degrees=(2, 3), n_max=900):
     return inputs.batch_workload(count, n_min=8, n_max=n_max, seed=seed, degrees=degrees)
 
 
-def _run(probs, nsteps, *, tb_depth=2, growth=0.1, grid=None):
-    with wcc.Batch(probs, tb_depth=tb_depth, tb_cfl_growth=growth) as b:
+def _run(probs, nsteps, *, tb_depth=2, growth=0.1, grid=None, graph_chunk=32):
+    with wcc.Batch(probs, tb_depth=tb_depth, tb_cfl_growth=growth, graph_chunk=graph_chunk) as b:
         b.set_initial()
         if grid is not None:
             b.set_grid(grid)
@@ -117,6 +117,21 @@ def test_any_persistent_grid_gives_the_same_result(grid):
     got, _, _, _, _ = _run(probs, 20, growth=10.0, grid=grid)
     for a, b in zip(ref, got):
         assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("growth", [0.1, -1.0])
+def test_direct_launches_equal_graphs(growth):
+    # graph_chunk 0 launches every pair directly; 6 pairs per graph leaves a
+    # direct tail; refusals (growth -1) go through the same recovery
+    probs = _batch(12, 17)
+    ref = _run(probs, 38, growth=growth)
+    for chunk in (0, 12):
+        got = _run(probs, 38, growth=growth, graph_chunk=chunk)
+        assert got[2] == ref[2] and got[3] == ref[3]
+        for a, b in zip(got[1], ref[1]):
+            assert np.array_equal(a, b)
+        for a, b in zip(got[0], ref[0]):
+            assert np.array_equal(a, b)
 
 
 def test_autotune_chooses_depth_and_keeps_the_state():
