@@ -72,6 +72,26 @@ struct Law2D {
     int limiter;
 };
 
+// 1/x and sqrt(x) for a positive normal x: FP64 as printed (IEEE division
+// and square root); FP32 from the hardware estimates, the reciprocal refined
+// by one Newton step (within an ulp or two)
+template <class T>
+__device__ __forceinline__ T recip_t(T x) {
+    if constexpr (sizeof(T) == 8) {
+        return (T)1 / x;
+    } else {
+        const float r = __fdividef(1.f, x);
+        return fmaf(r, fmaf(-x, r, 1.f), r);
+    }
+}
+template <class T>
+__device__ __forceinline__ T sqrt_t(T x) {
+    if constexpr (sizeof(T) == 8)
+        return sqrt(x);
+    else
+        return x * rsqrtf(x);
+}
+
 template <class T>
 __device__ __forceinline__ T weight_pow(T x, T alpha) {
     if constexpr (sizeof(T) == 8)
@@ -219,7 +239,7 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
                             });
                         });
                     });
-                    const T inv_rho = (T)1 / U[0][0][0][0];
+                    const T inv_rho = recip_t(U[0][0][0][0]);
                     w1[k][l][m] = s1 * inv_rho;
                     w2[k][l][m] = s2 * inv_rho;
                     T qxx = 0, qxy = 0, qyy = 0;
@@ -442,7 +462,7 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
                 w[m] = weight_pow<T>(weight_ratio(bmin, beta[m] + eps), alpha);
                 s += w[m];
             }
-            const T is = (T)1 / s;  // s >= 1
+            const T is = recip_t(s);  // s >= 1
 #pragma unroll
             for (int m = 0; m < 5; ++m) w[m] *= is;
         }
@@ -483,8 +503,15 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
                 den[m] = beta[m] * beta[m] + eps;
                 dmin = fminf(dmin, den[m]);
             }
-            const T lead = weight_pow<T>(dmin / st, alpha);  // the "1 +" of w_0, rescaled
-            if (!(st > (T)0) || isinf(lead)) {
+            // the "1 +" of w_0, rescaled.  dmin and st both scaled by 2^64
+            // (exact), so that a subnormal st (its dmin can be subnormal too:
+            // eps = 1e-40) is a normal number for the reciprocal; st above
+            // 2^62 gives lead = 0, its value to rounding
+            const T lead = weight_pow<T>((dmin * 0x1p64f) * recip_t(st * 0x1p64f), alpha);
+            // lead above 2^30 puts the other weights below 5 2^-30 of the
+            // sum: w_0 rounds to 1 (this also keeps the sum, and so the
+            // reciprocal below, in range)
+            if (!(st > (T)0) || !(lead < 0x1p30f)) {
                 w[0] = 1;
                 w[1] = w[2] = w[3] = w[4] = 0;
             } else {
@@ -495,7 +522,7 @@ __device__ __forceinline__ void limit_scalar(T (&d)[nq(P)], T ub, const T (&vv)[
                     if (m == 0) w[m] += lead;
                     s += w[m];
                 }
-                const T is = (T)1 / s;  // s >= 1
+                const T is = recip_t(s);  // s >= 1
 #pragma unroll
                 for (int m = 0; m < 5; ++m) w[m] *= is;
             }
@@ -559,15 +586,18 @@ __device__ __forceinline__ bool limit_euler(T (&D)[4][nq(P)], const T (&ub)[4], 
         b1 = gm1 / (c * c);
         ic = (T)1 / c;
     } else {
-        const T irho = (T)1 / rho;
+        const T irho = recip_t(rho);
         u = ub[1] * irho;
         v = ub[2] * irho;
         q2 = u * u + v * v;
         p = gm1 * (ub[3] - (T)0.5 * rho * q2);
         if (!(rho > (T)0) || !(p > (T)0)) return false;
-        c = sqrtf((T)law.gamma * p * irho);
+        // c and 1/c within an ulp of each other, so that the left and right
+        // eigenvectors stay inverse to float rounding (the projection and the
+        // back-projection then cancel where the weights are linear)
+        c = sqrt_t((T)law.gamma * p * irho);
+        ic = recip_t(c);
         H = (ub[3] + p) * irho;
-        ic = (T)1 / c;
         b1 = gm1 * ic * ic;
     }
     const T un = u * nx + v * ny, ut = -u * ny + v * nx;
@@ -620,11 +650,21 @@ __device__ __forceinline__ T cfl_rate(const T* centre, const Law2D& law, T idx, 
     } else if constexpr (SYS == BURGERS) {
         return fabs(centre[0]) * (idx + idy);
     } else {
-        const T rho = centre[0], u = centre[1] / rho, v = centre[2] / rho;
-        const T p = (T)(law.gamma - 1.0) * (centre[3] - (T)0.5 * rho * (u * u + v * v));
-        if (!(rho > (T)0) || !(p > (T)0)) return (T)NAN;
-        const T c = sqrt((T)law.gamma * p / rho);
-        return (fabs(u) + c) * idx + (fabs(v) + c) * idy;
+        const T rho = centre[0];
+        if constexpr (sizeof(T) == 8) {
+            const T u = centre[1] / rho, v = centre[2] / rho;
+            const T p = (T)(law.gamma - 1.0) * (centre[3] - (T)0.5 * rho * (u * u + v * v));
+            if (!(rho > (T)0) || !(p > (T)0)) return (T)NAN;
+            const T c = sqrt((T)law.gamma * p / rho);
+            return (fabs(u) + c) * idx + (fabs(v) + c) * idy;
+        } else {
+            if (!(rho > (T)0)) return (T)NAN;
+            const T irho = recip_t(rho), u = centre[1] * irho, v = centre[2] * irho;
+            const T p = (T)(law.gamma - 1.0) * (centre[3] - (T)0.5 * rho * (u * u + v * v));
+            if (!(p > (T)0)) return (T)NAN;
+            const T c = sqrt_t((T)law.gamma * p * irho);
+            return (fabs(u) + c) * idx + (fabs(v) + c) * idy;
+        }
     }
 }
 

@@ -204,7 +204,9 @@ def test_table3_mesh_1_10_on_gpu(golden_dir, precision):
     # float) has a rounding floor: the cell averages round by ~6e-8 per
     # half-step, which random-walks to an L1 of ~1e-6 over the ~430 half-steps
     # of the run, so its L1 is checked only where the printed L1 is above 1e-5
-    # (P <= 2); its L-inf is checked on every row.  With the limiter at P = 2
+    # (P <= 2); its L-inf is checked on every row, with that floor's maximum
+    # over the 10^4 cells (about four of its standard deviations, 5e-6) added
+    # to the allowance.  With the limiter at P = 2
     # the weights switch where a candidate's slope is at rounding level (the
     # limiter's P = 2 sensitivity), so FP32 gets 15 % there.  FP32-mixed keeps
     # the averages in float-float: every row's L1 and L-inf within 5 %, 15 %
@@ -229,7 +231,8 @@ def test_table3_mesh_1_10_on_gpu(golden_dir, precision):
         tol = 0.15 if (precision != wcc.FP64 and sch == "WCCS" and P == 2) else 0.05
         r1, rinf = e.mean() / l1 - 1, e.max() / linf - 1
         check_l1 = precision != wcc.FP32 or l1 > 1e-5
-        if not ((abs(r1) < tol or not check_l1) and abs(rinf) < tol):
+        floor_inf = 5e-6 if precision == wcc.FP32 else 0.0
+        if not ((abs(r1) < tol or not check_l1) and abs(e.max() - linf) < tol * linf + floor_inf):
             bad.append((sch, P, round(r1, 4), round(rinf, 4)))
     assert not bad, bad
 
