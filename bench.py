@@ -758,19 +758,19 @@ BYTES_2D_PER_CELL = {"fp32_mixed": 2 * 44 * 4, "fp32": 2 * 40 * 4, "fp64": 2 * 4
 # FADD/FMUL/FFMA (FP32 kernel, 128-thread strips) and DADD/DMUL/DFMA (FP64
 # kernel, 64-thread strips) thread instructions of one launch at n = 1024
 # divided by the 1024^2 cells (FMA = 2 flops; min/max, compares and
-# conversions not counted; the FP32 kernel's few FP64 instructions, 6 per
-# cell, are left out).  FP32-mixed: its current kernel (96-thread strips,
-# 19 rows per strip).
-FLOPS_2D_PER_CELL = {"fp32_mixed": (1443993240 + 2 * 2003037726 + 262689561) / 1048576.0,
-                     "fp32": (474529627 + 2 * 2199850085 + 288415269) / 1048576.0,
+# conversions not counted).  FP32-mixed: its current kernel (96-thread
+# strips, 19 rows per strip).  FP32: none, its kernel has changed since it
+# was counted (reciprocals from the hardware estimate).
+FLOPS_2D_PER_CELL = {"fp32_mixed": (1427237486 + 2 * 1959381186 + 268845174) / 1048576.0,
+                     "fp32": None,
                      "fp64": (412078081 + 2 * 2396458776 + 341564899) / 1048576.0}
 # DRAM bytes (read + write) of one launch per cell, same captures; scaled by
 # cells to the bench size.  The writes undercount the stored DOFs: part of
 # the output is still in L2 when the kernel ends.  FP32-mixed: one launch at
 # the bench size itself, 2048^2, per strip height (a strip re-reads one parent
 # row, so the bytes depend slightly on it); heights not captured report none.
-TRAFFIC_2D_MIXED_BY_ROWS = {19: (781659136 + 692695040) / 4194304.0}
-TRAFFIC_2D_PER_CELL = {"fp32_mixed": None, "fp32": (178708480 + 119950336) / 1048576.0,
+TRAFFIC_2D_MIXED_BY_ROWS = {19: (780970496 + 691807488) / 4194304.0}
+TRAFFIC_2D_PER_CELL = {"fp32_mixed": None, "fp32": None,
                        "fp64": (358728448 + 294830336) / 1048576.0}
 
 
