@@ -344,12 +344,15 @@ cudaError_t launch_stage_rate2d_sys(bool fp32, const void* planes, long long pit
 // the cell average (not the point value), planes (v, q >= 1) the scaled
 // derivatives in float, and plane NV * NQ + v the low part of the average.
 // A parent record: per variable its four shares of the children's averages
-// (hi[4], lo[4]), its vertex point value at t^{n+1/2} (hi, lo), and the
-// vertex derivatives q = 1 .. NQ1 - 1 (float).
+// and its vertex point value at t^{n+1/2}, float-float pairs stored as
+// float2 (pair field v * 4 + k for share k, NV * 4 + v for the vertex value),
+// then the vertex derivatives q = 1 .. NQ1 - 1 (float, from float offset
+// 10 NV of the record).
 template <int SYS, int P>
 __host__ __device__ constexpr int record_fields_mx() {
     return nvars(SYS) * (10 + nq(P - 1) - 1);
 }
+
 
 template <int SYS, int P>
 constexpr int strip_width_mx() {
@@ -366,12 +369,16 @@ struct RingReaderMx {
     __device__ __forceinline__ float get(int r, int f) const {
         return r == 0 ? lo[f * TW + t] : r == 1 ? lo[f * TW + t + 1] : r == 2 ? hi[f * TW + t + 1] : hi[f * TW + t];
     }
-    __device__ __forceinline__ ff cf(int r, int v) const { return ff{get(r, v * 8 + r), get(r, v * 8 + 4 + r)}; }
-    __device__ __forceinline__ ff v00(int r, int v) const {
-        return ff{get(r, NV * 8 + 2 * v), get(r, NV * 8 + 2 * v + 1)};
+    __device__ __forceinline__ ff get2(int r, int pf) const {
+        const float2* l2 = reinterpret_cast<const float2*>(lo);
+        const float2* h2 = reinterpret_cast<const float2*>(hi);
+        const float2 x = r == 0 ? l2[pf * TW + t] : r == 1 ? l2[pf * TW + t + 1] : r == 2 ? h2[pf * TW + t + 1] : h2[pf * TW + t];
+        return ff{x.x, x.y};
     }
+    __device__ __forceinline__ ff cf(int r, int v) const { return get2(r, v * 4 + r); }
+    __device__ __forceinline__ ff v00(int r, int v) const { return get2(r, NV * 4 + v); }
     __device__ __forceinline__ float V(int r, int v, int q) const {
-        return q == 0 ? get(r, NV * 8 + 2 * v) : get(r, NV * 10 + v * (NQ1 - 1) + q - 1);
+        return q == 0 ? get2(r, NV * 4 + v).hi : get(r, NV * 10 + v * (NQ1 - 1) + q - 1);
     }
 };
 
@@ -379,6 +386,7 @@ template <int SYS, int P, int TW>
 __global__ void __launch_bounds__(TW, 4) halfstep2d_mx(const Step2D a) {
     constexpr int NV = nvars(SYS), NQ = nq(P), NQ1 = nq(P - 1);
     constexpr int NF = record_fields_mx<SYS, P>();
+    static_assert((NF * TW) % 2 == 0, "the second row buffer of the ring must start on an 8-byte boundary");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float* ring = reinterpret_cast<float*>(smem_raw);  // [2][NF][TW]
 
@@ -447,14 +455,11 @@ __global__ void __launch_bounds__(TW, 4) halfstep2d_mx(const Step2D a) {
                 c[1] = ff_sum4(q4h, -hF.hi, hG.hi, -(dxy + oxy), q4l + (ll - tl));
                 c[2] = ff_sum4(q4h, -hF.hi, -hG.hi, oxy - sxy, q4l - (bl + ll));
                 c[3] = ff_rest3(ub[v], c[0], c[1], c[2]);
+                float2* r2 = reinterpret_cast<float2*>(r);
 #pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    r[(v * 8 + k) * TW + t] = c[k].hi;
-                    r[(v * 8 + 4 + k) * TW + t] = c[k].lo;
-                }
+                for (int k = 0; k < 4; ++k) r2[(v * 4 + k) * TW + t] = make_float2(c[k].hi, c[k].lo);
                 const ff v00 = ff_add_u(u00[v], par.V[v][0]);  // read as a pair only
-                r[(NV * 8 + 2 * v) * TW + t] = v00.hi;
-                r[(NV * 8 + 2 * v + 1) * TW + t] = v00.lo;
+                r2[(NV * 4 + v) * TW + t] = make_float2(v00.hi, v00.lo);
 #pragma unroll
                 for (int qq = 1; qq < NQ1; ++qq) r[(NV * 10 + v * (NQ1 - 1) + qq - 1) * TW + t] = par.V[v][qq];
             }

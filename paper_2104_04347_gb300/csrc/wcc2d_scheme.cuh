@@ -610,6 +610,22 @@ __device__ __forceinline__ bool limit_euler(T (&D)[4][nq(P)], const T (&ub)[4], 
                        {(T)1 - b2, b1 * u, b1 * v, -b1},
                        {-ut, -ny, nx, 0},
                        {(T)0.5 * (b2 - un * ic), (T)-0.5 * (b1 * u - nx * ic), (T)-0.5 * (b1 * v - ny * ic), (T)0.5 * b1}};
+    // With DEV the point value less the average is minus the even correction
+    // of the DOFs (k, l) != (0, 0) (the limiter keeps the average), a linear
+    // map that the projections commute with: it is formed on each side
+    // instead of being projected.
+    constexpr int Q0 = DEV ? 1 : 0;
+    auto even_corr = [](const T (&d)[NQ]) {
+        T s = 0;
+        unroll<P + 1>([&](auto kc) {
+            unroll<P + 1 - kc>([&](auto lc) {
+                constexpr int k = kc, l = lc;
+                if constexpr (k + l > 0 && !(k & 1) && !(l & 1))
+                    s += (T)(pow2m(k) / factd(k + 1) * pow2m(l) / factd(l + 1)) * d[qidx(k, l)];
+            });
+        });
+        return s;
+    };
     T cd[4][NQ], cub[4], cvv[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
@@ -624,20 +640,23 @@ __device__ __forceinline__ bool limit_euler(T (&D)[4][nq(P)], const T (&ub)[4], 
 #pragma unroll
             for (int r = 0; r < 4; ++r) cvv[i][r] += L[i][j] * vv[j][r];
 #pragma unroll
-            for (int qq = 0; qq < NQ; ++qq) cd[i][qq] += L[i][j] * D[j][qq];
+            for (int qq = Q0; qq < NQ; ++qq) cd[i][qq] += L[i][j] * D[j][qq];
         }
+        if constexpr (DEV) cd[i][0] = -even_corr(cd[i]);
     }
 #pragma unroll
     for (int i = 0; i < 4; ++i) limit_scalar<P, T>(cd[i], cub[i], cvv[i], law);
 #pragma unroll
-    for (int j = 0; j < 4; ++j)
+    for (int j = 0; j < 4; ++j) {
 #pragma unroll
-        for (int qq = 0; qq < NQ; ++qq) {
+        for (int qq = Q0; qq < NQ; ++qq) {
             T s = 0;
 #pragma unroll
             for (int i = 0; i < 4; ++i) s += R[j][i] * cd[i][qq];
             D[j][qq] = s;
         }
+        if constexpr (DEV) D[j][0] = -even_corr(D[j]);
+    }
     return true;
 }
 
