@@ -305,6 +305,8 @@ int launch_one(wcc2d_ctx* h, double dt_given, double cfl) {
     a.rows_per_cta = h->opt.rows_per_cta;
     a.dx = h->dx;
     a.dy = h->dy;
+    a.inv_dx = 1.0 / h->dx;
+    a.inv_dy = 1.0 / h->dy;
     a.dt_given = dt_given;
     a.cfl = cfl;
     a.law = h->law;

@@ -40,6 +40,7 @@ struct Step2D {
     int nx_old, ny_old, nx_new, ny_new;
     int parity, bc, rows_per_cta;
     double dx, dy;
+    double inv_dx, inv_dy;  // 1 / dx, 1 / dy (host)
     double dt_given;  // > 0: the half-step size; otherwise cfl / rate of the old stage
     double cfl;
     Law2D law;
@@ -78,6 +79,19 @@ __host__ __device__ constexpr int record_fields() {
 template <class T, int TW>
 __host__ __device__ constexpr size_t ring_bytes(int fields) {
     return 2 * (size_t)fields * TW * sizeof(T);
+}
+
+// The half-step size: dt_given, or cfl over the rate of the old stage.  One
+// thread takes the FP64 division and shares it (block barrier).
+__device__ __forceinline__ double step_dt2d(const Step2D& a) {
+    __shared__ double s_dt;
+    if (threadIdx.x == 0) {
+        double dt = a.dt_given;
+        if (!(dt > 0.0)) dt = a.cfl / __longlong_as_double((long long)a.st->rate_bits[a.parity]);
+        s_dt = dt;
+    }
+    __syncthreads();
+    return s_dt;
 }
 
 // Block-wide max of the rate and OR of the error bits, one atomic each per
@@ -149,10 +163,9 @@ __global__ void __launch_bounds__(TW, min_ctas2d<T>()) halfstep2d(const Step2D a
     const int j0 = blockIdx.y * a.rows_per_cta;
     const int rows = min(a.rows_per_cta, a.ny_new - j0);
 
-    double dt = a.dt_given;
-    if (!(dt > 0.0)) dt = a.cfl / __longlong_as_double((long long)a.st->rate_bits[a.parity]);
-    const T lamx = (T)(dt / a.dx), lamy = (T)(dt / a.dy);
-    const T idx = (T)(1.0 / a.dx), idy = (T)(1.0 / a.dy);
+    const double dt = step_dt2d(a);
+    const T lamx = (T)(dt * a.inv_dx), lamy = (T)(dt * a.inv_dy);
+    const T idx = (T)a.inv_dx, idy = (T)a.inv_dy;
 
     const T* in = static_cast<const T*>(a.in);
     T* out = static_cast<T*>(a.out);
@@ -396,15 +409,14 @@ __global__ void __launch_bounds__(TW, 4) halfstep2d_mx(const Step2D a) {
     const int j0 = blockIdx.y * a.rows_per_cta;
     const int rows = min(a.rows_per_cta, a.ny_new - j0);
 
-    double dt = a.dt_given;
-    if (!(dt > 0.0)) dt = a.cfl / __longlong_as_double((long long)a.st->rate_bits[a.parity]);
+    const double dt = step_dt2d(a);
     // lam rounded to float in every term, the leading flux terms included:
     // the half-step is one of size fl(lam) dx, the same in all its Taylor
     // terms (a float-float lam for the leading terms alone was measured to
     // move the fine-mesh errors away from FP64's, not towards them)
-    const float lamx = (float)(dt / a.dx), lamy = (float)(dt / a.dy);
+    const float lamx = (float)(dt * a.inv_dx), lamy = (float)(dt * a.inv_dy);
     const float hx = 0.5f * lamx, hy = 0.5f * lamy;
-    const float idx = (float)(1.0 / a.dx), idy = (float)(1.0 / a.dy);
+    const float idx = (float)a.inv_dx, idy = (float)a.inv_dy;
 
     const float* in = static_cast<const float*>(a.in);
     float* out = static_cast<float*>(a.out);
