@@ -51,6 +51,9 @@ struct Step2D {
 
 __device__ __forceinline__ int parent_index(int j, int n_old, int bc) {
     if (bc == PERIODIC) {
+        // one wrap covers every index a strip touches on meshes wider than
+        // the strip; the remainder is for the narrow ones
+        if (j >= -n_old && j < 2 * n_old) return j < 0 ? j + n_old : (j >= n_old ? j - n_old : j);
         j %= n_old;
         return j < 0 ? j + n_old : j;
     }
