@@ -760,7 +760,7 @@ BYTES_2D_PER_CELL = {"fp32_mixed": 2 * 44 * 4, "fp32": 2 * 40 * 4, "fp64": 2 * 4
 # divided by the 1024^2 cells (FMA = 2 flops; min/max, compares and
 # conversions not counted).  FP32-mixed: its current kernel (96-thread
 # strips, 19 rows per strip); FP32: 128-thread strips, 16 rows.
-FLOPS_2D_PER_CELL = {"fp32_mixed": (1427237486 + 2 * 1959381186 + 268845174) / 1048576.0,
+FLOPS_2D_PER_CELL = {"fp32_mixed": (1428286042 + 2 * 1928801992 + 264650802) / 1048576.0,
                      "fp32": (430120751 + 2 * 2157143529 + 276917623) / 1048576.0,
                      "fp64": (412078081 + 2 * 2396458776 + 341564899) / 1048576.0}
 # DRAM bytes (read + write) of one launch per cell, same captures; scaled by
@@ -768,7 +768,7 @@ FLOPS_2D_PER_CELL = {"fp32_mixed": (1427237486 + 2 * 1959381186 + 268845174) / 1
 # the output is still in L2 when the kernel ends.  FP32-mixed: one launch at
 # the bench size itself, 2048^2, per strip height (a strip re-reads one parent
 # row, so the bytes depend slightly on it); heights not captured report none.
-TRAFFIC_2D_MIXED_BY_ROWS = {19: (780970496 + 691807488) / 4194304.0}
+TRAFFIC_2D_MIXED_BY_ROWS = {19: (783792128 + 692393472) / 4194304.0}
 TRAFFIC_2D_PER_CELL = {"fp32_mixed": None, "fp32": (178908928 + 122445056) / 1048576.0,
                        "fp64": (358728448 + 294830336) / 1048576.0}
 
