@@ -90,6 +90,20 @@ def test_null_handle_calls_fail_cleanly():
     assert lib.wcc2d_step(None, 1, 0.3) == -1
     assert lib.wcc2d_synchronize(None) == -1
     assert lib.wcc2d_destroy(None) == 0
+    # the tuners, the pair statistics and the batch calls
+    i, j = ctypes.c_int(), ctypes.c_int()
+    n1, n2 = ctypes.c_int64(), ctypes.c_int64()
+    nu = ctypes.c_double()
+    assert lib.wcc_autotune(None, 0.2, ctypes.byref(i), ctypes.byref(j)) == -1
+    assert lib.wcc_tb_stats(None, ctypes.byref(n1), ctypes.byref(n2), ctypes.byref(nu)) == -1
+    assert lib.wcc_step_until(None, 1.0, 0.2, ctypes.byref(n1)) == -1
+    assert lib.wcc2d_autotune(None, 0.2, ctypes.byref(i)) == -1
+    assert lib.wcc_batch_step(None, 1, 0.2) == -1
+    assert lib.wcc_batch_autotune(None, 0.2, ctypes.byref(i)) == -1
+    assert lib.wcc_batch_get_tuning(None, ctypes.byref(i), ctypes.byref(j)) == -1
+    assert lib.wcc_batch_tb_stats(None, ctypes.byref(n1), ctypes.byref(n2)) == -1
+    assert lib.wcc_batch_synchronize(None) == -1
+    lib.wcc_batch_destroy(None)
 
 
 @pytest.mark.parametrize("kw,needle", [
