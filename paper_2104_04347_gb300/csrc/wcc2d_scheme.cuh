@@ -627,6 +627,68 @@ __device__ __forceinline__ bool limit_euler(T (&D)[4][nq(P)], const T (&ub)[4], 
         return s;
     };
     T cd[4][NQ], cub[4], cvv[4][4];
+    if constexpr (sizeof(T) == 4) {
+        // FP32: the projections two DOFs (two vertices) at a time in paired
+        // FP32 instructions (FFMA2)
+        constexpr int NPR = (NQ - Q0) / 2;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            cub[i] = 0;
+            if constexpr (!DEV) {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) cub[i] += L[i][j] * ub[j];
+            }
+#pragma unroll
+            for (int r = 0; r < 4; r += 2) {
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc = __ffma2_rn(make_float2(L[i][j], L[i][j]), make_float2(vv[j][r], vv[j][r + 1]), acc);
+                cvv[i][r] = acc.x;
+                cvv[i][r + 1] = acc.y;
+            }
+#pragma unroll
+            for (int pr = 0; pr < NPR; ++pr) {
+                const int qq = Q0 + 2 * pr;
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    acc = __ffma2_rn(make_float2(L[i][j], L[i][j]), make_float2(D[j][qq], D[j][qq + 1]), acc);
+                cd[i][qq] = acc.x;
+                cd[i][qq + 1] = acc.y;
+            }
+            if constexpr ((NQ - Q0) & 1) {
+                T sum = 0;
+#pragma unroll
+                for (int j = 0; j < 4; ++j) sum += L[i][j] * D[j][NQ - 1];
+                cd[i][NQ - 1] = sum;
+            }
+            if constexpr (DEV) cd[i][0] = -even_corr(cd[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) limit_scalar<P, T>(cd[i], cub[i], cvv[i], law);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int pr = 0; pr < NPR; ++pr) {
+                const int qq = Q0 + 2 * pr;
+                float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    acc = __ffma2_rn(make_float2(R[j][i], R[j][i]), make_float2(cd[i][qq], cd[i][qq + 1]), acc);
+                D[j][qq] = acc.x;
+                D[j][qq + 1] = acc.y;
+            }
+            if constexpr ((NQ - Q0) & 1) {
+                T sum = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) sum += R[j][i] * cd[i][NQ - 1];
+                D[j][NQ - 1] = sum;
+            }
+            if constexpr (DEV) D[j][0] = -even_corr(D[j]);
+        }
+        return true;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         cub[i] = 0;
