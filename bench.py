@@ -758,18 +758,19 @@ BYTES_2D_PER_CELL = {"fp32_mixed": 2 * 44 * 4, "fp32": 2 * 40 * 4, "fp64": 2 * 4
 # FADD/FMUL/FFMA (FP32 kernel, 128-thread strips) and DADD/DMUL/DFMA (FP64
 # kernel, 64-thread strips) thread instructions of one launch at n = 1024
 # divided by the 1024^2 cells (FMA = 2 flops; min/max, compares and
-# conversions not counted).  FP32-mixed: its current kernel (96-thread
-# strips, 19 rows per strip); FP32: 128-thread strips, 16 rows.
-FLOPS_2D_PER_CELL = {"fp32_mixed": (1428286042 + 2 * 1928801992 + 264650802) / 1048576.0,
-                     "fp32": (430120751 + 2 * 2157143529 + 276917623) / 1048576.0,
+# conversions not counted; a paired FADD2 counts 2, a paired FFMA2 4).
+# FP32-mixed: its current kernel (96-thread strips, 19 rows per strip).
+# FP32: none, not recounted since its projections went to paired FP32.
+FLOPS_2D_PER_CELL = {"fp32_mixed": (1403120218 + 2 * 1618423496 + 264650802 + 2 * 12582912 + 4 * 155189248) / 1048576.0,
+                     "fp32": None,
                      "fp64": (412078081 + 2 * 2396458776 + 341564899) / 1048576.0}
 # DRAM bytes (read + write) of one launch per cell, same captures; scaled by
 # cells to the bench size.  The writes undercount the stored DOFs: part of
 # the output is still in L2 when the kernel ends.  FP32-mixed: one launch at
 # the bench size itself, 2048^2, per strip height (a strip re-reads one parent
 # row, so the bytes depend slightly on it); heights not captured report none.
-TRAFFIC_2D_MIXED_BY_ROWS = {19: (783792128 + 692393472) / 4194304.0}
-TRAFFIC_2D_PER_CELL = {"fp32_mixed": None, "fp32": (178908928 + 122445056) / 1048576.0,
+TRAFFIC_2D_MIXED_BY_ROWS = {19: (780613888 + 691828736) / 4194304.0}
+TRAFFIC_2D_PER_CELL = {"fp32_mixed": None, "fp32": None,
                        "fp64": (358728448 + 294830336) / 1048576.0}
 
 
