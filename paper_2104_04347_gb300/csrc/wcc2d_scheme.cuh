@@ -192,6 +192,7 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
 
     T U[NV][P + 1][P + 1][P + 1];
     T w1[P + 1][P + 1][P + 1], w2[P + 1][P + 1][P + 1], Ep[P + 1][P + 1][P + 1];
+    float2 W[P + 1][P + 1][P + 1];  // plain FP32: the velocities (w1, w2) as pairs
     unroll<NV>([&](auto vc) {
         unroll<P + 1>([&](auto kc) {
             unroll<P + 1 - kc>([&](auto lc) { U[vc][kc][lc][0] = q[vc][qidx(kc, lc)]; });
@@ -225,6 +226,56 @@ __device__ __forceinline__ void parent_terms(const T (&q)[nvars(SYS)][nq(P)], T 
                     });
                     F[0] = (T)0.5 * s;
                     G[0] = F[0];
+                } else if constexpr (sizeof(T) == 4 && !MX) {
+                    // plain FP32: the two velocities, (q_xx, q_xy) and the two
+                    // energy fluxes two at a time in paired FP32 instructions
+                    // (FFMA2); the same operations as the scalar form below.
+                    // The FP32-mixed kernel keeps the scalar form: there the
+                    // pairs cost registers (spills) and it ran slower.
+                    float2 s12 = make_float2(U[1][k][l][m], U[2][k][l][m]);
+                    unroll<k + 1>([&](auto i) {
+                        unroll<l + 1>([&](auto j) {
+                            unroll<m + 1>([&](auto n) {
+                                if constexpr (i + j + n != 0) {
+                                    const float c = (float)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * U[0][i][j][n];
+                                    s12 = __ffma2_rn(make_float2(-c, -c), W[k - i][l - j][m - n], s12);
+                                }
+                            });
+                        });
+                    });
+                    const float inv_rho = recip_t(U[0][0][0][0]);
+                    W[k][l][m] = __fmul2_rn(s12, make_float2(inv_rho, inv_rho));
+                    float2 qx = make_float2(0.f, 0.f);
+                    float qyy = 0.f;
+                    unroll<k + 1>([&](auto i) {
+                        unroll<l + 1>([&](auto j) {
+                            unroll<m + 1>([&](auto n) {
+                                const float c = (float)(binomd(k, i) * binomd(l, j) * binomd(m, n));
+                                const float a1 = c * U[1][i][j][n], a2 = c * U[2][i][j][n];
+                                qx = __ffma2_rn(make_float2(a1, a1), W[k - i][l - j][m - n], qx);
+                                qyy = fmaf(a2, W[k - i][l - j][m - n].y, qyy);
+                            });
+                        });
+                    });
+                    const float p = (float)(law.gamma - 1.0) * (U[3][k][l][m] - 0.5f * (qx.x + qyy));
+                    Ep[k][l][m] = U[3][k][l][m] + p;
+                    float2 e12 = make_float2(0.f, 0.f);
+                    unroll<k + 1>([&](auto i) {
+                        unroll<l + 1>([&](auto j) {
+                            unroll<m + 1>([&](auto n) {
+                                const float c = (float)(binomd(k, i) * binomd(l, j) * binomd(m, n)) * Ep[i][j][n];
+                                e12 = __ffma2_rn(make_float2(c, c), W[k - i][l - j][m - n], e12);
+                            });
+                        });
+                    });
+                    F[0] = U[1][k][l][m];
+                    F[1] = qx.x + p;
+                    F[2] = qx.y;
+                    F[3] = e12.x;
+                    G[0] = U[2][k][l][m];
+                    G[1] = qx.y;
+                    G[2] = qyy + p;
+                    G[3] = e12.y;
                 } else {
                     // velocities from rho w = momentum, solved entry by entry
                     T s1 = U[1][k][l][m], s2 = U[2][k][l][m];
