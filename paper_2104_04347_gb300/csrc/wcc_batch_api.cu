@@ -816,6 +816,7 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
         cudaEventRecord(e1, b->stream);
         if (rc != WCC_OK || cudaEventSynchronize(e1) != cudaSuccess) {
             rc = rc != WCC_OK ? rc : WCC_E_CUDA;
+            restore_copy(false);  // the stage as it was, as far as the context allows
             break;
         }
         float ms = 0.f;
@@ -828,6 +829,7 @@ int wcc_batch_autotune(wcc_batch b, double cfl, int* ctas_out) {
                               cudaSuccess ||
                           cudaStreamSynchronize(b->stream) != cudaSuccess)) {
             rc = WCC_E_CUDA;
+            restore_copy(false);
             break;
         }
         if (!refused && ms < best) {
