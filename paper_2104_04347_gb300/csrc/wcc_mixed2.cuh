@@ -98,16 +98,6 @@ __device__ __forceinline__ ff2 fast_two_sum2(f2 a, f2 b) {
     return ff2{s, e};
 }
 
-__device__ __forceinline__ ff2 ff2_add(ff2 a, ff2 b) {
-    const ff2 s = two_sum2(a.hi, b.hi);
-    return fast_two_sum2(s.hi, s.lo + (a.lo + b.lo));
-}
-
-__device__ __forceinline__ ff2 ff2_add(ff2 a, f2 b) {
-    const ff2 s = two_sum2(a.hi, b);
-    return fast_two_sum2(s.hi, s.lo + a.lo);
-}
-
 // a + b where b is itself only FP32-accurate: Fast2Sum in place of TwoSum.
 // When |b| > |a.hi| the low bits lost are below ulp(b), within b's own error.
 __device__ __forceinline__ ff2 ff2_add_fp32(ff2 a, f2 b) {
@@ -115,36 +105,16 @@ __device__ __forceinline__ ff2 ff2_add_fp32(ff2 a, f2 b) {
     return fast_two_sum2(s.hi, s.lo + a.lo);
 }
 
-__device__ __forceinline__ ff2 ff2_neg(ff2 a) { return ff2{-a.hi, -a.lo}; }
-__device__ __forceinline__ ff2 ff2_sub(ff2 a, ff2 b) { return ff2_add(a, ff2_neg(b)); }
 __device__ __forceinline__ ff2 ff2_scale(ff2 a, float pow2) { return ff2{a.hi * f2(pow2), a.lo * f2(pow2)}; }
-
-__device__ __forceinline__ ff2 ff2_mul(ff2 a, ff2 b) {
-    const f2 p = a.hi * b.hi;
-    const f2 e = fma(a.hi, b.hi, -p);
-    return fast_two_sum2(p, fma(a.hi, b.lo, fma(a.lo, b.hi, e)));
-}
-
-// a / b for a normal b (a density): q1 = a.hi / b.hi, then the remainder
-// a - b q1 -- its leading part a.hi - b.hi q1 is exact (q1 is close to the
-// quotient, Sterbenz) and only needs FP32 accuracy -- divided by b.hi for
-// the correction q2.  One reciprocal estimate serves both quotients.
-__device__ __forceinline__ ff2 ff2_div(ff2 a, ff2 b) {
-    const f2 rb = rcp_approx(b.hi);
-    const f2 q1 = a.hi * rb;
-    const f2 p = b.hi * q1;
-    const f2 e = fma(b.hi, q1, -p);  // b.hi q1 = p + e exactly
-    const f2 rem = (a.hi - p) + (a.lo - fma(b.lo, q1, e));
-    return fast_two_sum2(q1, rem * rb);
-}
 
 // (a - b) rounded to a pair of floats, a and b close (Sterbenz on the hi parts)
 __device__ __forceinline__ f2 ff2_diff(ff2 a, ff2 b) { return (a.hi - b.hi) + (a.lo - b.lo); }
 
-// The same operations without the closing renormalisation, for results that
-// only feed further float-float arithmetic: (hi, lo) with lo a few ulp of hi
-// is as exact a representation of the value, and every operation above reads
-// both parts (a product takes hi * hi exactly and the lo cross terms).
+// Sums, products and quotients without a closing renormalisation, for
+// results that only feed further float-float arithmetic: (hi, lo) with lo a
+// few ulp of hi is as exact a representation of the value, and every
+// operation here reads both parts (a product takes hi * hi exactly and the lo
+// cross terms).
 __device__ __forceinline__ ff2 ff2_add_u(ff2 a, ff2 b) {
     const ff2 s = two_sum2(a.hi, b.hi);
     return ff2{s.hi, s.lo + (a.lo + b.lo)};
@@ -158,11 +128,15 @@ __device__ __forceinline__ ff2 ff2_mul_u(ff2 a, ff2 b) {
     const f2 e = fma(a.hi, b.hi, -p);
     return ff2{p, fma(a.hi, b.lo, fma(a.lo, b.hi, e))};
 }
+// a / b for a normal b (a density): q1 = a.hi / b.hi, then the remainder
+// a - b q1 -- its leading part a.hi - b.hi q1 is exact (q1 is close to the
+// quotient, Sterbenz) and only needs FP32 accuracy -- divided by b.hi for
+// the correction q2.  One reciprocal estimate serves both quotients.
 __device__ __forceinline__ ff2 ff2_div_u(ff2 a, ff2 b) {
     const f2 rb = rcp_approx(b.hi);
     const f2 q1 = a.hi * rb;
     const f2 p = b.hi * q1;
-    const f2 e = fma(b.hi, q1, -p);
+    const f2 e = fma(b.hi, q1, -p);  // b.hi q1 = p + e exactly
     const f2 rem = (a.hi - p) + (a.lo - fma(b.lo, q1, e));
     return ff2{q1, rem * rb};
 }
@@ -186,11 +160,7 @@ __device__ __forceinline__ ff2 ff2_add_diff(ff2 a, ff2 b, ff2 c) {
 // compensation buys).
 template <bool COMP>
 struct FF {
-    static __device__ __forceinline__ ff2 add(ff2 a, ff2 b) { return ff2_add(a, b); }
     static __device__ __forceinline__ ff2 add(ff2 a, f2 b) { return ff2_add_fp32(a, b); }
-    static __device__ __forceinline__ ff2 sub(ff2 a, ff2 b) { return ff2_sub(a, b); }
-    static __device__ __forceinline__ ff2 mul(ff2 a, ff2 b) { return ff2_mul(a, b); }
-    static __device__ __forceinline__ ff2 div(ff2 a, ff2 b) { return ff2_div(a, b); }
     static __device__ __forceinline__ f2 diff(ff2 a, ff2 b) { return ff2_diff(a, b); }
     static __device__ __forceinline__ ff2 add_u(ff2 a, ff2 b) { return ff2_add_u(a, b); }
     static __device__ __forceinline__ ff2 add_u(ff2 a, f2 b) { return ff2_add_fp32_u(a, b); }
@@ -205,7 +175,6 @@ struct FF<false> {
     static __device__ __forceinline__ ff2 mk(f2 h) { return ff2{h, f2(0.f)}; }
     static __device__ __forceinline__ ff2 add(ff2 a, ff2 b) { return mk(a.hi + b.hi); }
     static __device__ __forceinline__ ff2 add(ff2 a, f2 b) { return mk(a.hi + b); }
-    static __device__ __forceinline__ ff2 sub(ff2 a, ff2 b) { return mk(a.hi - b.hi); }
     static __device__ __forceinline__ ff2 mul(ff2 a, ff2 b) { return mk(a.hi * b.hi); }
     static __device__ __forceinline__ ff2 div(ff2 a, ff2 b) { return mk(fdiv_fast(a.hi, b.hi)); }
     static __device__ __forceinline__ f2 diff(ff2 a, ff2 b) { return a.hi - b.hi; }
