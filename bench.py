@@ -243,14 +243,32 @@ class ClockSampler:
 # ------------------------------------------------------------ CPU oracle
 
 
-def cpu_oracle_rate(log2n, seconds):
-    """Oracle cell-updates/s on the host cores over a bounded sample of the
-    workload: a contiguous window of the N = 2^log2n grid around the jump,
-    advanced with the CFL rule until ~`seconds` of CPU time are spent."""
+def host_info():
+    """The host the oracle ran on: logical cores, architecture and CPU model
+    (from lscpu where it exists)."""
+    import platform
+
+    model = platform.processor() or platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"nproc": os.cpu_count() or 1, "machine": platform.machine(), "cpu": model}
+
+
+def cpu_oracle_rate(log2n, seconds, threads=None):
+    """Oracle cell-updates/s on the host cores (all of them unless `threads`
+    is given) over a bounded sample of the workload: a contiguous window of
+    the N = 2^log2n grid around the jump, advanced with the CFL rule until
+    ~`seconds` of wall time are spent."""
     import oracle
     from paper_2104_04347_gb300 import inputs
 
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     oracle.set_threads(threads)
     N = 1 << log2n
     pr = inputs.euler_riemann_seeded(N, P)
@@ -317,8 +335,9 @@ def run_reference(args, rank, world):
                    "precision": "fp64", "halfsteps_per_step": HALFSTEPS_PER_STEP, "cfl": CFL,
                    "limiter": True, "parallelism": f"host cores x{cores}", "sample_cells": win + 1},
         "cpu_baseline": {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host": host_info()},
         "e2e": {"value": rate, "unit": "cell-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "per_full_step": {"value": rate / 2, "unit": "cell-full-steps/s"},
     }
     print(json.dumps(line), flush=True)
 
@@ -585,6 +604,7 @@ def run_wcc(args, rank, world):
                    "limiter": True, "l2": "state > L2 (252 / 403 MB per stage), no flush needed",
                    "parallelism": f"replicas x{world}"},
         "roofline": roof,
+        "per_full_step": {"value": head["value"] / 2, "unit": "cell-full-steps/s"},
         "e2e": e2e,
         "gpu_launches": head["gpu_launches"],
         "clocks": clk,
@@ -593,8 +613,10 @@ def run_wcc(args, rank, world):
     if rank == 0 and world == 1:
         line["l1_vs_oracle"] = l1_check()
         rate, cores, sample = cpu_oracle_rate(args.log2n, args.cpu_seconds)
+        rate1, _, sample1 = cpu_oracle_rate(args.log2n, args.cpu_seconds / 4, threads=1)
         line["cpu_baseline"] = {"value": rate, "unit": "cell-updates/s", "cores": cores, "kind": "oracle",
-                                "sample": sample}
+                                "sample": sample, "host": host_info(),
+                                "single_thread": {"value": rate1, "unit": "cell-updates/s", "sample": sample1}}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -24,5 +24,19 @@ def test_reference_arm_json_line():
     assert d["config"]["workload"].startswith("euler1d-riemann-N2^12-P3")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert cb["host"]["nproc"] >= 1 and cb["host"]["machine"] and cb["host"]["cpu"]
+    assert d["per_full_step"]["value"] == d["value"] / 2
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_oracle_rate_on_one_thread():
+    import oracle
+    sys.path.insert(0, ROOT)
+    import bench
+    before = oracle.get_threads()
+    try:
+        rate, threads, sample = bench.cpu_oracle_rate(12, 0.5, threads=1)
+    finally:
+        oracle.set_threads(before)
+    assert threads == 1 and rate > 0 and "half-steps" in sample
