@@ -364,10 +364,23 @@ def job_throughput(local_units, local_seconds, device):
     return reduce_over_ranks(local_units, "sum", device) / reduce_over_ranks(local_seconds, "max", device)
 
 
+def riemann_l1_exact(pr, q, t, parity=0):
+    """L1 distance (mean over the cells) of the centre density point values
+    q[:, 0, 0] of a stage from the exact solution of the seeded Riemann
+    problem (jump at 0.5) at time t."""
+    from oracle import exact
+    from paper_2104_04347_gb300 import inputs
+
+    x = inputs.centres(pr.N, pr.x_l, pr.x_r, pr.bc, parity)
+    rho, _, _ = exact.riemann_sample(*inputs.riemann_states(), (x - 0.5) / t)
+    return float(np.mean(np.abs(q[:, 0, 0] - rho)))
+
+
 def l1_check(log2n_small=12, halfsteps=2000):
     """L1 error (centre point values, scaled per variable) of both GPU
     precisions against the FP64 oracle on the bench workload at a small N,
-    each replaying its own realised dt sequence."""
+    each replaying its own realised dt sequence; and the density's L1
+    distance from the exact Riemann solution for both and for the oracle."""
     import oracle
     from paper_2104_04347_gb300 import inputs, wcc
 
@@ -388,6 +401,10 @@ def l1_check(log2n_small=12, halfsteps=2000):
         ref.step_dt(dts)
         scale = np.max(np.abs(ref.q[:, :, 0]), axis=0)
         out[name] = float(np.max(np.mean(np.abs(q[:, :, 0] - ref.q[:, :, 0]), axis=0) / scale))
+        t = float(np.sum(dts))
+        out.setdefault("density_l1_vs_exact", {"t": t})
+        out["density_l1_vs_exact"][name] = riemann_l1_exact(pr, q, t, halfsteps % 2)
+        out["density_l1_vs_exact"][f"oracle_on_{name}_dts"] = riemann_l1_exact(pr, ref.q, t, halfsteps % 2)
     return out
 
 

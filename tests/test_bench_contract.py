@@ -40,3 +40,25 @@ def test_oracle_rate_on_one_thread():
     finally:
         oracle.set_threads(before)
     assert threads == 1 and rate > 0 and "half-steps" in sample
+
+
+def test_riemann_l1_exact_of_the_oracle():
+    # the oracle's density on the bench workload (N = 2^10) approaches the
+    # exact Riemann solution: first order in L1 at the discontinuities
+    import numpy as np
+    import oracle
+    from paper_2104_04347_gb300 import inputs
+    sys.path.insert(0, ROOT)
+    import bench
+    errs = []
+    for N in (256, 1024):
+        pr = inputs.euler_riemann_seeded(N, 3)
+        law = oracle.make_law(oracle.EULER, 3, limiter=True, bc=oracle.TRANSMISSIVE)
+        s = oracle.Solver(law, pr.q0, pr.dx)
+        dts = oracle.constant_speed_dts(0.05, 0.2 * pr.dx / oracle.max_speed(law, pr.q0))
+        s.step_dt(dts)
+        errs.append(bench.riemann_l1_exact(pr, s.q, float(np.sum(dts)), len(dts) % 2))
+    assert errs[1] < 0.6 * errs[0] and errs[1] < 5e-3, errs
+    # the initial data itself is the exact solution at t -> 0
+    pr = inputs.euler_riemann_seeded(1000, 3)
+    assert bench.riemann_l1_exact(pr, pr.q0, 1e-12) < 2e-3
