@@ -402,7 +402,8 @@ def l1_check(log2n_small=12, halfsteps=2000):
         scale = np.max(np.abs(ref.q[:, :, 0]), axis=0)
         out[name] = float(np.max(np.mean(np.abs(q[:, :, 0] - ref.q[:, :, 0]), axis=0) / scale))
         t = float(np.sum(dts))
-        out.setdefault("density_l1_vs_exact", {"t": t})
+        out.setdefault("density_l1_vs_exact", {})
+        out["density_l1_vs_exact"][f"t_{name}"] = t
         out["density_l1_vs_exact"][name] = riemann_l1_exact(pr, q, t, halfsteps % 2)
         out["density_l1_vs_exact"][f"oracle_on_{name}_dts"] = riemann_l1_exact(pr, ref.q, t, halfsteps % 2)
     return out
